@@ -1,0 +1,413 @@
+/*
+ * tvi_oracle.c -- plain, slow, FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+ *
+ * Step-by-step backward-Euler Newton integration with dense LU, and the
+ * discrete adjoint with dense LU of the transposed step Jacobian.  No chunks,
+ * no cyclic reduction, no blocking: each series is integrated one step at a
+ * time exactly as the definitions in tvi_oracle.h state.  Series are
+ * independent (paper Sec. 2.1: initial conditions, parameters and times may
+ * differ per series), so the loop over series runs under OpenMP.
+ */
+#include "tvi_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Models: h(y,t;p), j = dh/dy, (dh/dp)^T a                                  */
+/* ------------------------------------------------------------------------ */
+
+int tvo_param_count(const tvo_model* m) {
+  if (!m || m->n <= 0) return -1;
+  switch (m->kind) {
+    case TVO_LINEAR: return m->n * m->n;
+    case TVO_VDP: return m->n == 2 ? 1 : -1;
+    case TVO_MLP_TANH:
+    case TVO_MLP_SILU:
+      if (m->h1 <= 0 || m->h2 <= 0) return -1;
+      return m->h1 * m->n + m->h1 + m->h2 * m->h1 + m->h2 + m->n * m->h2 + m->n;
+    default: return -1;
+  }
+}
+
+static double act(int kind, double z) {
+  if (kind == TVO_MLP_TANH) return tanh(z);
+  return z / (1.0 + exp(-z)); /* SiLU: z * sigmoid(z) */
+}
+
+static double act_d(int kind, double z) {
+  if (kind == TVO_MLP_TANH) {
+    double t = tanh(z);
+    return 1.0 - t * t;
+  }
+  double s = 1.0 / (1.0 + exp(-z));
+  return s + z * s * (1.0 - s);
+}
+
+/* Views into the flat MLP parameter vector. */
+typedef struct {
+  const double *W1, *b1, *W2, *b2, *W3, *b3;
+} mlp_view;
+
+static mlp_view mlp_split(const tvo_model* m, const double* p) {
+  mlp_view v;
+  int n = m->n, h1 = m->h1, h2 = m->h2;
+  v.W1 = p;
+  v.b1 = v.W1 + h1 * n;
+  v.W2 = v.b1 + h1;
+  v.b2 = v.W2 + h2 * h1;
+  v.W3 = v.b2 + h2;
+  v.b3 = v.W3 + n * h2;
+  return v;
+}
+
+/* Forward pass of the MLP keeping pre-activations z1[h1], z2[h2], z3[n] and
+ * activations a1[h1], a2[h2]; returns h in out[n]. */
+static void mlp_forward(const tvo_model* m, const double* p, const double* y, double* z1,
+                        double* a1, double* z2, double* a2, double* z3, double* out) {
+  int n = m->n, h1 = m->h1, h2 = m->h2;
+  mlp_view v = mlp_split(m, p);
+  for (int r = 0; r < h1; ++r) {
+    double s = v.b1[r];
+    for (int c = 0; c < n; ++c) s += v.W1[r * n + c] * y[c];
+    z1[r] = s;
+    a1[r] = act(m->kind, s);
+  }
+  for (int r = 0; r < h2; ++r) {
+    double s = v.b2[r];
+    for (int c = 0; c < h1; ++c) s += v.W2[r * h1 + c] * a1[c];
+    z2[r] = s;
+    a2[r] = act(m->kind, s);
+  }
+  for (int r = 0; r < n; ++r) {
+    double s = v.b3[r];
+    for (int c = 0; c < h2; ++c) s += v.W3[r * h2 + c] * a2[c];
+    z3[r] = s;
+    out[r] = (m->kind == TVO_MLP_TANH) ? tanh(s) : s;
+  }
+}
+
+static double out_d(const tvo_model* m, double z3) {
+  if (m->kind == TVO_MLP_TANH) {
+    double t = tanh(z3);
+    return 1.0 - t * t;
+  }
+  return 1.0; /* SiLU network: linear output layer */
+}
+
+void tvo_rhs(const tvo_model* m, const double* p, const double* y, double t, double* h) {
+  (void)t; /* all models here are autonomous */
+  int n = m->n;
+  if (m->kind == TVO_LINEAR) {
+    for (int r = 0; r < n; ++r) {
+      double s = 0.0;
+      for (int c = 0; c < n; ++c) s += p[r * n + c] * y[c];
+      h[r] = s;
+    }
+  } else if (m->kind == TVO_VDP) {
+    double mu = p[0];
+    h[0] = y[1];
+    h[1] = mu * (1.0 - y[0] * y[0]) * y[1] - y[0];
+  } else {
+    double* w = (double*)malloc(sizeof(double) * (2 * m->h1 + 2 * m->h2 + n));
+    mlp_forward(m, p, y, w, w + m->h1, w + 2 * m->h1, w + 2 * m->h1 + m->h2,
+                w + 2 * m->h1 + 2 * m->h2, h);
+    free(w);
+  }
+}
+
+void tvo_jac(const tvo_model* m, const double* p, const double* y, double t, double* j) {
+  (void)t;
+  int n = m->n;
+  if (m->kind == TVO_LINEAR) {
+    memcpy(j, p, sizeof(double) * n * n);
+  } else if (m->kind == TVO_VDP) {
+    double mu = p[0];
+    j[0] = 0.0;
+    j[1] = 1.0;
+    j[2] = -2.0 * mu * y[0] * y[1] - 1.0;
+    j[3] = mu * (1.0 - y[0] * y[0]);
+  } else {
+    /* j = D3 W3 D2 W2 D1 W1 with D_i = diag(act'(z_i)); chain rule written out
+     * column by column of the input: J[:, c] = d h / d y_c. */
+    int h1 = m->h1, h2 = m->h2;
+    mlp_view v = mlp_split(m, p);
+    double* w = (double*)malloc(sizeof(double) * (3 * h1 + 3 * h2 + 2 * n));
+    double *z1 = w, *a1 = z1 + h1, *z2 = a1 + h1, *a2 = z2 + h2, *z3 = a2 + h2, *o = z3 + n;
+    double *u1 = o + n, *u2 = u1 + h1;
+    mlp_forward(m, p, y, z1, a1, z2, a2, z3, o);
+    for (int c = 0; c < n; ++c) {
+      for (int r = 0; r < h1; ++r) u1[r] = act_d(m->kind, z1[r]) * v.W1[r * n + c];
+      for (int r = 0; r < h2; ++r) {
+        double s = 0.0;
+        for (int q = 0; q < h1; ++q) s += v.W2[r * h1 + q] * u1[q];
+        u2[r] = act_d(m->kind, z2[r]) * s;
+      }
+      for (int r = 0; r < n; ++r) {
+        double s = 0.0;
+        for (int q = 0; q < h2; ++q) s += v.W3[r * h2 + q] * u2[q];
+        j[r * n + c] = out_d(m, z3[r]) * s;
+      }
+    }
+    free(w);
+  }
+}
+
+void tvo_vjp_p(const tvo_model* m, const double* p, const double* y, double t, const double* a,
+               double scale, double* gp) {
+  (void)t;
+  int n = m->n;
+  if (m->kind == TVO_LINEAR) {
+    /* h_r = sum_c A_rc y_c  =>  dh_r/dA_rc = y_c, so (dh/dA)^T a = a y^T. */
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) gp[r * n + c] += scale * a[r] * y[c];
+  } else if (m->kind == TVO_VDP) {
+    /* dh/dmu = [0, (1 - y1^2) y2]. */
+    gp[0] += scale * a[1] * (1.0 - y[0] * y[0]) * y[1];
+  } else {
+    int h1 = m->h1, h2 = m->h2;
+    mlp_view v = mlp_split(m, p);
+    double* w = (double*)malloc(sizeof(double) * (3 * h1 + 3 * h2 + 3 * n));
+    double *z1 = w, *a1 = z1 + h1, *z2 = a1 + h1, *a2 = z2 + h2, *z3 = a2 + h2, *o = z3 + n;
+    double *d3 = o + n, *d2 = d3 + n, *d1 = d2 + h2;
+    mlp_forward(m, p, y, z1, a1, z2, a2, z3, o);
+    /* gradient slots, same order as the flat layout */
+    double* gW1 = gp;
+    double* gb1 = gW1 + h1 * n;
+    double* gW2 = gb1 + h1;
+    double* gb2 = gW2 + h2 * h1;
+    double* gW3 = gb2 + h2;
+    double* gb3 = gW3 + n * h2;
+    for (int r = 0; r < n; ++r) d3[r] = a[r] * out_d(m, z3[r]);
+    for (int r = 0; r < n; ++r) {
+      gb3[r] += scale * d3[r];
+      for (int c = 0; c < h2; ++c) gW3[r * h2 + c] += scale * d3[r] * a2[c];
+    }
+    for (int c = 0; c < h2; ++c) {
+      double s = 0.0;
+      for (int r = 0; r < n; ++r) s += v.W3[r * h2 + c] * d3[r];
+      d2[c] = s * act_d(m->kind, z2[c]);
+    }
+    for (int r = 0; r < h2; ++r) {
+      gb2[r] += scale * d2[r];
+      for (int c = 0; c < h1; ++c) gW2[r * h1 + c] += scale * d2[r] * a1[c];
+    }
+    for (int c = 0; c < h1; ++c) {
+      double s = 0.0;
+      for (int r = 0; r < h2; ++r) s += v.W2[r * h1 + c] * d2[r];
+      d1[c] = s * act_d(m->kind, z1[c]);
+    }
+    for (int r = 0; r < h1; ++r) {
+      gb1[r] += scale * d1[r];
+      for (int c = 0; c < n; ++c) gW1[r * n + c] += scale * d1[r] * y[c];
+    }
+    free(w);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense LU with partial pivoting: solve M x = rhs (M is n x n, row-major).  */
+/* Overwrites M and rhs; returns 0, or 1 if a pivot is exactly zero.         */
+/* ------------------------------------------------------------------------ */
+static int lu_solve(int n, double* M, double* rhs) {
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    double best = fabs(M[k * n + k]);
+    for (int r = k + 1; r < n; ++r) {
+      double v = fabs(M[r * n + k]);
+      if (v > best) {
+        best = v;
+        piv = r;
+      }
+    }
+    if (best == 0.0) return 1;
+    if (piv != k) {
+      for (int c = 0; c < n; ++c) {
+        double t = M[k * n + c];
+        M[k * n + c] = M[piv * n + c];
+        M[piv * n + c] = t;
+      }
+      double t = rhs[k];
+      rhs[k] = rhs[piv];
+      rhs[piv] = t;
+    }
+    for (int r = k + 1; r < n; ++r) {
+      double f = M[r * n + k] / M[k * n + k];
+      M[r * n + k] = 0.0;
+      for (int c = k + 1; c < n; ++c) M[r * n + c] -= f * M[k * n + c];
+      rhs[r] -= f * rhs[k];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double s = rhs[r];
+    for (int c = r + 1; c < n; ++c) s -= M[r * n + c] * rhs[c];
+    rhs[r] = s / M[r * n + r];
+  }
+  return 0;
+}
+
+static double inf_norm(int n, const double* v) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double a = fabs(v[i]);
+    if (!(a <= s)) s = a; /* also propagates NaN */
+  }
+  return s;
+}
+
+static double step_dt(const double* tb, const int* lengths, int b, int k) {
+  /* dt_k = t_k - t_{k-1} (Sec. 2.2); padded steps beyond the series length have dt = 0 */
+  if (lengths && k > lengths[b]) return 0.0;
+  return tb[k] - tb[k - 1];
+}
+
+int tvo_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward: Sec. 2.2 backward Euler + Newton, previous-step starting guess.   */
+/* ------------------------------------------------------------------------ */
+int tvo_forward(const tvo_model* m, int B, int N, const double* y0, const double* times,
+                const int* lengths, const double* params, double tol_abs, double tol_rel,
+                int max_iter, int nthreads, double* y, int* iters, int* status) {
+  int P = tvo_param_count(m);
+  if (P < 0 || B < 0 || N < 0 || max_iter < 0) return TVO_BADARG;
+  int n = m->n;
+  int worst = TVO_OK;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(max : worst)
+#endif
+  for (int b = 0; b < B; ++b) {
+    const double* p = m->per_series ? params + (size_t)b * P : params;
+    const double* tb = times + (size_t)b * (N + 1);
+    double* yb = y + (size_t)b * (N + 1) * n;
+    double* G = (double*)malloc(sizeof(double) * (3 * n + 2 * n * n));
+    double* hv = G + n;
+    double* yk = hv + n;
+    double* J = yk + n;
+    int st = TVO_OK;
+    memcpy(yb, y0 + (size_t)b * n, sizeof(double) * n);
+    for (int k = 1; k <= N; ++k) {
+      const double* yprev = yb + (size_t)(k - 1) * n;
+      double dt = step_dt(tb, lengths, b, k);
+      double tk = tb[k];
+      memcpy(yk, yprev, sizeof(double) * n); /* 0y_{k} = y_{k-1} */
+      double norm0 = 0.0;
+      int it = 0;
+      for (;;) {
+        /* G = y_k - y_{k-1} - dt h(y_k, t_k; p) */
+        tvo_rhs(m, p, yk, tk, hv);
+        for (int i = 0; i < n; ++i) G[i] = yk[i] - yprev[i] - dt * hv[i];
+        double nr = inf_norm(n, G);
+        if (it == 0) norm0 = nr;
+        if (!isfinite(nr)) {
+          st = TVO_NONFINITE;
+          break;
+        }
+        if (nr <= tol_abs || nr <= tol_rel * norm0) break;
+        if (it >= max_iter) {
+          if (st == TVO_OK) st = TVO_NOT_CONVERGED;
+          break;
+        }
+        /* J = I - dt j(y_k); y_k -= J^{-1} G */
+        tvo_jac(m, p, yk, tk, J);
+        for (int r = 0; r < n; ++r)
+          for (int c = 0; c < n; ++c) J[r * n + c] = (r == c ? 1.0 : 0.0) - dt * J[r * n + c];
+        if (lu_solve(n, J, G)) {
+          st = TVO_SINGULAR;
+          break;
+        }
+        for (int i = 0; i < n; ++i) yk[i] -= G[i];
+        ++it;
+      }
+      if (iters) iters[(size_t)b * N + (k - 1)] = it;
+      memcpy(yb + (size_t)k * n, yk, sizeof(double) * n);
+      if (st == TVO_NONFINITE || st == TVO_SINGULAR) {
+        /* leave the rest of the trajectory as NaN: nothing after this is defined */
+        for (int q = k + 1; q <= N; ++q)
+          for (int i = 0; i < n; ++i) yb[(size_t)q * n + i] = NAN;
+        if (iters)
+          for (int q = k + 1; q <= N; ++q) iters[(size_t)b * N + (q - 1)] = 0;
+        break;
+      }
+    }
+    if (status) status[b] = st;
+    if (st > worst) worst = st;
+    free(G);
+  }
+  return worst;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint: App. A.1, discrete form of the backward-Euler adjoint.           */
+/* ------------------------------------------------------------------------ */
+int tvo_adjoint(const tvo_model* m, int B, int N, const double* times, const int* lengths,
+                const double* params, const double* y, const double* grad_out, int nthreads,
+                double* dparams, double* dy0) {
+  int P = tvo_param_count(m);
+  if (P < 0 || B < 0 || N < 0) return TVO_BADARG;
+  int n = m->n;
+  size_t dp_len = m->per_series ? (size_t)B * P : (size_t)P;
+  memset(dparams, 0, sizeof(double) * dp_len);
+  int worst = TVO_OK;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#else
+  nthreads = 1;
+#endif
+  /* shared parameters: one private accumulator per series, summed in series
+   * order afterwards so the result does not depend on the thread count */
+  double* acc = NULL;
+  if (!m->per_series) acc = (double*)calloc((size_t)B * P, sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(max : worst)
+#endif
+  for (int b = 0; b < B; ++b) {
+    const double* p = m->per_series ? params + (size_t)b * P : params;
+    double* gp = m->per_series ? dparams + (size_t)b * P : acc + (size_t)b * P;
+    const double* tb = times + (size_t)b * (N + 1);
+    const double* yb = y + (size_t)b * (N + 1) * n;
+    const double* gb = grad_out + (size_t)b * (N + 1) * n;
+    double* a = (double*)malloc(sizeof(double) * (2 * n + n * n));
+    double* rhs = a + n;
+    double* JT = rhs + n;
+    for (int i = 0; i < n; ++i) a[i] = 0.0; /* a_{N+1} = 0 */
+    for (int k = N; k >= 1; --k) {
+      double dt = step_dt(tb, lengths, b, k);
+      const double* yk = yb + (size_t)k * n;
+      /* (I - dt j_k)^T a_k = a_{k+1} + dL/dy_k */
+      for (int i = 0; i < n; ++i) rhs[i] = a[i] + gb[(size_t)k * n + i];
+      double J[64 * 64];
+      double* Jp = (n <= 64) ? J : (double*)malloc(sizeof(double) * n * n);
+      tvo_jac(m, p, yk, tb[k], Jp);
+      for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) JT[c * n + r] = (r == c ? 1.0 : 0.0) - dt * Jp[r * n + c];
+      if (Jp != J) free(Jp);
+      if (lu_solve(n, JT, rhs)) {
+        if (TVO_SINGULAR > worst) worst = TVO_SINGULAR;
+      }
+      for (int i = 0; i < n; ++i) a[i] = rhs[i];
+      /* dL/dp += dt_k (dh/dp)^T a_k */
+      if (dt != 0.0) tvo_vjp_p(m, p, yk, tb[k], a, dt, gp);
+    }
+    if (dy0)
+      for (int i = 0; i < n; ++i) dy0[(size_t)b * n + i] = a[i] + gb[i];
+    free(a);
+  }
+  if (acc) {
+    for (int b = 0; b < B; ++b)
+      for (int q = 0; q < P; ++q) dparams[q] += acc[(size_t)b * P + q];
+    free(acc);
+  }
+  return worst;
+}

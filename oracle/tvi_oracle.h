@@ -1,0 +1,89 @@
+/*
+ * tvi_oracle.h -- CPU FP64 oracle for batched backward-Euler integration and
+ * its discrete adjoint.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the independent checker of the
+ * GPU path.  Only the test suite, the smoke check and the benchmark's CPU
+ * baseline leg may load it.  It shares no code, header, table or helper with
+ * the CUDA library, and the CUDA library never calls it.
+ *
+ * What it computes (the plain definitions the chunked method reaches):
+ *   forward  -- for every series b and every step k = 1..N, the root of the
+ *               backward-Euler equation  y_k - y_{k-1} - dt_k h(y_k, t_k; p) = 0
+ *               (paper Sec. 2.2, Eq. backward-euler), found by Newton's method
+ *               from the previous-step guess y_{k-1} with the discrete Jacobian
+ *               I - dt_k j(y_k), j = dh/dy (Sec. 2.2), each Newton system
+ *               solved by dense LU with partial pivoting.
+ *   adjoint  -- the exact gradient of a loss L(y_0..y_N) through those discrete
+ *               equations (App. A.1, derived discrete form):
+ *                 a_{N+1} = 0
+ *                 (I - dt_k j(y_k))^T a_k = a_{k+1} + dL/dy_k,   k = N..1
+ *                 dL/dp   = sum_k dt_k (dh/dp(y_k, t_k; p))^T a_k
+ *                 dL/dy_0 = a_1 + dL/dy_0 (explicit part)
+ *
+ * Model right-hand sides h(y, t; p) (the ODE of Sec. 2.1, Eqs. 1-2):
+ *   TVO_LINEAR    h = A y,                    p = A (n x n, row-major)
+ *   TVO_VDP       h = [y2, mu (1 - y1^2) y2 - y1],   p = mu  (n = 2)
+ *   TVO_MLP_TANH  h = tanh(W3 tanh(W2 tanh(W1 y + b1) + b2) + b3)
+ *                 (the neural ODE of Sec. 5.1.1 without the forcing input)
+ *   TVO_MLP_SILU  h = W3 silu(W2 silu(W1 y + b1) + b2) + b3
+ * MLP parameter layout (flat, FP64): W1[h1][n] b1[h1] W2[h2][h1] b2[h2]
+ * W3[n][h2] b3[n]; W are row-major (out x in).
+ *
+ * Array layouts (row-major, contiguous):
+ *   y0 [B][n], times [B][N+1], lengths [B] (or NULL = all N steps real),
+ *   params [B][P] when per_series else [P], y [B][N+1][n] with y[b][0] = y0[b],
+ *   grad_out [B][N+1][n], dparams same shape as params, dy0 [B][n].
+ * Steps k > lengths[b] are padding: their dt is taken as 0, so y_k = y_{k-1}.
+ */
+#ifndef TVI_ORACLE_H
+#define TVI_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { TVO_LINEAR = 0, TVO_VDP = 1, TVO_MLP_TANH = 2, TVO_MLP_SILU = 3 };
+enum { TVO_OK = 0, TVO_NOT_CONVERGED = 1, TVO_NONFINITE = 2, TVO_SINGULAR = 3, TVO_BADARG = -1 };
+
+typedef struct {
+  int kind;        /* TVO_LINEAR / TVO_VDP / TVO_MLP_TANH / TVO_MLP_SILU */
+  int n;           /* state size */
+  int h1, h2;      /* MLP hidden widths (ignored otherwise) */
+  int per_series;  /* 1: params [B][P]; 0: one shared parameter vector [P] */
+} tvo_model;
+
+/* Number of parameters P of one parameter vector, or -1 on a bad model. */
+int tvo_param_count(const tvo_model* m);
+
+/* h(y, t; p) into h[n]. */
+void tvo_rhs(const tvo_model* m, const double* p, const double* y, double t, double* h);
+/* j = dh/dy into j[n][n] (row-major: j[r*n+c] = dh_r/dy_c). */
+void tvo_jac(const tvo_model* m, const double* p, const double* y, double t, double* j);
+/* gp[P] += scale * (dh/dp)^T a. */
+void tvo_vjp_p(const tvo_model* m, const double* p, const double* y, double t,
+               const double* a, double scale, double* gp);
+
+/* Step-by-step backward-Euler Newton integration.  Per step, Newton stops when
+ * ||G||_inf <= tol_abs or ||G||_inf <= tol_rel * ||G_0||_inf, or after
+ * max_iter updates.  iters [B][N] (or NULL) receives the Newton updates taken
+ * per step; status [B] (or NULL) receives TVO_OK / TVO_NOT_CONVERGED /
+ * TVO_NONFINITE / TVO_SINGULAR for the series.  nthreads <= 0 uses the OpenMP
+ * default.  Returns TVO_OK, TVO_BADARG, or the worst series status. */
+int tvo_forward(const tvo_model* m, int B, int N, const double* y0, const double* times,
+                const int* lengths, const double* params, double tol_abs, double tol_rel,
+                int max_iter, int nthreads, double* y, int* iters, int* status);
+
+/* Discrete adjoint of tvo_forward's equations at the trajectory y.  Writes
+ * dparams (zeroed first) and dy0 (may be NULL). */
+int tvo_adjoint(const tvo_model* m, int B, int N, const double* times, const int* lengths,
+                const double* params, const double* y, const double* grad_out, int nthreads,
+                double* dparams, double* dy0);
+
+/* Threads OpenMP will use for nthreads <= 0. */
+int tvo_max_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,129 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module only draws inputs (initial states, time grids, parameters, loss
+gradients).  It holds none of the integration method's arithmetic, and both
+the oracle and the CUDA path consume what it returns.  Every generator takes
+an explicit seed (numpy PCG64) so that both sides see identical inputs.
+
+Each generator returns a dict with
+  spec    -- model description {"kind", "n", "hidden", "per_series"}
+  y0      -- [B][n] float64
+  times   -- [B][N+1] float64 (times[b][0] is the start time)
+  params  -- float64, [B][P] when spec["per_series"] else [P]
+  lengths -- [B] int32, or None when every series uses all N steps
+plus generator-specific extras.
+
+Default sizes are the paper-shaped workloads:
+  linear_stiff  n=4 stiff linear system, 16 series, 1000 uniform steps on [0, 1]
+  vdp           van der Pol n=2, 128 series, 10,000 log-spaced steps per series
+  mlp_ode       neural ODE n=16, MLP 16-64-64-16 tanh, 64 series, 2000 steps on [0, 10]
+  mlp_large     neural ODE n=32, MLP 32-128-128-32 SiLU, 512 series, 20,000 padded
+                steps with per-series lengths uniform in [2000, 20000]
+"""
+import numpy as np
+
+SEED_LINEAR, SEED_VDP, SEED_MLP, SEED_PREDICTOR, SEED_MLP_LARGE = 1001, 1002, 1003, 1004, 1005
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def uniform_times(B, N, t_end):
+    """t_k = k t_end / N for every series."""
+    return np.tile(np.linspace(0.0, t_end, N + 1), (B, 1))
+
+
+def log_times(B, N, t_end, decades=6.0):
+    """t_0 = 0 and t_k = t_end 10^(-decades + decades (k-1)/(N-1)), k = 1..N:
+    a geometric grid from t_end 10^-decades up to t_end."""
+    k = np.arange(1, N + 1, dtype=np.float64)
+    t = np.empty(N + 1)
+    t[0] = 0.0
+    t[1:] = t_end * 10.0 ** (-decades + decades * (k - 1) / max(N - 1, 1))
+    return np.tile(t, (B, 1))
+
+
+def linear_stiff(seed=SEED_LINEAR, B=16, N=1000, n=4, t_end=1.0, lam_decades=(0.0, 4.0)):
+    """dy/dt = A y with A = -Q diag(lam) Q^T, Q a seeded random orthogonal matrix
+    (QR of a Gaussian matrix, signs fixed so diag(R) > 0) and lam log-uniform in
+    [10^lam_decades[0], 10^lam_decades[1]].  One A shared by all series."""
+    g = _rng(seed)
+    X = g.standard_normal((n, n))
+    Q, R = np.linalg.qr(X)
+    Q = Q * np.sign(np.diag(R))[None, :]
+    lam = 10.0 ** g.uniform(lam_decades[0], lam_decades[1], n)
+    A = -(Q * lam[None, :]) @ Q.T
+    y0 = g.standard_normal((B, n))
+    return {"spec": {"kind": "linear", "n": n, "hidden": (0, 0), "per_series": False},
+            "y0": y0, "times": uniform_times(B, N, t_end), "params": A.reshape(-1).copy(),
+            "lengths": None, "Q": Q, "lam": lam}
+
+
+def vdp(seed=SEED_VDP, B=128, N=10000, t_max=3.0, resolve=500.0, mu_decades=(1.0, 3.0)):
+    """van der Pol, mu log-uniform in [10, 1000] per series, y0 uniform in [-2, 2]^2,
+    N log-spaced steps (6 decades).  Series b ends at t_end = min(t_max, resolve / mu_b):
+    the last (largest) log step is then at most 0.0014 t_end, so mu dt <= 0.69 at
+    every step and the grid resolves the fast time scale 1/mu everywhere.  Times
+    therefore differ per series."""
+    g = _rng(seed)
+    mu = 10.0 ** g.uniform(mu_decades[0], mu_decades[1], B)
+    y0 = g.uniform(-2.0, 2.0, (B, 2))
+    t_end = np.minimum(t_max, resolve / mu)
+    times = log_times(B, N, 1.0) * t_end[:, None]
+    return {"spec": {"kind": "vdp", "n": 2, "hidden": (0, 0), "per_series": True},
+            "y0": y0, "times": times, "params": mu.reshape(B, 1).copy(), "lengths": None}
+
+
+def xavier_mlp(g, n, hidden):
+    """Flat MLP parameters W1 b1 W2 b2 W3 b3 (W row-major out x in): Xavier-uniform
+    weights U(-a, a), a = sqrt(6 / (fan_in + fan_out)); zero biases."""
+    sizes = [n, hidden[0], hidden[1], n]
+    parts = []
+    for fan_in, fan_out in zip(sizes[:-1], sizes[1:]):
+        a = np.sqrt(6.0 / (fan_in + fan_out))
+        parts.append(g.uniform(-a, a, (fan_out, fan_in)).reshape(-1))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts)
+
+
+def mlp_ode(seed=SEED_MLP, B=64, N=2000, n=16, hidden=(64, 64), act="tanh", t_end=10.0,
+            lengths_range=None):
+    """Neural ODE dy/dt = MLP(y).  y0 ~ N(0, 1).  'params' is the trained model,
+    'target_params' a second seeded network of the same architecture whose
+    trajectory from the same y0 serves as the regression target."""
+    g = _rng(seed)
+    params = xavier_mlp(g, n, hidden)
+    target = xavier_mlp(g, n, hidden)
+    y0 = g.standard_normal((B, n))
+    lengths = None
+    if lengths_range is not None:
+        lengths = g.integers(lengths_range[0], lengths_range[1] + 1, B).astype(np.int32)
+    kind = "mlp_tanh" if act == "tanh" else "mlp_silu"
+    return {"spec": {"kind": kind, "n": n, "hidden": tuple(hidden), "per_series": False},
+            "y0": y0, "times": uniform_times(B, N, t_end), "params": params,
+            "target_params": target, "lengths": lengths}
+
+
+def mlp_large(seed=SEED_MLP_LARGE, B=512, N=20000, n=32, hidden=(128, 128), t_end=10.0,
+              lengths_range=(2000, 20000)):
+    """n = 32 SiLU neural ODE, per-series random lengths padded into one launch."""
+    return mlp_ode(seed=seed, B=B, N=N, n=n, hidden=hidden, act="silu", t_end=t_end,
+                   lengths_range=lengths_range)
+
+
+def random_grad_out(seed, B, N, n, scale=1.0):
+    """A seeded dL/dy for every output [B][N+1][n] (adjoint parity inputs)."""
+    return scale * _rng(seed).standard_normal((B, N + 1, n))
+
+
+def random_times(seed, B, N, t_end=1.0, spread=0.5):
+    """Per-series non-uniform grids: positive steps drawn U(1-spread, 1+spread),
+    rescaled per series to end at t_end times a per-series factor in [0.5, 1.5]."""
+    g = _rng(seed)
+    steps = g.uniform(1.0 - spread, 1.0 + spread, (B, N))
+    ends = t_end * g.uniform(0.5, 1.5, B)
+    steps = steps / steps.sum(axis=1, keepdims=True) * ends[:, None]
+    t = np.zeros((B, N + 1))
+    t[:, 1:] = np.cumsum(steps, axis=1)
+    return t
