@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput of chunked backward-Euler forward + adjoint, in series*steps/s.
+
+Workload (default): stiff van der Pol, n = 2, 128 series x 10,000 log-spaced
+steps per series, Newton tolerance 1e-10; chunk 1000 with FP32 blocks and
+cyclic reduction plus FP64 residuals.  One step = tvi_integrate + tvi_adjoint
+over the whole batch.  The same library with chunk = 1 and FP64 blocks (the
+sequential scheme, same Newton tolerance, same launch strategy) is timed in
+the same run for the chunked/sequential ratio.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle on
+the same workload instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "series*steps/s fwd+adjoint vs chunk=1 sequential on GB300, same Newton tol"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 rate (no measured FP64 peak is provided)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chunk", type=int, default=1000)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--rpt", type=int, default=0, help="steps per thread (0 = library default)")
+    ap.add_argument("--B", type=int, default=128)
+    ap.add_argument("--N", type=int, default=10000)
+    ap.add_argument("--baseline-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-chunk1", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload_config(args):
+    return {"workload": f"van der Pol n=2, {args.B} series x {args.N} log-spaced steps, "
+                        f"mu log-uniform [10,1000], Newton tol {args.tol:g}",
+            "B": args.B, "N": args.N, "chunk": args.chunk,
+            "blocks": args.precision, "residual": "fp64", "tol_abs": args.tol}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def time_oracle(w, g, tol, seconds, min_reps=1):
+    import oracle
+    m = oracle.Model.from_spec(w["spec"])
+    B, N = w["times"].shape[0], w["times"].shape[1] - 1
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        y, _, _ = oracle.forward(m, w["y0"], w["times"], w["params"], tol_abs=tol, max_iter=100)
+        oracle.adjoint(m, w["times"], w["params"], y, g)
+        reps += 1
+        el = time.perf_counter() - t0
+        if reps >= min_reps and el >= seconds:
+            break
+    return B * N * reps / el, reps, el, oracle.max_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workloads.vdp(B=args.B, N=args.N)
+    g = workloads.random_grad_out(2002, args.B, args.N, 2)
+    per_step = max(args.cpu_seconds / max(args.steps, 1), 0.0)
+    for _ in range(args.warmup):
+        time_oracle(w, g, args.tol, 0.0)
+    vals, t_total = [], 0.0
+    reps_total = 0
+    for _ in range(args.steps):
+        v, reps, el, cores = time_oracle(w, g, args.tol, per_step)
+        vals.append(v)
+        t_total += el
+        reps_total += reps
+    value = args.B * args.N * reps_total / t_total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "series*steps/s",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": "series*steps/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"whole workload, {reps_total} forward+adjoint passes"},
+            "e2e": {"value": value, "unit": "series*steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.samples, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append((time.perf_counter(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        sel = [p for (t, p) in self.samples if t0 <= t <= t1]
+        if not sel:  # region shorter than the sampling period: nearest samples
+            sel = [p for (t, p) in sorted(self.samples, key=lambda s: abs(s[0] - (t0 + t1) / 2))[:3]]
+        if not sel:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[0]) for p in sel if num(p[0]) is not None]
+        mx = [num(p[1]) for p in sel if num(p[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in sel for i in range(4) if p[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(sel)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2310_08649_gb300 import build as lib_build
+    lib_build.build()
+    import paper_2310_08649_gb300 as tvi
+
+    dev = torch.device("cuda", local)
+    # weak scaling: every rank integrates its own batch of the same shape
+    w = workloads.vdp(B=args.B, N=args.N, seed=workloads.SEED_VDP + 1000 * rank)
+    g = workloads.random_grad_out(2002 + rank, args.B, args.N, 2)
+    B, N = args.B, args.N
+
+    def d(a, dtype=torch.float64):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).to(dev)
+
+    y0, times, params, grad = d(w["y0"]), d(w["times"]), d(w["params"]), d(g)
+    model = tvi.Model.from_spec(w["spec"])
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def make(opts):
+        ws = tvi.make_workspace(model, opts, B, N, dev)
+        y = torch.empty((B, N + 1, 2), dtype=torch.float64, device=dev)
+        stats = torch.empty((B, 4), dtype=torch.int32, device=dev)
+        st = torch.empty((B,), dtype=torch.int32, device=dev)
+        dp = torch.empty_like(params)
+        dy0 = torch.empty_like(y0)
+        return ws, y, stats, st, dp, dy0
+
+    def timed_steps(opts, K, W, per_launch=True):
+        ws, y, stats, st, dp, dy0 = make(opts)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+
+        def step(e=None):
+            if e:
+                e[0].record(stream)
+            tvi.integrate(model, opts, y0, times, params, None, y, stats, st, ws, stream)
+            if e:
+                e[1].record(stream)
+            tvi.adjoint(model, opts, times, params, y, grad, None, dp, dy0, ws, stream)
+            if e:
+                e[2].record(stream)
+        for _ in range(W):
+            flush.fill_(1)
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(K):
+            flush.fill_(k & 0xff)  # L2 flush between timed steps (outside the events)
+            step(ev[k])
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        fwd = [a.elapsed_time(b) for a, b, _ in ev]
+        adj = [b.elapsed_time(c) for _, b, c in ev]
+        assert int(st.max().item()) == 0, "a series failed to converge"
+        return {"fwd_ms": fwd, "adj_ms": adj, "total_ms": float(np.sum(fwd) + np.sum(adj)),
+                "stats": stats.cpu().numpy(), "t0": t0, "t1": t1}
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    opts = tvi.Options(chunk=args.chunk, tol_abs=args.tol, precision=args.precision,
+                       rows_per_thread=args.rpt, sync_status=False)
+    res = timed_steps(opts, args.steps, args.warmup)
+    total_ms = torch.tensor([res["total_ms"]], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(total_ms, op=dist.ReduceOp.MAX)
+    total_ms = float(total_ms.item())
+    units = B * N * world * args.steps
+    value = units / (total_ms / 1e3)
+
+    # end-to-end through the public API: pinned host inputs in, gradients out
+    h = {k: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64).pin_memory()
+         for k, v in (("y0", w["y0"]), ("times", w["times"]), ("params", w["params"]),
+                      ("grad", g))}
+    ws, y, stats, st, dp, dy0 = make(opts)
+    dev_in = {k: torch.empty_like(v, device=dev) for k, v in h.items()}
+    h_dp = torch.empty(dp.shape, dtype=torch.float64).pin_memory()
+    h_dy0 = torch.empty(dy0.shape, dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * 8 for v in h.values())
+    d2h = (dp.numel() + dy0.numel()) * 8
+
+    def e2e_step():
+        for k in h:
+            dev_in[k].copy_(h[k], non_blocking=True)
+        tvi.integrate(model, opts, dev_in["y0"], dev_in["times"], dev_in["params"], None, y,
+                      stats, st, ws, stream)
+        tvi.adjoint(model, opts, dev_in["times"], dev_in["params"], y, dev_in["grad"], None, dp,
+                    dy0, ws, stream)
+        h_dp.copy_(dp, non_blocking=True)
+        h_dy0.copy_(dy0, non_blocking=True)
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    K2 = max(1, min(args.steps, 50))
+    e_ms = 0.0
+    for k in range(K2):
+        flush.fill_(k & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e_ms += a.elapsed_time(b)
+    e2e_value = B * N * K2 / (e_ms / 1e3)
+
+    # chunk = 1 sequential FP64 scheme: same library, tolerance and launch strategy
+    chunk1 = None
+    if not args.no_chunk1:
+        o1 = tvi.Options(chunk=1, tol_abs=args.tol, precision="fp64", sync_status=False)
+        r1 = timed_steps(o1, args.baseline_steps, 1)
+        v1 = B * N * args.baseline_steps / (r1["total_ms"] / 1e3)
+        chunk1 = {"value": v1, "ms_per_step": r1["total_ms"] / args.baseline_steps,
+                  "fwd_ms": float(np.mean(r1["fwd_ms"])), "adj_ms": float(np.mean(r1["adj_ms"])),
+                  "chunk": 1, "blocks": "fp64", "ratio": value / v1}
+    clocks.stop()
+    clk = clocks.summary(res["t0"], res["t1"])
+
+    # roofline of the dominant kernel (FP64 pipe: the residual is the FP64 work)
+    fwd_ms, adj_ms = float(np.mean(res["fwd_ms"])), float(np.mean(res["adj_ms"]))
+    stats_np = res["stats"]
+    upd = stats_np[:, 0].astype(np.float64)
+    nchk = stats_np[:, 1].astype(np.float64)
+    # per series: (updates + chunks) residual passes x (N/chunks) steps x 13 FP64 flops,
+    # plus updates x (N/chunks) steps x 2 FP64 flops (dy -= d)
+    steps_per_chunk = N / np.maximum(nchk, 1)
+    fwd_flops = float(np.sum(((upd + nchk) * 13.0 + upd * 2.0) * steps_per_chunk))
+    refine = opts.adjoint_refine if args.precision != "fp64" else 0
+    adj_flops = float(B * N * (refine * 24.0 + 6.0))
+    if fwd_ms >= adj_ms:
+        name, flops, ms = "forward_small_kernel<vdp,fp32>", fwd_flops, fwd_ms
+    else:
+        name, flops, ms = "adjoint_small_kernel<vdp,fp32>", adj_flops, adj_ms
+    achieved = flops / (ms / 1e3) / 1e12
+    roofline = {"kernel": name, "bound": "alu", "pipe": "fp64", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64 (recipe table)",
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "fwd_ms": fwd_ms, "adj_ms": adj_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, reps, el, cores = time_oracle(w, g, args.tol, args.cpu_seconds)
+        cpu = {"value": v, "unit": "series*steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"whole workload ({B}x{N}), {reps} forward+adjoint passes, {el:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "series*steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic", "config": dict(workload_config(args),
+                                                     l2="flushed between timed steps (256 MB write)",
+                                                     parallelism=f"series replicas x{world}"),
+                "newton_updates_per_chunk": float(upd.sum() / max(nchk.sum(), 1)),
+                "newton_stats": {"updates_per_series_mean": float(upd.mean()),
+                                 "updates_per_series_max": int(upd.max()),
+                                 "chunks_per_series_max": int(nchk.max()),
+                                 "retries_total": int(stats_np[:, 2].sum()),
+                                 "retries_max": int(stats_np[:, 2].max()),
+                                 "max_updates_one_chunk": int(stats_np[:, 3].max())},
+                "chunk1_fp64": chunk1, "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": "series*steps/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": 2 * args.steps, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,157 @@
+/*
+ * tvi.h -- C ABI of the time-vectorized implicit integrator (sm_103a).
+ *
+ * Batched backward-Euler integration of dy/dt = h(y, t; p) over n_batch
+ * independent series (paper Sec. 2.1, Eqs. 1-4), vectorized over a chunk of
+ * sequential time steps (Sec. 2.3): each Newton iteration assembles the
+ * residual of Eq. batched-backward-euler and the block lower-bidiagonal Jacobian
+ * (diagonal I - dt_k j_k, sub-diagonal -I; Eq. batched-update) for every
+ * (series, step) pair of the chunk and solves it by parallel cyclic reduction
+ * (Sec. 3.2, Alg. 3).  The adjoint (App. A.1-A.2) solves the transposed,
+ * reversed block-bidiagonal system chunk by chunk and forms dL/dparams.
+ *
+ * Conventions shared by every entry point:
+ *   - All array pointers are DEVICE pointers unless stated otherwise, row-major
+ *     and contiguous, FP64 unless stated otherwise.  The caller owns every
+ *     buffer; the library allocates no device memory and keeps no pointer after
+ *     a call returns.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
+ *     enqueued on it.  A call synchronises `stream` only when it must read a
+ *     result back to form its return code (see tvi_options.sync_status).
+ *   - Errors are returned, never raised: no call aborts, traps or prints.  The
+ *     text of the last error of the calling host thread is tvi_last_error().
+ *   - rhs/jac are chosen by tvi_model.kind; callers do not pass functions.
+ */
+#ifndef TVI_H
+#define TVI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TVI_OK = 0,
+  TVI_EINVAL = -1,        /* bad argument: sizes, NULL pointer, unsupported combination */
+  TVI_EWORKSPACE = -2,    /* workspace NULL or smaller than tvi_workspace_bytes() */
+  TVI_ECUDA = -3,         /* a CUDA runtime call failed (text in tvi_last_error) */
+  TVI_ENOTCONV = -4,      /* some series hit the Newton iteration limit on a one-step chunk */
+  TVI_ENONFINITE = -5,    /* some series produced a NaN/Inf residual on a one-step chunk */
+  TVI_EUNSUPPORTED = -7   /* model/precision/size combination not built */
+} tvi_status;
+
+/* Model right-hand sides h(y, t; p) (autonomous: t is accepted, not used).
+ *   TVI_MODEL_LINEAR    h = A y; p = A [n][n] (row-major).  n in {2, 4}.
+ *   TVI_MODEL_VDP       van der Pol: h = [y2, mu (1 - y1^2) y2 - y1]; p = [mu].  n = 2.
+ *   TVI_MODEL_MLP_TANH  h = tanh(W3 tanh(W2 tanh(W1 y + b1) + b2) + b3)  (the neural
+ *                       ODE of Sec. 5.1.1 without forcing input).
+ *   TVI_MODEL_MLP_SILU  h = W3 silu(W2 silu(W1 y + b1) + b2) + b3.
+ * MLP parameters are one flat FP64 vector W1[h1][n] b1[h1] W2[h2][h1] b2[h2]
+ * W3[n][h2] b3[n] (W row-major, out x in). */
+typedef enum {
+  TVI_MODEL_LINEAR = 0,
+  TVI_MODEL_VDP = 1,
+  TVI_MODEL_MLP_TANH = 2,
+  TVI_MODEL_MLP_SILU = 3
+} tvi_model_kind;
+
+/* Arithmetic of the block Jacobian, its inverse and the cyclic reduction.
+ * The Newton residual, its norm, the Newton update and every output stay in
+ * FP64 in all modes, so Newton acts as iterative refinement and converges to
+ * the FP64 solution of the discrete equations. */
+typedef enum {
+  TVI_PREC_FP64 = 0,
+  TVI_PREC_FP32 = 1,
+  TVI_PREC_BF16 = 2       /* BF16 block products, FP32 accumulation (n >= 16) */
+} tvi_precision;
+
+typedef struct {
+  int kind;        /* tvi_model_kind */
+  int n;           /* state size */
+  int hidden1;     /* MLP hidden widths (0 otherwise) */
+  int hidden2;
+  int per_series;  /* 1: params [B][P] (one vector per series); 0: one shared [P] */
+} tvi_model;
+
+typedef struct {
+  int chunk;          /* steps solved together (n_chunk, Sec. 2.3); >= 1 */
+  double tol_abs;     /* Newton stops for a series when ||R||_inf <= tol_abs ... */
+  double tol_rel;     /* ... or ||R||_inf <= tol_rel ||R_0||_inf (norm over the whole chunk) */
+  int max_iter;       /* Newton update limit per chunk attempt */
+  int precision;      /* tvi_precision */
+  int retry_halving;  /* 1: a chunk whose Newton fails (limit, non-finite, or residual
+                         still > 10x its start after 4 updates) is re-solved from the same
+                         start with half the steps, recursively down to one step; after
+                         each success the chunk doubles back up to `chunk`.  The equations
+                         solved are the same, so the result is the same. */
+  int adjoint_refine; /* FP64-residual refinement sweeps of each adjoint chunk solve
+                         (used when precision != FP64) */
+  int rows_per_thread;/* solver tiling: steps held by one thread (0 = automatic) */
+  int sync_status;    /* 1: synchronise `stream` and fold per-series status into the
+                         return code; 0: return TVI_OK after enqueueing (status only
+                         in the series_status array) */
+} tvi_options;
+
+/* Fill *opt with defaults: chunk 1, tol_abs 1e-8, tol_rel 0, max_iter 50, FP64,
+ * retry_halving 1, adjoint_refine 2, rows_per_thread 0, sync_status 1. */
+void tvi_default_options(tvi_options* opt);
+
+/* Number of parameters P of one parameter vector, or -1 for a bad model. */
+int tvi_param_count(const tvi_model* model);
+
+/* Device workspace (bytes) that tvi_integrate / tvi_adjoint need for B series
+ * of N steps.  The caller allocates it (alignment 256 B) and may reuse it for
+ * any later call with the same or smaller sizes. */
+size_t tvi_workspace_bytes(const tvi_model* model, const tvi_options* opt, int B, int N);
+
+/*
+ * Forward integration, chunked backward Euler with Newton (Alg. 1).
+ *   B, N        series and steps; times has N+1 entries per series.
+ *   y0          [B][n]       initial states.
+ *   times       [B][N+1]     per-series time points; dt_k = t_k - t_{k-1} (Sec. 2.2).
+ *   lengths     [B] int32 or NULL.  Steps k > lengths[b] are padding: dt_k = 0, so
+ *               y_k = y_{k-1} exactly.
+ *   params      [B][P] or [P] (tvi_model.per_series).
+ *   y_out       [B][N+1][n]  trajectory; y_out[b][0] = y0[b] (like scipy odeint).
+ *   stats       [B][4] int32 or NULL: total Newton updates, chunks solved,
+ *               chunk retries (halvings), largest Newton count of one chunk.
+ *   series_status [B] int32 or NULL: 0 ok, 1 Newton limit, 2 non-finite residual.
+ *   workspace   >= tvi_workspace_bytes(model, opt, B, N) bytes of device memory.
+ * Newton starts every chunk from dy = 0 (Sec. 2.3) and stops per series (Alg. 1,
+ * converged series are frozen).  A failed chunk is retried by halving when
+ * opt->retry_halving; otherwise, or on a one-step chunk, the series' status is
+ * set and its integration continues from the unconverged iterate.
+ * Returns TVI_OK, an argument error, or (sync_status = 1) TVI_ENOTCONV /
+ * TVI_ENONFINITE if any series failed.
+ */
+tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, int N,
+                         const double* y0, const double* times, const int* lengths,
+                         const double* params, double* y_out, int* stats, int* series_status,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Discrete adjoint of tvi_integrate's equations (App. A.1, chunked per App. A.2).
+ *   y           [B][N+1][n]  the trajectory tvi_integrate produced (checkpoint: the
+ *               Jacobians are recomputed from it, nothing else is kept).
+ *   grad_out    [B][N+1][n]  dL/dy_k for every output, including k = 0.
+ *   dparams     [B][P] or [P] output: dL/dp = sum_k dt_k (dh/dp(y_k))^T a_k, where
+ *               a solves (I - dt_k j(y_k))^T a_k = a_{k+1} + dL/dy_k, a_{N+1} = 0.
+ *   dy0         [B][n] output or NULL: dL/dy0 = a_1 + dL/dy_0.
+ * The adjoint chunk size is opt->chunk.  Returns TVI_OK or an argument error.
+ */
+tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, int N,
+                       const double* times, const int* lengths, const double* params,
+                       const double* y, const double* grad_out, double* dparams, double* dy0,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* Text of the last error on the calling host thread ("" if none). */
+const char* tvi_last_error(void);
+
+/* Library build identification, e.g. "tvi sm_103a". */
+const char* tvi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

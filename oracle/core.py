@@ -61,6 +61,8 @@ def _load():
             lib.tvo_adjoint.argtypes = [mp, ctypes.c_int, ctypes.c_int, dp, ip, dp, dp, dp,
                                         ctypes.c_int, dp, dp]
             lib.tvo_adjoint.restype = ctypes.c_int
+            lib.tvo_step_matrices.argtypes = [mp, ctypes.c_int, ctypes.c_int, dp, ip, dp, dp, dp]
+            lib.tvo_step_matrices.restype = ctypes.c_int
             lib.tvo_max_threads.argtypes = []
             lib.tvo_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -141,3 +143,37 @@ def adjoint(model, times, params, y, grad_out, lengths=None, nthreads=0):
     if rc < 0:
         raise ValueError("tvo_adjoint rejected its arguments")
     return dparams, dy0
+
+
+def step_matrices(model, times, params, y, lengths=None):
+    """A_k = I - dt_k j(y_k) for every series and step: [B][N][n][n]."""
+    times, params, y = _f64(times), _f64(params), _f64(y)
+    B, Np1, n = y.shape
+    lens = None if lengths is None else np.ascontiguousarray(lengths, dtype=np.int32)
+    A = np.empty((B, Np1 - 1, n, n))
+    rc = _load().tvo_step_matrices(ctypes.byref(model.c()), B, Np1 - 1, _dptr(times), _iptr(lens),
+                                   _dptr(params), _dptr(y), _dptr(A))
+    if rc < 0:
+        raise ValueError("tvo_step_matrices rejected its arguments")
+    return A
+
+
+def forward_error_estimate(model, times, params, y, tol, lengths=None, trials=4, seed=0):
+    """Relative forward error (per series) that Newton stopping at residual tol
+    leaves in a backward-Euler trajectory: random per-step residuals r_k, uniform
+    in [-tol, tol]^n, propagated through the linearised recursion
+    d_k = A_k^-1 (d_{k-1} + r_k); the largest max_k |d_k| / max_k |y_k| over trials."""
+    A = step_matrices(model, times, params, y, lengths)
+    B, N, n, _ = A.shape
+    g = np.random.default_rng(seed)
+    scale = np.maximum(np.abs(y).max(axis=(1, 2)), 1e-300)
+    est = np.zeros(B)
+    for _ in range(trials):
+        d = np.zeros((B, n))
+        dmax = np.zeros(B)
+        r = g.uniform(-tol, tol, (B, N, n))
+        for k in range(N):
+            d = np.linalg.solve(A[:, k], (d + r[:, k])[..., None])[..., 0]
+            dmax = np.maximum(dmax, np.abs(d).max(axis=1))
+        est = np.maximum(est, dmax / scale)
+    return est

@@ -411,3 +411,25 @@ int tvo_adjoint(const tvo_model* m, int B, int N, const double* times, const int
   }
   return worst;
 }
+
+int tvo_step_matrices(const tvo_model* m, int B, int N, const double* times, const int* lengths,
+                      const double* params, const double* y, double* A) {
+  int P = tvo_param_count(m);
+  if (P < 0 || B < 0 || N < 0) return TVO_BADARG;
+  int n = m->n;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+  for (int b = 0; b < B; ++b) {
+    const double* p = m->per_series ? params + (size_t)b * P : params;
+    const double* tb = times + (size_t)b * (N + 1);
+    for (int k = 1; k <= N; ++k) {
+      double dt = step_dt(tb, lengths, b, k);
+      double* Ak = A + ((size_t)b * N + (k - 1)) * n * n;
+      tvo_jac(m, p, y + ((size_t)b * (N + 1) + k) * n, tb[k], Ak);
+      for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) Ak[r * n + c] = (r == c ? 1.0 : 0.0) - dt * Ak[r * n + c];
+    }
+  }
+  return TVO_OK;
+}

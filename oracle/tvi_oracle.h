@@ -80,6 +80,13 @@ int tvo_adjoint(const tvo_model* m, int B, int N, const double* times, const int
                 const double* params, const double* y, const double* grad_out, int nthreads,
                 double* dparams, double* dy0);
 
+/* Step matrices A_k = I - dt_k j(y_k) of every series and step k = 1..N at a
+ * given trajectory y, into A [B][N][n][n] (dt_k = 0 on padded steps).  Used to
+ * propagate perturbations through the linearised backward-Euler recursion
+ * (forward-error estimates in the tests). */
+int tvo_step_matrices(const tvo_model* m, int B, int N, const double* times, const int* lengths,
+                      const double* params, const double* y, double* A);
+
 /* Threads OpenMP will use for nthreads <= 0. */
 int tvo_max_threads(void);
 

@@ -1,0 +1,219 @@
+// tvi_api.cu -- the C ABI declared in include/tvi.h: argument checks, workspace
+// layout, kernel dispatch and status read-back.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "tvi.h"
+#include "tvi_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+tvi_status fail(tvi_status code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+tvi_status fail(tvi_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+tvi_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(TVI_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+// Workspace layout (all offsets 256-byte aligned):
+//   [0]        int worst status word
+//   [256]      double partials [B][P]  (adjoint, shared parameters)
+struct Layout {
+  size_t worst, partials, total;
+};
+
+Layout layout(int B, int P) {
+  Layout l;
+  l.worst = 0;
+  l.partials = 256;
+  l.total = l.partials + align256(static_cast<size_t>(B) * static_cast<size_t>(P) * sizeof(double));
+  return l;
+}
+
+tvi_status check_model(const tvi_model* m) {
+  if (!m) return fail(TVI_EINVAL, "model is NULL");
+  if (tvi_param_count(m) < 0)
+    return fail(TVI_EINVAL, "bad model (kind %d, n %d, hidden %d/%d)", m->kind, m->n, m->hidden1,
+                m->hidden2);
+  if (!tvi::small_supported(m->kind, m->n))
+    return fail(TVI_EUNSUPPORTED, "model kind %d with n = %d is not built", m->kind, m->n);
+  return TVI_OK;
+}
+
+tvi_status check_opt(const tvi_options* o) {
+  if (!o) return fail(TVI_EINVAL, "options are NULL");
+  if (o->chunk < 1) return fail(TVI_EINVAL, "chunk must be >= 1 (got %d)", o->chunk);
+  if (o->max_iter < 0) return fail(TVI_EINVAL, "max_iter must be >= 0");
+  if (!(o->tol_abs >= 0.0) || !(o->tol_rel >= 0.0))
+    return fail(TVI_EINVAL, "tolerances must be >= 0");
+  if (o->precision != tvi::kPrecFp64 && o->precision != tvi::kPrecFp32)
+    return fail(TVI_EUNSUPPORTED, "precision %d is not built for small state sizes", o->precision);
+  if (o->adjoint_refine < 0 || o->adjoint_refine > 16)
+    return fail(TVI_EINVAL, "adjoint_refine must be in [0, 16]");
+  return TVI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tvi_default_options(tvi_options* opt) {
+  if (!opt) return;
+  opt->chunk = 1;
+  opt->tol_abs = 1e-8;
+  opt->tol_rel = 0.0;
+  opt->max_iter = 50;
+  opt->precision = TVI_PREC_FP64;
+  opt->retry_halving = 1;
+  opt->adjoint_refine = 2;
+  opt->rows_per_thread = 0;
+  opt->sync_status = 1;
+}
+
+int tvi_param_count(const tvi_model* m) {
+  if (!m || m->n <= 0) return -1;
+  switch (m->kind) {
+    case TVI_MODEL_LINEAR: return m->n * m->n;
+    case TVI_MODEL_VDP: return m->n == 2 ? 1 : -1;
+    case TVI_MODEL_MLP_TANH:
+    case TVI_MODEL_MLP_SILU:
+      if (m->hidden1 <= 0 || m->hidden2 <= 0) return -1;
+      return m->hidden1 * m->n + m->hidden1 + m->hidden2 * m->hidden1 + m->hidden2 +
+             m->n * m->hidden2 + m->n;
+    default: return -1;
+  }
+}
+
+size_t tvi_workspace_bytes(const tvi_model* model, const tvi_options* opt, int B, int N) {
+  (void)opt;
+  (void)N;
+  int P = tvi_param_count(model);
+  if (P < 0 || B < 0) return 0;
+  return layout(B, P).total;
+}
+
+tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, int N,
+                         const double* y0, const double* times, const int* lengths,
+                         const double* params, double* y_out, int* stats, int* series_status,
+                         void* workspace, size_t workspace_bytes, void* stream) {
+  g_last_error.clear();
+  tvi_status r = check_model(model);
+  if (r != TVI_OK) return r;
+  if ((r = check_opt(opt)) != TVI_OK) return r;
+  if (B < 0 || N < 0) return fail(TVI_EINVAL, "B and N must be >= 0 (got %d, %d)", B, N);
+  if (B == 0) return TVI_OK;
+  if (!y0 || !times || !params || !y_out)
+    return fail(TVI_EINVAL, "y0, times, params and y_out must not be NULL");
+  const int P = tvi_param_count(model);
+  const Layout l = layout(B, P);
+  if (!workspace || workspace_bytes < l.total)
+    return fail(TVI_EWORKSPACE, "workspace of %zu bytes needed (got %zu)", l.total,
+                workspace ? workspace_bytes : static_cast<size_t>(0));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+
+  tvi::FwdArgs a;
+  a.B = B;
+  a.N = N;
+  a.chunk = opt->chunk < tvi::kSmallMaxChunk ? opt->chunk : tvi::kSmallMaxChunk;
+  a.max_iter = opt->max_iter;
+  a.retry_halving = opt->retry_halving ? 1 : 0;
+  a.per_series = model->per_series ? 1 : 0;
+  a.tol_abs = opt->tol_abs;
+  a.tol_rel = opt->tol_rel;
+  a.y0 = y0;
+  a.times = times;
+  a.lengths = lengths;
+  a.params = params;
+  a.y_out = y_out;
+  a.stats = stats;
+  a.series_status = series_status;
+  a.worst = reinterpret_cast<int*>(ws + l.worst);
+
+  cudaError_t e = cudaMemsetAsync(a.worst, 0, sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "tvi_integrate: clearing the status word");
+  int rpt, threads;
+  tvi::small_launch_shape(a.chunk, opt->rows_per_thread, &rpt, &threads);
+  e = tvi::small_forward(model->kind, model->n, opt->precision, rpt, threads, a, s);
+  if (e != cudaSuccess) return cuda_fail(e, "tvi_integrate: kernel launch");
+  if (!opt->sync_status) return TVI_OK;
+  int worst = 0;
+  e = cudaMemcpyAsync(&worst, a.worst, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "tvi_integrate: status read-back");
+  if (worst == 2) return fail(TVI_ENONFINITE, "a series produced a non-finite residual");
+  if (worst == 1) return fail(TVI_ENOTCONV, "a series hit the Newton iteration limit");
+  return TVI_OK;
+}
+
+tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, int N,
+                       const double* times, const int* lengths, const double* params,
+                       const double* y, const double* grad_out, double* dparams, double* dy0,
+                       void* workspace, size_t workspace_bytes, void* stream) {
+  g_last_error.clear();
+  tvi_status r = check_model(model);
+  if (r != TVI_OK) return r;
+  if ((r = check_opt(opt)) != TVI_OK) return r;
+  if (B < 0 || N < 0) return fail(TVI_EINVAL, "B and N must be >= 0 (got %d, %d)", B, N);
+  if (B == 0) return TVI_OK;
+  if (!times || !params || !y || !grad_out || !dparams)
+    return fail(TVI_EINVAL, "times, params, y, grad_out and dparams must not be NULL");
+  const int P = tvi_param_count(model);
+  const Layout l = layout(B, P);
+  if (!workspace || workspace_bytes < l.total)
+    return fail(TVI_EWORKSPACE, "workspace of %zu bytes needed (got %zu)", l.total,
+                workspace ? workspace_bytes : static_cast<size_t>(0));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+
+  tvi::AdjArgs a;
+  a.B = B;
+  a.N = N;
+  a.chunk = opt->chunk < tvi::kSmallMaxChunk ? opt->chunk : tvi::kSmallMaxChunk;
+  a.refine = opt->precision == tvi::kPrecFp64 ? 0 : opt->adjoint_refine;
+  a.per_series = model->per_series ? 1 : 0;
+  a.times = times;
+  a.lengths = lengths;
+  a.params = params;
+  a.y = y;
+  a.grad_out = grad_out;
+  a.dparams = dparams;
+  a.dy0 = dy0;
+  a.partials = reinterpret_cast<double*>(ws + l.partials);
+  if (N == 0) {
+    // no steps: dL/dp = 0 and dL/dy0 = grad_out[:, 0]
+    size_t dp_bytes = (a.per_series ? static_cast<size_t>(B) : 1u) * P * sizeof(double);
+    cudaError_t e = cudaMemsetAsync(dparams, 0, dp_bytes, s);
+    if (e == cudaSuccess && dy0)
+      e = cudaMemcpyAsync(dy0, grad_out, static_cast<size_t>(B) * model->n * sizeof(double),
+                          cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? TVI_OK : cuda_fail(e, "tvi_adjoint: empty integration");
+  }
+  int rpt, threads;
+  tvi::small_launch_shape(a.chunk, opt->rows_per_thread, &rpt, &threads);
+  cudaError_t e = tvi::small_adjoint(model->kind, model->n, opt->precision, rpt, threads, a, P, s);
+  if (e != cudaSuccess) return cuda_fail(e, "tvi_adjoint: kernel launch");
+  return TVI_OK;
+}
+
+const char* tvi_last_error(void) { return g_last_error.c_str(); }
+
+const char* tvi_version(void) { return "tvi sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,55 @@
+// tvi_internal.h -- argument blocks and launchers shared by the C-ABI layer and
+// the kernel translation units.  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace tvi {
+
+enum { kKindLinear = 0, kKindVdp = 1, kKindMlpTanh = 2, kKindMlpSilu = 3 };
+enum { kPrecFp64 = 0, kPrecFp32 = 1, kPrecBf16 = 2 };
+
+// Largest chunk the fused small-state kernels hold on chip; a larger requested
+// chunk is solved as chunks of this size (same equations, same result).
+constexpr int kSmallMaxChunk = 1024;
+
+// Thread bound of the fused kernels by steps per thread: more steps per thread
+// need more registers, so fewer threads (the block always holds 1024 steps).
+__host__ __device__ constexpr int small_max_threads(int rpt) {
+  return rpt == 1 ? 512 : 1024 / rpt;
+}
+
+struct FwdArgs {
+  int B, N, chunk, max_iter, retry_halving, per_series;
+  double tol_abs, tol_rel;
+  const double* y0;
+  const double* times;
+  const int* lengths;
+  const double* params;
+  double* y_out;
+  int* stats;          // [B][4] or null
+  int* series_status;  // [B] or null
+  int* worst;          // device word: max status over series
+};
+
+struct AdjArgs {
+  int B, N, chunk, refine, per_series;
+  const double* times;
+  const int* lengths;
+  const double* params;
+  const double* y;
+  const double* grad_out;
+  double* dparams;
+  double* dy0;       // [B][n] or null
+  double* partials;  // [B][P] per-series gradient partials (shared parameters)
+};
+
+bool small_supported(int kind, int n);
+void small_launch_shape(int chunk, int preferred, int* rpt, int* threads);
+cudaError_t small_forward(int kind, int n, int precision, int rpt, int threads, const FwdArgs& a,
+                          cudaStream_t s);
+cudaError_t small_adjoint(int kind, int n, int precision, int rpt, int threads, const AdjArgs& a,
+                          int P, cudaStream_t s);
+
+}  // namespace tvi

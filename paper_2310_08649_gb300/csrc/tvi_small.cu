@@ -1,0 +1,499 @@
+// tvi_small.cu -- fused per-series kernels for small state sizes (n <= 4).
+//
+// One thread block owns one series for the whole integration: it marches
+// through the chunks (Alg. 1 outer loop), runs the Newton loop of each chunk
+// on-chip (residual assembly, convergence norm, block inverses, cyclic
+// reduction, update), writes the converged chunk to the trajectory and
+// carries y_{i+c} to the next chunk.  Series are independent (Sec. 2.1), so
+// blocks never wait on one another and a converged series stops iterating
+// while others continue (the per-series freezing reading of Alg. 1).
+//
+// Thread t holds the RPT consecutive steps t*RPT .. t*RPT+RPT-1 of the chunk.
+// Per Newton iteration:
+//   residual   R_j = dy_j - dy_{j-1} - dt_j h(y_i + dy_j)     FP64 (Eq. batched-backward-euler)
+//   norm       ||R||_inf over the chunk, block max             FP64 bits, integer pipe
+//   blocks     A_j = I - dt_j j(y_i + dy_j), M_j = A_j^-1, v_j = M_j R_j      in T
+//   reduction  d_j = M_j d_{j-1} + v_j  by serial runs + cyclic reduction  in T
+//   update     dy_j -= d_j                                   FP64
+// T = double (FP64 mode) or float (mixed mode: the FP64 residual makes Newton
+// an iterative refinement that converges to the FP64 solution).
+#include "tvi_device.cuh"
+#include "tvi_internal.h"
+#include "tvi_models.cuh"
+
+namespace tvi {
+
+namespace {
+
+// Newton outcome of one chunk attempt.
+enum { kConv = 0, kMaxIter = 1, kNonFinite = 2, kDiverged = 3 };
+
+template <class Model, typename T, int RPT>
+__global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(FwdArgs a) {
+  constexpr int NS = Model::NS;
+  constexpr bool kMixed = sizeof(T) != sizeof(double);
+  __shared__ Aff<NS, T> s_wtot[32];
+  __shared__ double s_wlast[32][NS];
+  __shared__ unsigned long long s_red[32];
+  __shared__ double s_carry[NS];
+
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int N = a.N;
+  const double* tb = a.times + static_cast<size_t>(b) * (N + 1);
+  double* yb = a.y_out + static_cast<size_t>(b) * (N + 1) * NS;
+  const int len = a.lengths ? min(max(a.lengths[b], 0), N) : N;
+
+  Model mdl;
+  mdl.load(a.params, b, a.per_series);
+
+  double yi[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) yi[s] = a.y0[static_cast<size_t>(b) * NS + s];
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) yb[s] = yi[s];
+  }
+
+  int st = 0, tot_iters = 0, n_chunks = 0, retries = 0, max_it = 0, streak = 0;
+  int i = 0, c_cur = a.chunk;
+  while (i < N) {
+    const int L = min(c_cur, N - i);
+    // warps holding at least one step of this attempt; the rest skip all work
+    const int nwa = ((L + RPT - 1) / RPT + 31) / 32;
+    const bool wact = warp < nwa;
+    const bool can_halve = a.retry_halving && c_cur > 1;
+    // ---- per-thread rows of this chunk attempt ----
+    double dt[RPT], dy[RPT][NS];
+    T dtT[RPT], yiT[NS], dyT[RPT][NS];  // block-precision shadows (mixed mode)
+    bool act[RPT];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) yiT[s] = narrow<T>(yi[s]);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int j = tid * RPT + r;
+      const int k = i + 1 + j;
+      act[r] = j < L;
+      dt[r] = (act[r] && k <= len) ? (tb[k] - tb[k - 1]) : 0.0;
+      dtT[r] = narrow<T>(dt[r]);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        dy[r][s] = 0.0;  // Sec. 2.3 guess: dy = 0
+        dyT[r][s] = T(0);
+      }
+    }
+
+    double norm0 = 0.0;
+    int it = 0, outcome = kConv;
+    for (;;) {
+      // dy_{j-1} of the first own row: last row of the previous thread
+      double prev[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) prev[s] = __shfl_up_sync(kFull, dy[RPT - 1][s], 1);
+      if (wact && lane == 31) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) s_wlast[warp][s] = dy[RPT - 1][s];
+      }
+      __syncthreads();
+      if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) prev[s] = (warp > 0) ? s_wlast[warp - 1][s] : 0.0;
+      }
+      // ---- residual, FP64 ----
+      double R[RPT][NS];
+      unsigned long long mx = 0ull;
+      if (wact) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          double y[NS], h[NS];
+#pragma unroll
+          for (int s = 0; s < NS; ++s) y[s] = yi[s] + dy[r][s];
+          mdl.rhs(y, h);
+#pragma unroll
+          for (int s = 0; s < NS; ++s) {
+            const double pv = (r == 0) ? prev[s] : dy[r - 1][s];
+            R[r][s] = act[r] ? fma(-dt[r], h[s], dy[r][s] - pv) : 0.0;
+            mx = umax64(mx, abs_bits(R[r][s]));
+          }
+        }
+      }
+      const unsigned long long nb = block_max_u64(mx, s_red, lane, warp, nwarps, nwa);
+      const double nr = __longlong_as_double(static_cast<long long>(nb));
+      if (it == 0) norm0 = nr;
+      if (nb >= kNonFiniteBits) { outcome = kNonFinite; break; }
+      if (nr <= a.tol_abs || nr <= a.tol_rel * norm0) { outcome = kConv; break; }
+      if (it >= a.max_iter) { outcome = kMaxIter; break; }
+      // When a smaller chunk can still be tried, an attempt whose residual is
+      // still above 10x its starting value after 4 updates is abandoned early
+      // (a heuristic for speed only: the retry solves the same equations).
+      if (can_halve && it >= 4 && nr > 10.0 * norm0) { outcome = kDiverged; break; }
+
+      // ---- blocks, their inverses, and the cyclic-reduction solve ----
+      Aff<NS, T> f[RPT];
+      T d[RPT][NS];
+      if (wact) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          if (act[r]) {
+            T yt[NS], A[NS][NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+              if constexpr (kMixed) yt[s] = yiT[s] + dyT[r][s];
+              else yt[s] = yi[s] + dy[r][s];
+            }
+            mdl.step_matrix(yt, dtT[r], A);
+            block_inverse<NS, T>(A, f[r].M);
+            T Rt[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) Rt[q] = narrow<T>(R[r][q]);
+#pragma unroll
+            for (int p = 0; p < NS; ++p) {
+              T sacc = T(0);
+#pragma unroll
+              for (int q = 0; q < NS; ++q) sacc = fma(f[r].M[p][q], Rt[q], sacc);
+              f[r].v[p] = sacc;
+            }
+          } else {
+            aff_identity(f[r]);
+          }
+        }
+      }
+      solve_chain<NS, T, RPT>(f, d, s_wtot, lane, warp, nwa);
+      // ---- Newton update, FP64 accumulate ----
+      if (wact) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+          for (int s = 0; s < NS; ++s)
+            if (act[r]) {
+              dy[r][s] -= widen<T>(d[r][s]);
+              if constexpr (kMixed) dyT[r][s] -= d[r][s];
+            }
+      }
+      ++it;
+    }
+
+    if (outcome != kConv && can_halve) {
+      c_cur = (c_cur + 1) / 2;  // re-solve from the same chunk start with half the steps
+      ++retries;
+      streak = 0;
+      __syncthreads();  // s_wlast / s_red reuse
+      continue;
+    }
+    if (outcome == kNonFinite) st = 2;
+    else if (outcome != kConv && st == 0) st = 1;
+    tot_iters += it;
+    ++n_chunks;
+    max_it = max(max_it, it);
+
+    // ---- write the chunk's trajectory and carry y_{i+L} ----
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int j = tid * RPT + r;
+      if (act[r]) {
+        double* out = yb + static_cast<size_t>(i + 1 + j) * NS;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) out[s] = yi[s] + dy[r][s];
+      }
+      if (j == L - 1) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) s_carry[s] = yi[s] + dy[r][s];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < NS; ++s) yi[s] = s_carry[s];
+    __syncthreads();
+    i += L;
+    // after two successes in a row the chunk grows back by doubling, up to
+    // the requested size (as in step-size control)
+    if (++streak >= 2) {
+      c_cur = min(a.chunk, 2 * c_cur);
+      streak = 0;
+    }
+  }
+
+  if (tid == 0) {
+    if (a.stats) {
+      int* o = a.stats + static_cast<size_t>(b) * 4;
+      o[0] = tot_iters;
+      o[1] = n_chunks;
+      o[2] = retries;
+      o[3] = max_it;
+    }
+    if (a.series_status) a.series_status[b] = st;
+    if (st) atomicMax(a.worst, st);
+  }
+}
+
+// Adjoint of one series, chunks in reverse (App. A.2).  Within a chunk of L
+// steps k = i+1..i+L the unknowns are taken in reverse order, q = i+L+1-k, so
+//     A_k^T a_k - a_{k+1} = g_k    becomes    x_q = A_k^-T x_{q-1} + A_k^-T g_k,
+// x_{-1} = a_{i+L+1} (the carry from the later chunk, folded into row 0) -- the
+// same chain as the forward pass with transposed blocks.  In mixed precision
+// the chain is solved in T and refined with FP64 residuals
+//     r_k = g_k + a_{k+1} - A_k^T a_k   (A_k in FP64).
+template <class Model, typename T, int RPT>
+__global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(AdjArgs a) {
+  constexpr int NS = Model::NS;
+  constexpr int NP = Model::NP;
+  __shared__ Aff<NS, T> s_wtot[32];
+  __shared__ double s_wlast[32][NS];
+  __shared__ double s_carry[NS];
+  __shared__ double s_acc[32][NP];
+
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int N = a.N, c = a.chunk;
+  const double* tb = a.times + static_cast<size_t>(b) * (N + 1);
+  const double* yb = a.y + static_cast<size_t>(b) * (N + 1) * NS;
+  const double* gb = a.grad_out + static_cast<size_t>(b) * (N + 1) * NS;
+  const int len = a.lengths ? min(max(a.lengths[b], 0), N) : N;
+
+  Model mdl;
+  mdl.load(a.params, b, a.per_series);
+
+  double carry[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) carry[s] = 0.0;  // a_{N+1} = 0
+  double acc[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) acc[p] = 0.0;
+
+  const int n_chunks = (N + c - 1) / c;
+  for (int ci = n_chunks - 1; ci >= 0; --ci) {
+    const int i = ci * c;
+    const int L = min(c, N - i);
+    const int nwa = ((L + RPT - 1) / RPT + 31) / 32;
+    double yk[RPT][NS], gk[RPT][NS], dt[RPT], av[RPT][NS];
+    bool act[RPT];
+    Aff<NS, T> f[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int q = tid * RPT + r;
+      act[r] = q < L;
+      const int k = i + L - q;
+      dt[r] = (act[r] && k <= len) ? (tb[k] - tb[k - 1]) : 0.0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        yk[r][s] = act[r] ? yb[static_cast<size_t>(k) * NS + s] : 0.0;
+        gk[r][s] = act[r] ? gb[static_cast<size_t>(k) * NS + s] : 0.0;
+      }
+      if (act[r]) {
+        T yt[NS], A[NS][NS], Ai[NS][NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) yt[s] = narrow<T>(yk[r][s]);
+        mdl.step_matrix(yt, narrow<T>(dt[r]), A);
+        block_inverse<NS, T>(A, Ai);
+#pragma unroll
+        for (int p = 0; p < NS; ++p)
+#pragma unroll
+          for (int q2 = 0; q2 < NS; ++q2) f[r].M[p][q2] = Ai[q2][p];  // A^-T
+        double rhs[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) rhs[s] = gk[r][s] + ((q == 0) ? carry[s] : 0.0);
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+          T sacc = T(0);
+#pragma unroll
+          for (int q2 = 0; q2 < NS; ++q2) sacc = fma(f[r].M[p][q2], narrow<T>(rhs[q2]), sacc);
+          f[r].v[p] = sacc;
+        }
+      } else {
+        aff_identity(f[r]);
+      }
+    }
+    {
+      T x[RPT][NS];
+      solve_chain<NS, T, RPT>(f, x, s_wtot, lane, warp, nwa);
+#pragma unroll
+      for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) av[r][s] = act[r] ? widen<T>(x[r][s]) : 0.0;
+    }
+    // ---- FP64-residual refinement (mixed precision) ----
+    for (int ref = 0; ref < a.refine; ++ref) {
+      double nxt[NS];  // a_{k+1} of the first own row: last row of the previous thread
+#pragma unroll
+      for (int s = 0; s < NS; ++s) nxt[s] = __shfl_up_sync(kFull, av[RPT - 1][s], 1);
+      if (lane == 31) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) s_wlast[warp][s] = av[RPT - 1][s];
+      }
+      __syncthreads();
+      if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) nxt[s] = (warp > 0) ? s_wlast[warp - 1][s] : 0.0;
+      }
+      if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) nxt[s] = carry[s];
+      }
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        double A[NS][NS];
+        mdl.step_matrix(yk[r], dt[r], A);
+        double res[NS];
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+          double sacc = gk[r][p] + ((r == 0) ? nxt[p] : av[r - 1][p]);
+#pragma unroll
+          for (int q2 = 0; q2 < NS; ++q2) sacc = fma(-A[q2][p], av[r][q2], sacc);
+          res[p] = act[r] ? sacc : 0.0;
+        }
+#pragma unroll
+        for (int p = 0; p < NS; ++p) {
+          T sacc = T(0);
+#pragma unroll
+          for (int q2 = 0; q2 < NS; ++q2) sacc = fma(f[r].M[p][q2], narrow<T>(res[q2]), sacc);
+          f[r].v[p] = act[r] ? sacc : T(0);
+        }
+      }
+      T x[RPT][NS];
+      solve_chain<NS, T, RPT>(f, x, s_wtot, lane, warp, nwa);
+#pragma unroll
+      for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) av[r][s] += act[r] ? widen<T>(x[r][s]) : 0.0;
+      __syncthreads();  // s_wlast reuse
+    }
+    // ---- parameter VJP: acc += dt_k (dh/dp)^T a_k ----
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+      if (act[r] && dt[r] != 0.0) mdl.vjp_p(yk[r], av[r], dt[r], acc);
+    // ---- carry a_{i+1} (row L-1) to the earlier chunk ----
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (tid * RPT + r == L - 1) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) s_carry[s] = av[r][s];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < NS; ++s) carry[s] = s_carry[s];
+    __syncthreads();
+  }
+
+  // dL/dy0 = a_1 + dL/dy_0
+  if (tid == 0 && a.dy0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) a.dy0[static_cast<size_t>(b) * NS + s] = carry[s] + gb[s];
+  }
+  // deterministic block sum of the parameter gradient: warp tree, then warps in order
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    double v = acc[p];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (lane == 0) s_acc[warp][p] = v;
+  }
+  __syncthreads();
+  if (tid < NP) {
+    double v = 0.0;
+    for (int w = 0; w < nwarps; ++w) v += s_acc[w][tid];
+    double* dst = a.per_series ? a.dparams + static_cast<size_t>(b) * NP
+                               : a.partials + static_cast<size_t>(b) * NP;
+    dst[tid] = v;
+  }
+}
+
+template <class Model, typename T, int RPT>
+cudaError_t launch_fwd(const FwdArgs& a, int threads, cudaStream_t s) {
+  forward_small_kernel<Model, T, RPT><<<a.B, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class Model, typename T, int RPT>
+cudaError_t launch_adj(const AdjArgs& a, int threads, cudaStream_t s) {
+  adjoint_small_kernel<Model, T, RPT><<<a.B, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class Model, typename T>
+cudaError_t dispatch_fwd_rpt(const FwdArgs& a, int rpt, int threads, cudaStream_t s) {
+  switch (rpt) {
+    case 1: return launch_fwd<Model, T, 1>(a, threads, s);
+    case 2: return launch_fwd<Model, T, 2>(a, threads, s);
+    case 4: return launch_fwd<Model, T, 4>(a, threads, s);
+    case 8: return launch_fwd<Model, T, 8>(a, threads, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class Model, typename T>
+cudaError_t dispatch_adj_rpt(const AdjArgs& a, int rpt, int threads, cudaStream_t s) {
+  switch (rpt) {
+    case 1: return launch_adj<Model, T, 1>(a, threads, s);
+    case 2: return launch_adj<Model, T, 2>(a, threads, s);
+    case 4: return launch_adj<Model, T, 4>(a, threads, s);
+    case 8: return launch_adj<Model, T, 8>(a, threads, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+__global__ void sum_partials_kernel(const double* partials, int B, int P, double* out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  double s = 0.0;
+  for (int b = 0; b < B; ++b) s += partials[static_cast<size_t>(b) * P + p];  // series order
+  out[p] = s;
+}
+
+}  // namespace
+
+bool small_supported(int kind, int n) {
+  if (kind == kKindVdp) return n == 2;
+  if (kind == kKindLinear) return n == 2 || n == 4;
+  return false;
+}
+
+// Steps per thread: the smallest power of two whose block fits the kernel's
+// thread bound, raised to `preferred` when given; threads = ceil(c / rpt)
+// rounded up to a whole warp.  Every shape holds up to kSmallMaxChunk steps.
+void small_launch_shape(int chunk, int preferred, int* rpt, int* threads) {
+  int r = 1;
+  while (r < 8 && (chunk + r - 1) / r > small_max_threads(r)) r *= 2;
+  if (preferred == 1 || preferred == 2 || preferred == 4 || preferred == 8) r = r > preferred ? r : preferred;
+  int t = (chunk + r - 1) / r;
+  t = ((t + 31) / 32) * 32;
+  if (t > small_max_threads(r)) t = small_max_threads(r);
+  *rpt = r;
+  *threads = t;
+}
+
+cudaError_t small_forward(int kind, int n, int precision, int rpt, int threads, const FwdArgs& a,
+                          cudaStream_t s) {
+  const bool f64 = precision == kPrecFp64;
+  if (kind == kKindVdp)
+    return f64 ? dispatch_fwd_rpt<ModelVdp, double>(a, rpt, threads, s)
+               : dispatch_fwd_rpt<ModelVdp, float>(a, rpt, threads, s);
+  if (n == 2)
+    return f64 ? dispatch_fwd_rpt<ModelLinear<2>, double>(a, rpt, threads, s)
+               : dispatch_fwd_rpt<ModelLinear<2>, float>(a, rpt, threads, s);
+  return f64 ? dispatch_fwd_rpt<ModelLinear<4>, double>(a, rpt, threads, s)
+             : dispatch_fwd_rpt<ModelLinear<4>, float>(a, rpt, threads, s);
+}
+
+cudaError_t small_adjoint(int kind, int n, int precision, int rpt, int threads, const AdjArgs& a,
+                          int P, cudaStream_t s) {
+  const bool f64 = precision == kPrecFp64;
+  cudaError_t e;
+  if (kind == kKindVdp)
+    e = f64 ? dispatch_adj_rpt<ModelVdp, double>(a, rpt, threads, s)
+            : dispatch_adj_rpt<ModelVdp, float>(a, rpt, threads, s);
+  else if (n == 2)
+    e = f64 ? dispatch_adj_rpt<ModelLinear<2>, double>(a, rpt, threads, s)
+            : dispatch_adj_rpt<ModelLinear<2>, float>(a, rpt, threads, s);
+  else
+    e = f64 ? dispatch_adj_rpt<ModelLinear<4>, double>(a, rpt, threads, s)
+            : dispatch_adj_rpt<ModelLinear<4>, float>(a, rpt, threads, s);
+  if (e != cudaSuccess) return e;
+  if (!a.per_series) {
+    sum_partials_kernel<<<(P + 127) / 128, 128, 0, s>>>(a.partials, a.B, P, a.dparams);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace tvi

@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads, exports every symbol include/tvi.h declares,
+and its host-side logic (argument checks, sizes) works without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2310_08649_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "tvi.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tvi_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2310_08649_gb300 import _lib
+    declared = _declared_functions()
+    assert declared, "no declarations parsed"
+    assert set(declared) == set(_lib.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert lib.tvi_version().decode().startswith("tvi")
+
+
+def test_defaults_param_counts_and_workspace(lib):
+    from paper_2310_08649_gb300 import Model, Options, _lib
+    o = _lib.TviOptions()
+    lib.tvi_default_options(ctypes.byref(o))
+    assert (o.chunk, o.tol_abs, o.max_iter, o.precision, o.retry_halving, o.sync_status) == \
+        (1, 1e-8, 50, 0, 1, 1)
+    assert Model("vdp", 2, per_series=True).param_count() == 1
+    assert Model("linear", 4).param_count() == 16
+    assert Model("mlp_tanh", 16, (64, 64)).param_count() == 6288
+    assert Model("mlp_silu", 32, (128, 128)).param_count() == 24864
+    assert Model("vdp", 3).param_count() == -1
+    from paper_2310_08649_gb300 import workspace_bytes
+    ws = workspace_bytes(Model("linear", 4), Options(chunk=50), 16, 1000)
+    assert ws >= 256 + 16 * 16 * 8 and ws % 256 == 0
+
+
+def test_argument_errors_are_returned_without_touching_the_gpu(lib):
+    """Validation happens before any CUDA call, so these run on a CPU-only host."""
+    from paper_2310_08649_gb300 import Model, Options, _lib
+    m = Model("vdp", 2, per_series=True).c()
+    vp = ctypes.c_void_p(16)  # never dereferenced: every call below fails validation first
+
+    def call(model, opts, B=4, N=10, y0=vp, ws=vp, ws_bytes=1 << 20):
+        return lib.tvi_integrate(ctypes.byref(model), ctypes.byref(opts), B, N, y0, vp, None, vp,
+                                 vp, None, None, ws, ws_bytes, None)
+    assert call(m, Options(chunk=0).c()) == -1
+    assert call(m, Options(tol_abs=-1.0).c()) == -1
+    assert call(m, Options(precision="bf16").c()) == -7
+    assert call(Model("vdp", 3).c(), Options().c()) == -1
+    assert call(Model("linear", 3).c(), Options().c()) == -7
+    assert call(m, Options().c(), B=-1) == -1
+    assert call(m, Options().c(), y0=None) == -1
+    assert call(m, Options().c(), ws=None) == -2
+    assert call(m, Options().c(), ws_bytes=8) == -2
+    assert "workspace" in lib.tvi_last_error().decode()
+    assert call(m, Options().c(), B=0) == 0

@@ -60,15 +60,17 @@ def linear_stiff(seed=SEED_LINEAR, B=16, N=1000, n=4, t_end=1.0, lam_decades=(0.
             "lengths": None, "Q": Q, "lam": lam}
 
 
-def vdp(seed=SEED_VDP, B=128, N=10000, t_max=3.0, resolve=500.0, mu_decades=(1.0, 3.0)):
+def vdp(seed=SEED_VDP, B=128, N=10000, t_max=3.0, mu_dt_max=0.69, mu_decades=(1.0, 3.0)):
     """van der Pol, mu log-uniform in [10, 1000] per series, y0 uniform in [-2, 2]^2,
-    N log-spaced steps (6 decades).  Series b ends at t_end = min(t_max, resolve / mu_b):
-    the last (largest) log step is then at most 0.0014 t_end, so mu dt <= 0.69 at
-    every step and the grid resolves the fast time scale 1/mu everywhere.  Times
-    therefore differ per series."""
+    N log-spaced steps (6 decades).  The largest log step is about
+    t_end 6 ln(10) / (N - 1), so series b ends at
+        t_end = min(t_max, mu_dt_max (N - 1) / (6 ln(10) mu_b))
+    (= min(3, 500 / mu_b) at N = 10,000): mu dt <= mu_dt_max at every step and the
+    grid resolves the fast time scale 1/mu everywhere.  Times differ per series."""
     g = _rng(seed)
     mu = 10.0 ** g.uniform(mu_decades[0], mu_decades[1], B)
     y0 = g.uniform(-2.0, 2.0, (B, 2))
+    resolve = 500.0 * (N - 1) / 9999.0 * (mu_dt_max / 0.69)
     t_end = np.minimum(t_max, resolve / mu)
     times = log_times(B, N, 1.0) * t_end[:, None]
     return {"spec": {"kind": "vdp", "n": 2, "hidden": (0, 0), "per_series": True},
