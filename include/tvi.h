@@ -145,6 +145,33 @@ tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, in
                        const double* y, const double* grad_out, double* dparams, double* dy0,
                        void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * tvi_adjoint without a workspace, for callers that cannot allocate device
+ * memory (code where cudaMalloc is unavailable or forbidden: a host callback or
+ * real-time loop that must not enter the allocator, a plugin whose host owns
+ * every allocation, a process whose allocator has reserved the whole device).
+ * The paper has no counterpart: this is an interface convenience.
+ *
+ * Arguments and results are those of tvi_adjoint, minus the workspace.  The
+ * per-series partial gradients of shared parameters live instead in a fixed
+ * 4 MiB array inside the library's device image, which every GPU that loads the
+ * library holds until the process exits; B * P > 524,288 with shared
+ * parameters (per_series = 0) is rejected with TVI_EINVAL.  Per-series
+ * parameters need no scratch.  The call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current); make that
+ * first call before any stream capture.  All calls share the one array: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on it
+ * and must be serialised by the caller.  Every call overwrites the entries it
+ * reads, so nothing from an earlier call leaks into a later result.
+ */
+tvi_status tvi_adjoint_noalloc(const tvi_model* model, const tvi_options* opt, int B, int N,
+                               const double* times, const int* lengths, const double* params,
+                               const double* y, const double* grad_out, double* dparams,
+                               double* dy0, void* stream);
+
 /* Text of the last error on the calling host thread ("" if none). */
 const char* tvi_last_error(void);
 

@@ -19,7 +19,7 @@ TVI_ENOTCONV, TVI_ENONFINITE = -4, -5
 
 # every symbol include/tvi.h declares
 EXPORTS = ("tvi_default_options", "tvi_param_count", "tvi_workspace_bytes", "tvi_integrate",
-           "tvi_adjoint", "tvi_last_error", "tvi_version")
+           "tvi_adjoint", "tvi_adjoint_noalloc", "tvi_last_error", "tvi_version")
 
 
 class TviModel(ctypes.Structure):
@@ -68,6 +68,9 @@ def load():
             lib.tvi_adjoint.argtypes = [mp, op, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp,
                                         vp, vp, vp, sz, vp]
             lib.tvi_adjoint.restype = ctypes.c_int
+            lib.tvi_adjoint_noalloc.argtypes = [mp, op, ctypes.c_int, ctypes.c_int, vp, vp, vp,
+                                                vp, vp, vp, vp, vp]
+            lib.tvi_adjoint_noalloc.restype = ctypes.c_int
             lib.tvi_last_error.argtypes = []
             lib.tvi_last_error.restype = ctypes.c_char_p
             lib.tvi_version.argtypes = []

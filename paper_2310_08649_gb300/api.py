@@ -158,6 +158,33 @@ def adjoint(model, opts, times, params, y, grad_out, lengths=None, dparams=None,
     return dparams, dy0
 
 
+def adjoint_noalloc(model, opts, times, params, y, grad_out, lengths=None, dparams=None,
+                    dy0=None, stream=None):
+    """tvi_adjoint_noalloc: the adjoint without a workspace, for callers that cannot
+    allocate device memory (its scratch is a fixed array inside the library).
+    Pass dparams and dy0 to keep the call itself free of allocations.
+    Returns (dparams, dy0)."""
+    lib = _lib.load()
+    B, Np1, n = y.shape
+    N = Np1 - 1
+    dev = y.device
+    _check(times, "times", torch.float64, (B, N + 1))
+    _check(params, "params", torch.float64, _param_shape(model, B))
+    _check(y, "y", torch.float64, (B, N + 1, model.n))
+    _check(grad_out, "grad_out", torch.float64, (B, N + 1, model.n))
+    _check(lengths, "lengths", torch.int32, (B,), allow_none=True)
+    if dparams is None:
+        dparams = torch.empty(_param_shape(model, B), dtype=torch.float64, device=dev)
+    if dy0 is None:
+        dy0 = torch.empty((B, n), dtype=torch.float64, device=dev)
+    rc = lib.tvi_adjoint_noalloc(ctypes.byref(model.c()), ctypes.byref(opts.c()), B, N,
+                                 _ptr(times), _ptr(lengths), _ptr(params), _ptr(y),
+                                 _ptr(grad_out), _ptr(dparams), _ptr(dy0), _stream(stream))
+    if rc != 0:
+        raise _lib.TviError(rc, _lib.last_error())
+    return dparams, dy0
+
+
 class Integrate(torch.autograd.Function):
     """y = Integrate.apply(y0, params, times, model, opts, lengths): forward is
     tvi_integrate, backward is tvi_adjoint (gradients w.r.t. y0 and params)."""

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "tvi.h"
@@ -217,3 +218,114 @@ const char* tvi_last_error(void) { return g_last_error.c_str(); }
 const char* tvi_version(void) { return "tvi sm_103a"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free adjoint.
+//
+// Some callers cannot allocate device memory at all: code running where
+// cudaMalloc is forbidden or unavailable (inside a host callback or a
+// real-time loop that must not block on the allocator, a plugin whose host
+// application owns every allocation, a process running under an allocator
+// that has already reserved the whole device).  tvi_adjoint needs a caller-
+// provided workspace for the per-series partial gradients of shared
+// parameters; this variant keeps that scratch in a fixed array that lives in
+// the library's device image instead.
+//
+// The array is loaded with the library's GPU code, so every GPU that loads the
+// library holds its kNoAllocScratchBytes until the process exits.  Host code
+// cannot use the array's name as a device address (on the host it names a
+// shadow variable), so the device address is looked up with
+// cudaGetSymbolAddress once per device, with that device current, on the first
+// call made on it; make that first call before any stream capture.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchDoubles = static_cast<size_t>(1) << 19;  // 4 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+namespace {
+
+// Device address of g_noalloc_scratch on the current device (looked up once).
+tvi_status noalloc_scratch(double** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "tvi_adjoint_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(TVI_EUNSUPPORTED, "tvi_adjoint_noalloc: device %d beyond the supported %d", dev,
+                kNoAllocMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                       "tvi_adjoint_noalloc: cudaGetSymbolAddress of the scratch array");
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return TVI_OK;
+}
+
+}  // namespace
+
+extern "C" tvi_status tvi_adjoint_noalloc(const tvi_model* model, const tvi_options* opt, int B,
+                                          int N, const double* times, const int* lengths,
+                                          const double* params, const double* y,
+                                          const double* grad_out, double* dparams, double* dy0,
+                                          void* stream) {
+  g_last_error.clear();
+  tvi_status r = check_model(model);
+  if (r != TVI_OK) return r;
+  if ((r = check_opt(opt)) != TVI_OK) return r;
+  if (B < 0 || N < 0) return fail(TVI_EINVAL, "B and N must be >= 0 (got %d, %d)", B, N);
+  if (B == 0) return TVI_OK;
+  if (!times || !params || !y || !grad_out || !dparams)
+    return fail(TVI_EINVAL, "times, params, y, grad_out and dparams must not be NULL");
+  const int P = tvi_param_count(model);
+  const size_t need = model->per_series ? 0 : static_cast<size_t>(B) * static_cast<size_t>(P);
+  if (need > kNoAllocScratchDoubles)
+    return fail(TVI_EINVAL,
+                "tvi_adjoint_noalloc: B * P = %zu partial gradients exceed the fixed scratch of "
+                "%zu doubles (%zu bytes); use tvi_adjoint with a workspace",
+                need, kNoAllocScratchDoubles, kNoAllocScratchDoubles * sizeof(double));
+  double* scratch = nullptr;
+  if ((r = noalloc_scratch(&scratch)) != TVI_OK) return r;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  tvi::AdjArgs a;
+  a.B = B;
+  a.N = N;
+  a.chunk = opt->chunk < tvi::kSmallMaxChunk ? opt->chunk : tvi::kSmallMaxChunk;
+  a.refine = opt->precision == tvi::kPrecFp64 ? 0 : opt->adjoint_refine;
+  a.per_series = model->per_series ? 1 : 0;
+  a.times = times;
+  a.lengths = lengths;
+  a.params = params;
+  a.y = y;
+  a.grad_out = grad_out;
+  a.dparams = dparams;
+  a.dy0 = dy0;
+  // Every series block writes all P entries of its own row before the
+  // reduction reads them, so the scratch needs no clearing between calls.
+  a.partials = scratch;
+  if (N == 0) {
+    size_t dp_bytes = (a.per_series ? static_cast<size_t>(B) : 1u) * P * sizeof(double);
+    cudaError_t e = cudaMemsetAsync(dparams, 0, dp_bytes, s);
+    if (e == cudaSuccess && dy0)
+      e = cudaMemcpyAsync(dy0, grad_out, static_cast<size_t>(B) * model->n * sizeof(double),
+                          cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? TVI_OK : cuda_fail(e, "tvi_adjoint_noalloc: empty integration");
+  }
+  int rpt, threads;
+  tvi::small_launch_shape(a.chunk, opt->rows_per_thread, &rpt, &threads);
+  cudaError_t e = tvi::small_adjoint(model->kind, model->n, opt->precision, rpt, threads, a, P, s);
+  if (e != cudaSuccess) return cuda_fail(e, "tvi_adjoint_noalloc: kernel launch");
+  return TVI_OK;
+}
