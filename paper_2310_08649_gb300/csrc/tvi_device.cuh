@@ -222,17 +222,26 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsig
   return a > b ? a : b;
 }
 
-// Max over the first `nwa` warps of the block (the others pass 0).  All threads
-// must call it; the caller guarantees a __syncthreads() between two
-// consecutive calls (s_red is reused).
+// Barrier over the first `nthreads` threads of the block (whole warps).  The
+// whole block uses barrier 0 (__syncthreads); a leading subset of its warps uses
+// named barrier 1, so warps without work need not take part.
+__device__ __forceinline__ void sync_first(int nthreads) {
+  if (nthreads == static_cast<int>(blockDim.x))
+    __syncthreads();
+  else
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Max over the `nwa` warps that call it (the block's first nwa warps).  The
+// caller guarantees a barrier between two consecutive calls (s_red is reused).
 __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v,
                                                             unsigned long long* s_red, int lane,
-                                                            int warp, int nwarps, int nwa) {
+                                                            int warp, int nwa) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(kFull, v, o));
-  if (nwarps == 1) return v;  // uniform: a one-warp block needs no barrier
-  if (lane == 0 && warp < nwa) s_red[warp] = v;
-  __syncthreads();
+  if (nwa == 1) return v;  // one warp: no barrier needed
+  if (lane == 0) s_red[warp] = v;
+  sync_first(32 * nwa);
   unsigned long long r = s_red[0];
   for (int w = 1; w < nwa; ++w) r = umax64(r, s_red[w]);
   return r;
@@ -240,33 +249,29 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
 
 // ---------------------------------------------------------------------------
 // Solve the chain d_j = M_j d_{j-1} + v_j over the block's rows, d_{-1} = 0.
-// Thread t holds rows t*RPT .. t*RPT+RPT-1 in f[]; rows past the chunk end must
-// hold the identity map.  Only the first `nwa` warps hold rows; the others skip
-// all work but still reach the barriers.  On return x[r] = d of each own row
-// (active warps only).  Synchronisation: two __syncthreads() when nwa > 1.
+// Called by the block's first `nwa` warps only; thread t holds rows
+// t*RPT .. t*RPT+RPT-1 in f[], and rows past the chunk end must hold the
+// identity map.  On return x[r] = d of each own row.  Synchronisation: two
+// barriers over those warps when nwa > 1.
 // ---------------------------------------------------------------------------
 template <int NS, typename T, int RPT>
 __device__ __forceinline__ void solve_chain(const Aff<NS, T> (&f)[RPT], T (&x)[RPT][NS],
                                             Aff<NS, T>* s_wtot, int lane, int warp, int nwa) {
-  const bool wact = warp < nwa;
-  Aff<NS, T> seg;
-  if (wact) {
-    // (1) serial composition of the thread's own rows
-    seg = f[0];
+  // (1) serial composition of the thread's own rows
+  Aff<NS, T> seg = f[0];
 #pragma unroll
-    for (int r = 1; r < RPT; ++r) seg = compose(f[r], seg);
-    // (2) cyclic reduction over the lanes of the warp
+  for (int r = 1; r < RPT; ++r) seg = compose(f[r], seg);
+  // (2) cyclic reduction over the lanes of the warp
 #pragma unroll
-    for (int s = 1; s < 32; s <<= 1) {
-      Aff<NS, T> o = shfl_up_aff(seg, s);
-      if (lane >= s) seg = compose(seg, o);
-    }
+  for (int s = 1; s < 32; s <<= 1) {
+    Aff<NS, T> o = shfl_up_aff(seg, s);
+    if (lane >= s) seg = compose(seg, o);
   }
   // (3) cyclic reduction over the warps; vin = d at the end of the previous thread
   T vin[NS];
   if (nwa > 1) {
-    if (wact && lane == 31) s_wtot[warp] = seg;
-    __syncthreads();
+    if (lane == 31) s_wtot[warp] = seg;
+    sync_first(32 * nwa);
     if (warp == 0) {
       Aff<NS, T> w;
       if (lane < nwa)
@@ -282,8 +287,7 @@ __device__ __forceinline__ void solve_chain(const Aff<NS, T> (&f)[RPT], T (&x)[R
         for (int i = 0; i < NS; ++i) s_wtot[lane].v[i] = w.v[i];
       }
     }
-    __syncthreads();
-    if (!wact) return;
+    sync_first(32 * nwa);
     T vex[NS], vfull[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) vex[i] = (warp > 0) ? s_wtot[warp - 1].v[i] : T(0);
@@ -300,7 +304,6 @@ __device__ __forceinline__ void solve_chain(const Aff<NS, T> (&f)[RPT], T (&x)[R
       vin[i] = (lane == 0) ? vex[i] : u;
     }
   } else {
-    if (!wact) return;
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
       T u = __shfl_up_sync(kFull, seg.v[i], 1);

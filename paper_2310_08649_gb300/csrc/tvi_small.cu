@@ -36,9 +36,10 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
   __shared__ double s_wlast[32][NS];
   __shared__ unsigned long long s_red[32];
   __shared__ double s_carry[NS];
+  __shared__ int s_ctl[2];  // outcome and Newton updates of the last attempt
 
   const int b = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int N = a.N;
   const double* tb = a.times + static_cast<size_t>(b) * (N + 1);
   double* yb = a.y_out + static_cast<size_t>(b) * (N + 1) * NS;
@@ -85,16 +86,19 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
 
     double norm0 = 0.0;
     int it = 0, outcome = kConv;
+    // Only the nwa warps holding steps run the Newton loop; they synchronise on
+    // a named barrier among themselves, the others wait at the barrier after it.
+    if (wact) {
     for (;;) {
       // dy_{j-1} of the first own row: last row of the previous thread
       double prev[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) prev[s] = __shfl_up_sync(kFull, dy[RPT - 1][s], 1);
-      if (wact && lane == 31) {
+      if (lane == 31) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) s_wlast[warp][s] = dy[RPT - 1][s];
       }
-      __syncthreads();
+      sync_first(32 * nwa);
       if (lane == 0) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) prev[s] = (warp > 0) ? s_wlast[warp - 1][s] : 0.0;
@@ -117,7 +121,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
           }
         }
       }
-      const unsigned long long nb = block_max_u64(mx, s_red, lane, warp, nwarps, nwa);
+      const unsigned long long nb = block_max_u64(mx, s_red, lane, warp, nwa);
       const double nr = __longlong_as_double(static_cast<long long>(nb));
       if (it == 0) norm0 = nr;
       if (nb >= kNonFiniteBits) { outcome = kNonFinite; break; }
@@ -172,6 +176,14 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
       }
       ++it;
     }
+    if (tid == 0) {
+      s_ctl[0] = outcome;
+      s_ctl[1] = it;
+    }
+    }  // wact
+    __syncthreads();
+    outcome = s_ctl[0];
+    it = s_ctl[1];
 
     if (outcome != kConv && can_halve) {
       c_cur = (c_cur + 1) / 2;  // re-solve from the same chunk start with half the steps
@@ -268,6 +280,9 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
     double yk[RPT][NS], gk[RPT][NS], dt[RPT], av[RPT][NS];
     bool act[RPT];
     Aff<NS, T> f[RPT];
+    // warps holding no step of a short (last) chunk skip to the carry barrier
+    const bool wact = warp < nwa;
+    if (wact) {
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       const int q = tid * RPT + r;
@@ -320,7 +335,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
 #pragma unroll
         for (int s = 0; s < NS; ++s) s_wlast[warp][s] = av[RPT - 1][s];
       }
-      __syncthreads();
+      sync_first(32 * nwa);
       if (lane == 0) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) nxt[s] = (warp > 0) ? s_wlast[warp - 1][s] : 0.0;
@@ -355,12 +370,13 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
       for (int r = 0; r < RPT; ++r)
 #pragma unroll
         for (int s = 0; s < NS; ++s) av[r][s] += act[r] ? widen<T>(x[r][s]) : 0.0;
-      __syncthreads();  // s_wlast reuse
+      sync_first(32 * nwa);  // s_wlast reuse
     }
     // ---- parameter VJP: acc += dt_k (dh/dp)^T a_k ----
 #pragma unroll
     for (int r = 0; r < RPT; ++r)
       if (act[r] && dt[r] != 0.0) mdl.vjp_p(yk[r], av[r], dt[r], acc);
+    }  // wact
     // ---- carry a_{i+1} (row L-1) to the earlier chunk ----
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
