@@ -47,14 +47,33 @@ Layout layout(int B, int P) {
   return l;
 }
 
+bool is_mlp(const tvi_model* m) {
+  return m->kind == TVI_MODEL_MLP_TANH || m->kind == TVI_MODEL_MLP_SILU;
+}
+
 tvi_status check_model(const tvi_model* m) {
   if (!m) return fail(TVI_EINVAL, "model is NULL");
   if (tvi_param_count(m) < 0)
     return fail(TVI_EINVAL, "bad model (kind %d, n %d, hidden %d/%d)", m->kind, m->n, m->hidden1,
                 m->hidden2);
+  if (is_mlp(m)) {
+    if (m->per_series)
+      return fail(TVI_EUNSUPPORTED, "MLP models take one shared parameter vector");
+    if (!tvi::mlp_supported(m->n, m->hidden1, m->hidden2))
+      return fail(TVI_EUNSUPPORTED,
+                  "MLP sizes n %d, hidden %d/%d not built (n <= 32, hidden <= 128, multiples of 4)",
+                  m->n, m->hidden1, m->hidden2);
+    return TVI_OK;
+  }
   if (!tvi::small_supported(m->kind, m->n))
     return fail(TVI_EUNSUPPORTED, "model kind %d with n = %d is not built", m->kind, m->n);
   return TVI_OK;
+}
+
+// chunk the MLP path runs with: the requested one, at most N (and at least 1)
+int mlp_chunk(const tvi_options* o, int N) {
+  const int c = o->chunk < N ? o->chunk : N;
+  return c < 1 ? 1 : c;
 }
 
 tvi_status check_opt(const tvi_options* o) {
@@ -102,10 +121,13 @@ int tvi_param_count(const tvi_model* m) {
 }
 
 size_t tvi_workspace_bytes(const tvi_model* model, const tvi_options* opt, int B, int N) {
-  (void)opt;
-  (void)N;
   int P = tvi_param_count(model);
-  if (P < 0 || B < 0) return 0;
+  if (P < 0 || B < 0 || N < 0) return 0;
+  if (is_mlp(model)) {
+    if (!opt || !tvi::mlp_supported(model->n, model->hidden1, model->hidden2)) return 0;
+    return tvi::mlp_workspace_bytes(model->n, model->hidden1, model->hidden2, B, mlp_chunk(opt, N),
+                                    opt->precision);
+  }
   return layout(B, P).total;
 }
 
@@ -123,8 +145,9 @@ tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, 
     return fail(TVI_EINVAL, "y0, times, params and y_out must not be NULL");
   const int P = tvi_param_count(model);
   const Layout l = layout(B, P);
-  if (!workspace || workspace_bytes < l.total)
-    return fail(TVI_EWORKSPACE, "workspace of %zu bytes needed (got %zu)", l.total,
+  const size_t need = tvi_workspace_bytes(model, opt, B, N);
+  if (!workspace || workspace_bytes < need)
+    return fail(TVI_EWORKSPACE, "workspace of %zu bytes needed (got %zu)", need,
                 workspace ? workspace_bytes : static_cast<size_t>(0));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);
@@ -147,6 +170,17 @@ tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, 
   a.series_status = series_status;
   a.worst = reinterpret_cast<int*>(ws + l.worst);
 
+  if (is_mlp(model)) {
+    a.chunk = mlp_chunk(opt, N);
+    int worst = 0;
+    cudaError_t e = tvi::mlp_forward(model->kind, model->n, model->hidden1, model->hidden2,
+                                     opt->precision, a, workspace, s,
+                                     opt->sync_status ? &worst : nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "tvi_integrate (MLP path)");
+    if (worst == 2) return fail(TVI_ENONFINITE, "a series produced a non-finite residual");
+    if (worst == 1) return fail(TVI_ENOTCONV, "a series hit the Newton iteration limit");
+    return TVI_OK;
+  }
   cudaError_t e = cudaMemsetAsync(a.worst, 0, sizeof(int), s);
   if (e != cudaSuccess) return cuda_fail(e, "tvi_integrate: clearing the status word");
   int rpt, threads;
@@ -177,8 +211,9 @@ tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, in
     return fail(TVI_EINVAL, "times, params, y, grad_out and dparams must not be NULL");
   const int P = tvi_param_count(model);
   const Layout l = layout(B, P);
-  if (!workspace || workspace_bytes < l.total)
-    return fail(TVI_EWORKSPACE, "workspace of %zu bytes needed (got %zu)", l.total,
+  const size_t need = tvi_workspace_bytes(model, opt, B, N);
+  if (!workspace || workspace_bytes < need)
+    return fail(TVI_EWORKSPACE, "workspace of %zu bytes needed (got %zu)", need,
                 workspace ? workspace_bytes : static_cast<size_t>(0));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);
@@ -197,6 +232,12 @@ tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, in
   a.dparams = dparams;
   a.dy0 = dy0;
   a.partials = reinterpret_cast<double*>(ws + l.partials);
+  if (is_mlp(model)) {
+    a.chunk = mlp_chunk(opt, N);
+    cudaError_t e = tvi::mlp_adjoint(model->kind, model->n, model->hidden1, model->hidden2,
+                                     opt->precision, a, workspace, s);
+    return e == cudaSuccess ? TVI_OK : cuda_fail(e, "tvi_adjoint (MLP path)");
+  }
   if (N == 0) {
     // no steps: dL/dp = 0 and dL/dy0 = grad_out[:, 0]
     size_t dp_bytes = (a.per_series ? static_cast<size_t>(B) : 1u) * P * sizeof(double);
@@ -283,6 +324,8 @@ extern "C" tvi_status tvi_adjoint_noalloc(const tvi_model* model, const tvi_opti
   g_last_error.clear();
   tvi_status r = check_model(model);
   if (r != TVI_OK) return r;
+  if (is_mlp(model))
+    return fail(TVI_EUNSUPPORTED, "tvi_adjoint_noalloc covers the linear and van der Pol models");
   if ((r = check_opt(opt)) != TVI_OK) return r;
   if (B < 0 || N < 0) return fail(TVI_EINVAL, "B and N must be >= 0 (got %d, %d)", B, N);
   if (B == 0) return TVI_OK;

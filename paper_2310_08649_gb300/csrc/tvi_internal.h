@@ -52,4 +52,14 @@ cudaError_t small_forward(int kind, int n, int precision, int rpt, int threads, 
 cudaError_t small_adjoint(int kind, int n, int precision, int rpt, int threads, const AdjArgs& a,
                           int P, cudaStream_t s);
 
+// Neural-ODE (MLP right-hand side) path: shared parameters, n <= 32 and hidden
+// widths <= 128, all multiples of 4.  The chunk in the argument blocks is the
+// effective one (<= N); workspace as sized by mlp_workspace_bytes.
+bool mlp_supported(int n, int h1, int h2);
+size_t mlp_workspace_bytes(int n, int h1, int h2, int B, int chunk, int precision);
+cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const FwdArgs& a,
+                        void* workspace, cudaStream_t s, int* host_worst);
+cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const AdjArgs& a,
+                        void* workspace, cudaStream_t s);
+
 }  // namespace tvi

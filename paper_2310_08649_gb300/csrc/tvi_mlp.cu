@@ -1,0 +1,1003 @@
+// tvi_mlp.cu -- neural-ODE models (h = MLP(y)), state sizes up to 32.
+//
+// The right-hand side is the three-layer MLP of the paper's neural ODE (Sec.
+// 5.1.1): tanh after every layer, or SiLU after the two hidden layers with a
+// linear output.  Evaluating it in FP64 for the Newton residual costs
+// 2 (n h1 + h1 h2 + h2 n) FP64 flops per (series, step) -- 12.3k at n = 16,
+// 49k at n = 32 -- which on GB300 (FP64 at 1/64 of FP32) outweighs the rest of
+// an iteration, so this path spreads the steps of all series over the whole GPU
+// instead of giving each series one block.  One Newton iteration of a chunk
+// (Alg. 1), all series at once, converged series skipped:
+//   mlp_residual_kernel  FP64 MLP at y_i + dy_j -> R_j (Eq. batched-backward-
+//                        euler), per-series max |R| (integer atomics on FP64
+//                        bits), activation derivatives (FP64, so FP64 blocks
+//                        are exact)
+//   mlp_check_kernel     per-series convergence (reading C-4); the host reads
+//                        how many series still iterate
+//   mlp_blocks_kernel    J = D3 W3 D2 W2 D1 W1, A = I - dt J, M = A^-1 in the
+//                        block precision
+//   mlp_chain_kernel     d_j = M_j (d_{j-1} + R_j) per series, dy -= d (FP64)
+// The adjoint (App. A.2) runs the chunks in reverse with transposed blocks,
+// FP64 refinement residuals r = g + a_next - a + dt J^T a from an FP64
+// vector-Jacobian product (mlp_vjp_kernel), and the parameter gradient
+// sum_k dt_k (dh/dp)^T a_k as tiled outer-product sums (mlp_param_grad_kernel).
+#include <cuda_runtime.h>
+
+#include "tvi_device.cuh"
+#include "tvi_internal.h"
+
+namespace tvi {
+
+namespace {
+
+constexpr int kTileThreads = 256;
+
+struct MlpDims {
+  int n, h1, h2, P;
+};
+
+struct MlpW {
+  const double *W1, *b1, *W2, *b2, *W3, *b3;
+};
+
+__device__ __forceinline__ MlpW mlp_split(const double* p, const MlpDims& d) {
+  MlpW w;
+  w.W1 = p;
+  w.b1 = w.W1 + d.h1 * d.n;
+  w.W2 = w.b1 + d.h1;
+  w.b2 = w.W2 + d.h2 * d.h1;
+  w.W3 = w.b2 + d.h2;
+  w.b3 = w.W3 + d.n * d.h2;
+  return w;
+}
+
+// activation and its derivative (FP64)
+template <int KIND>
+__device__ __forceinline__ void act_hidden(double z, double& a, double& da) {
+  if constexpr (KIND == kKindMlpTanh) {
+    a = tanh(z);
+    da = 1.0 - a * a;
+  } else {
+    const double s = 1.0 / (1.0 + exp(-z));
+    a = z * s;
+    da = s + z * s * (1.0 - s);
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ void act_out(double z, double& a, double& da) {
+  if constexpr (KIND == kKindMlpTanh) {
+    a = tanh(z);
+    da = 1.0 - a * a;
+  } else {
+    a = z;
+    da = 1.0;
+  }
+}
+
+__device__ __forceinline__ int step_of(int reverse, int i0, int L, int j) {
+  return reverse ? i0 + L - j : i0 + 1 + j;
+}
+
+__device__ __forceinline__ double step_dt(const double* tb, int len, int k) {
+  return (k <= len) ? tb[k] - tb[k - 1] : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 forward pass for a tile of TP pairs held in shared memory.  Thread t
+// takes pair p = t % TP and every G-th output row (G = threads / TP), so the
+// lanes of a warp read the same weight row (broadcast through the read-only
+// cache).  Layouts [row][TP] keep the pairs contiguous (no bank conflicts).
+//   sy [n][TP] in; sa1 [h1][TP], sa2 [h2][TP], sz3 [n][TP] out;
+//   sd1, sd2 (optional) receive act'(z) of the hidden layers (FP64);
+//   dv_tile (optional) receives act'(z) of the hidden layers ([pair][dvs]).
+// ---------------------------------------------------------------------------
+template <int KIND, int TP>
+__device__ __forceinline__ void mlp_tile_forward(const MlpW& w, const MlpDims& d, const double* sy,
+                                                 double* sa1, double* sa2, double* sz3,
+                                                 double* sd1, double* sd2, int np,
+                                                 double* dv_tile, int dvs) {
+  constexpr int G = kTileThreads / TP;
+  const int t = threadIdx.x, p = t % TP, g = t / TP;
+  const bool live = p < np;
+  for (int r = g; r < d.h1; r += G) {
+    double acc = w.b1[r];
+    const double* wr = w.W1 + r * d.n;
+    for (int c = 0; c < d.n; ++c) acc = fma(__ldg(wr + c), sy[c * TP + p], acc);
+    double a, da;
+    act_hidden<KIND>(acc, a, da);
+    sa1[r * TP + p] = a;
+    if (sd1) sd1[r * TP + p] = da;
+    if (dv_tile && live) dv_tile[p * dvs + r] = da;
+  }
+  __syncthreads();
+  for (int r = g; r < d.h2; r += G) {
+    double acc = w.b2[r];
+    const double* wr = w.W2 + r * d.h1;
+    for (int c = 0; c < d.h1; ++c) acc = fma(__ldg(wr + c), sa1[c * TP + p], acc);
+    double a, da;
+    act_hidden<KIND>(acc, a, da);
+    sa2[r * TP + p] = a;
+    if (sd2) sd2[r * TP + p] = da;
+    if (dv_tile && live) dv_tile[p * dvs + d.h1 + r] = da;
+  }
+  __syncthreads();
+  for (int r = g; r < d.n; r += G) {
+    double acc = w.b3[r];
+    const double* wr = w.W3 + r * d.h2;
+    for (int c = 0; c < d.h2; ++c) acc = fma(__ldg(wr + c), sa2[c * TP + p], acc);
+    sz3[r * TP + p] = acc;
+  }
+  __syncthreads();
+}
+
+__global__ void convert_weights_kernel(const double* p, float* f, int P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P) f[i] = static_cast<float>(p[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Residual (forward) or activation derivatives at the stored trajectory
+// (adjoint).  Grid: (ceil(L / TP), B).
+// ---------------------------------------------------------------------------
+struct ResidualArgs {
+  MlpDims d;
+  int B, N, i0, L, c;
+  int reverse;               // 1: adjoint -- y from the trajectory at step i0 + L - j, no R
+  const double* times;
+  const int* lengths;
+  const double* params;
+  const double* yi;          // [B][n] chunk start (forward)
+  const double* dy;          // [B][c][n] (forward)
+  const double* ytraj;       // [B][N+1][n] (adjoint)
+  double* R;                 // [B][c][n] (forward)
+  double* dv;                // [B][c][h1+h2+n]
+  unsigned long long* norm;  // [B] max |R| bits (forward)
+  const int* active;         // [B] or null
+};
+
+template <int KIND, int TP>
+__global__ void __launch_bounds__(kTileThreads) mlp_residual_kernel(ResidualArgs a) {
+  extern __shared__ double smem[];
+  const int b = blockIdx.y;
+  if (a.active && !a.active[b]) return;
+  const MlpDims d = a.d;
+  const int j0 = blockIdx.x * TP;
+  const int np = min(TP, a.L - j0);
+  double* sy = smem;
+  double* sa1 = sy + d.n * TP;
+  double* sa2 = sa1 + d.h1 * TP;
+  double* sz3 = sa2 + d.h2 * TP;
+  const MlpW w = mlp_split(a.params, d);
+  const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
+  const int len = a.lengths ? min(max(a.lengths[b], 0), a.N) : a.N;
+  const double* dyb = a.dy ? a.dy + static_cast<size_t>(b) * a.c * d.n : nullptr;
+  for (int e = threadIdx.x; e < d.n * TP; e += kTileThreads) {
+    const int c = e / TP, p = e % TP;
+    double v = 0.0;
+    if (p < np) {
+      const int j = j0 + p;
+      if (a.reverse)
+        v = a.ytraj[(static_cast<size_t>(b) * (a.N + 1) + step_of(1, a.i0, a.L, j)) * d.n + c];
+      else
+        v = a.yi[b * d.n + c] + dyb[j * d.n + c];
+    }
+    sy[e] = v;
+  }
+  __syncthreads();
+  const int dvs = d.h1 + d.h2 + d.n;
+  double* dv_tile = a.dv + (static_cast<size_t>(b) * a.c + j0) * dvs;
+  mlp_tile_forward<KIND, TP>(w, d, sy, sa1, sa2, sz3, nullptr, nullptr, np, dv_tile, dvs);
+  constexpr int G = kTileThreads / TP;
+  const int t = threadIdx.x, p = t % TP, g = t / TP;
+  unsigned long long mx = 0ull;
+  if (p < np) {
+    const int j = j0 + p;
+    const double dt = step_dt(tb, len, step_of(a.reverse, a.i0, a.L, j));
+    for (int r = g; r < d.n; r += G) {
+      double h, dh;
+      act_out<KIND>(sz3[r * TP + p], h, dh);
+      dv_tile[p * dvs + d.h1 + d.h2 + r] = dh;
+      if (!a.reverse) {
+        const double prev = (j > 0) ? dyb[(j - 1) * d.n + r] : 0.0;
+        const double R = fma(-dt, h, dyb[j * d.n + r] - prev);
+        a.R[(static_cast<size_t>(b) * a.c + j) * d.n + r] = R;
+        mx = umax64(mx, abs_bits(R));
+      }
+    }
+  }
+  if (!a.reverse) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = umax64(mx, __shfl_xor_sync(kFull, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(a.norm + b, mx);
+  }
+}
+
+struct CheckArgs {
+  int B, it, max_iter;
+  double tol_abs, tol_rel;
+  unsigned long long* norm;  // [B] cleared here for the next iteration
+  double* norm0;             // [B]
+  int* active;               // [B]
+  int* status;               // [B] (sticky)
+  int* iters;                // [B] Newton updates of the current chunk
+  int* remaining;            // device word: series still iterating
+};
+
+// Alg. 1 convergence test per series; counts the series that need another update.
+__global__ void mlp_check_kernel(CheckArgs a) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.B || !a.active[b]) return;
+  const unsigned long long nb = a.norm[b];
+  a.norm[b] = 0ull;
+  const double nr = __longlong_as_double(static_cast<long long>(nb));
+  if (a.it == 0) a.norm0[b] = nr;
+  bool stop = false;
+  if (nb >= kNonFiniteBits) {
+    a.status[b] = 2;
+    stop = true;
+  } else if (nr <= a.tol_abs || nr <= a.tol_rel * a.norm0[b]) {
+    stop = true;
+  } else if (a.it >= a.max_iter) {
+    if (a.status[b] == 0) a.status[b] = 1;
+    stop = true;
+  }
+  if (stop) {
+    a.active[b] = 0;
+  } else {
+    a.iters[b] = a.it + 1;
+    atomicAdd(a.remaining, 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Blocks: per pair J = D3 W3 D2 W2 D1 W1, A = I - dt J, M = A^-1 (A^-T when
+// reverse) in the block precision T.  A thread block takes TP consecutive steps
+// of one series and forms the products for all of them as two register-tiled
+// GEMMs over the columns (pair, input component):
+//     G [h2][TP n] = W2 [h2][h1] . U [h1][TP n],   U[q][(p, c)] = d1[p][q] W1[q][c]
+//     J [n][TP n]  = W3 [n][h2]  . (D2 G)
+// (4 x 4 outputs per thread; weights through the read-only cache; U and G in
+// shared memory).  Each warp then inverts pairs by Gauss-Jordan with partial
+// pivoting on [A | I] in shared memory.  Needs n, h1, h2 multiples of 4.
+// ---------------------------------------------------------------------------
+struct BlocksArgs {
+  MlpDims d;
+  int B, N, i0, L, c;
+  int reverse;
+  const double* times;
+  const int* lengths;
+  const float* Wf;    // FP32 copy of the parameters (same layout), FP32 blocks
+  const double* Wd;   // the FP64 parameters, FP64 blocks
+  const double* dv;   // [B][c][h1+h2+n]
+  const int* active;  // [B] or null
+  void* M;            // [B][c][n][n] in T
+};
+
+// weight i of the flat parameter vector in the block precision
+template <typename T>
+__device__ __forceinline__ T wget(const BlocksArgs& a, int i) {
+  if constexpr (sizeof(T) == sizeof(double)) return __ldg(a.Wd + i);
+  else return __ldg(a.Wf + i);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, int TP) {
+  extern __shared__ unsigned char smem_raw[];
+  const MlpDims d = a.d;
+  const int n = d.n, h1 = d.h1, h2 = d.h2;
+  const int NT = TP * n;
+  const int b = blockIdx.y;
+  if (a.active && !a.active[b]) return;
+  const int j0 = blockIdx.x * TP;
+  const int np = min(TP, a.L - j0);
+  T* sU = reinterpret_cast<T*>(smem_raw);  // [h1][NT]
+  T* sG = sU + h1 * NT;                     // [h2][NT]
+  T* sA = sG + h2 * NT;                     // [TP][n][2n]
+  T* sdt = sA + TP * n * 2 * n;             // [TP]
+  const int oW2 = h1 * n + h1;            // offsets in the flat parameter vector
+  const int oW3 = oW2 + h2 * h1 + h2;
+  const int dvs = h1 + h2 + n;
+  const double* dvt = a.dv + (static_cast<size_t>(b) * a.c + j0) * dvs;
+  const int tid = threadIdx.x;
+  const int len = a.lengths ? min(max(a.lengths[b], 0), a.N) : a.N;
+  const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
+  for (int p = tid; p < TP; p += kTileThreads)
+    sdt[p] = static_cast<T>(p < np ? step_dt(tb, len, step_of(a.reverse, a.i0, a.L, j0 + p)) : 0.0);
+  for (int e = tid; e < h1 * NT; e += kTileThreads) {
+    const int q = e / NT, col = e % NT, p = col / n, c = col % n;
+    sU[e] = (p < np) ? static_cast<T>(dvt[p * dvs + q]) * wget<T>(a, q * n + c) : T(0);
+  }
+  __syncthreads();
+  {  // G = D2 W2 U
+    const int tn = NT / 4, tiles = (h2 / 4) * tn;
+    for (int tt = tid; tt < tiles; tt += kTileThreads) {
+      const int r0 = (tt / tn) * 4, c0 = (tt % tn) * 4;
+      T acc[4][4] = {};
+      for (int q = 0; q < h1; ++q) {
+        T wv[4], uv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) wv[i] = wget<T>(a, oW2 + (r0 + i) * h1 + q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) uv[i] = sU[q * NT + c0 + i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int k2 = 0; k2 < 4; ++k2) acc[i][k2] = fma(wv[i], uv[k2], acc[i][k2]);
+      }
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) {
+        const int p = (c0 + k2) / n;
+        const bool live = p < np;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const T d2v = live ? static_cast<T>(dvt[p * dvs + h1 + r0 + i]) : T(0);
+          sG[(r0 + i) * NT + c0 + k2] = d2v * acc[i][k2];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  {  // A = I - dt D3 W3 G, augmented with I
+    const int tn = NT / 4, tiles = (n / 4) * tn;
+    for (int tt = tid; tt < tiles; tt += kTileThreads) {
+      const int r0 = (tt / tn) * 4, c0 = (tt % tn) * 4;
+      T acc[4][4] = {};
+      for (int q = 0; q < h2; ++q) {
+        T wv[4], gv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) wv[i] = wget<T>(a, oW3 + (r0 + i) * h2 + q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) gv[i] = sG[q * NT + c0 + i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int k2 = 0; k2 < 4; ++k2) acc[i][k2] = fma(wv[i], gv[k2], acc[i][k2]);
+      }
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) {
+        const int col = c0 + k2, p = col / n, c = col % n;
+        if (p >= np) continue;
+        T* Ap = sA + p * n * 2 * n;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = r0 + i;
+          const T J = static_cast<T>(dvt[p * dvs + h1 + h2 + r]) * acc[i][k2];
+          Ap[r * 2 * n + c] = ((r == c) ? T(1) : T(0)) - sdt[p] * J;
+          Ap[r * 2 * n + n + c] = (r == c) ? T(1) : T(0);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int p = warp; p < np; p += kTileThreads / 32) {
+    T* Ap = sA + p * n * 2 * n;
+    for (int kk = 0; kk < n; ++kk) {
+      T best = (lane >= kk && lane < n) ? fabs(Ap[lane * 2 * n + kk]) : T(-1);
+      int piv = lane;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(kFull, best, o);
+        const int op = __shfl_xor_sync(kFull, piv, o);
+        if (ob > best || (ob == best && op < piv)) {
+          best = ob;
+          piv = op;
+        }
+      }
+      if (piv != kk) {
+        for (int col = lane; col < 2 * n; col += 32) {
+          const T tmp = Ap[kk * 2 * n + col];
+          Ap[kk * 2 * n + col] = Ap[piv * 2 * n + col];
+          Ap[piv * 2 * n + col] = tmp;
+        }
+      }
+      __syncwarp();
+      const T inv = T(1) / Ap[kk * 2 * n + kk];
+      __syncwarp();
+      for (int col = lane; col < 2 * n; col += 32) Ap[kk * 2 * n + col] *= inv;
+      __syncwarp();
+      for (int e = lane; e < n * 2 * n; e += 32) {
+        const int r = e / (2 * n), col = e % (2 * n);
+        if (r != kk && col != kk) Ap[e] = fma(-Ap[r * 2 * n + kk], Ap[kk * 2 * n + col], Ap[e]);
+      }
+      __syncwarp();
+      for (int r = lane; r < n; r += 32)
+        if (r != kk) Ap[r * 2 * n + kk] = T(0);
+      __syncwarp();
+    }
+    T* Mo = static_cast<T*>(a.M) + (static_cast<size_t>(b) * a.c + j0 + p) * n * n;
+    for (int e = lane; e < n * n; e += 32) {
+      const int r = e / n, col = e % n;
+      Mo[e] = a.reverse ? Ap[col * 2 * n + n + r] : Ap[r * 2 * n + n + col];
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block substitution d_j = M_j (d_{j-1} + rhs_j), d_{-1} = x_init (Alg. 2 on the
+// normalised blocks): one warp per series, lane r owns component r and keeps
+// row r of M_j in registers, the next row prefetched.  For n = 16-32 this is
+// n^2 work per step against the n^3 per step of a cyclic reduction, the
+// trade-off the paper reports for larger systems.
+// ---------------------------------------------------------------------------
+struct ChainArgs {
+  int B, n, L, c, N, i0, reverse;
+  const void* M;           // [B][c][n][n] in T
+  const double* rhs_buf;   // [B][c][n] rhs by row, or null
+  const double* rhs_traj;  // [B][N+1][n] rhs by step (adjoint dL/dy), or null
+  const double* x_init;    // [B][n] d_{-1}, or null (zero)
+  const int* active;       // [B] or null
+  double* x;               // [B][c][n]
+  int mode;                // 0: x -= d   1: x = d   2: x += d
+};
+
+template <typename T>
+__global__ void mlp_chain_kernel(ChainArgs a) {
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= a.B || (a.active && !a.active[b])) return;
+  const int n = a.n;
+  const bool own = lane < n;
+  const T* Mb = static_cast<const T*>(a.M) + static_cast<size_t>(b) * a.c * n * n;
+  double* xb = a.x + static_cast<size_t>(b) * a.c * n;
+  T mrow[32], mnext[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) mrow[q] = (own && q < n && a.L > 0) ? Mb[lane * n + q] : T(0);
+  T dprev = (a.x_init && own) ? static_cast<T>(a.x_init[b * n + lane]) : T(0);
+  for (int j = 0; j < a.L; ++j) {
+    if (j + 1 < a.L) {
+      const T* Mn = Mb + static_cast<size_t>(j + 1) * n * n + lane * n;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) mnext[q] = (own && q < n) ? Mn[q] : T(0);
+    }
+    double r = 0.0;
+    if (own) {
+      if (a.rhs_buf)
+        r = a.rhs_buf[(static_cast<size_t>(b) * a.c + j) * n + lane];
+      else
+        r = a.rhs_traj[(static_cast<size_t>(b) * (a.N + 1) + step_of(a.reverse, a.i0, a.L, j)) * n +
+                       lane];
+    }
+    const T u = dprev + static_cast<T>(r);  // component `lane` of d_{j-1} + rhs_j
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      if (q < n) acc = fma(mrow[q], __shfl_sync(kFull, u, q), acc);
+    }
+    dprev = own ? acc : T(0);
+    if (own) {
+      double& o = xb[j * n + lane];
+      const double dd = static_cast<double>(acc);
+      if (a.mode == 0) o -= dd;
+      else if (a.mode == 1) o = dd;
+      else o += dd;
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) mrow[q] = mnext[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 vector-Jacobian product at the stored trajectory (adjoint).  For each
+// pair (row j = step k = i0 + L - j) with adjoint a_j:
+//   delta3 = a * h'(z3), delta2 = (W3^T delta3) * act'(z2),
+//   delta1 = (W2^T delta2) * act'(z1), J^T a = W1^T delta1.
+// Outputs (each optional):
+//   res  r_j = g_k + a_{j-1} - a_j + dt_k J^T a_j  (a_{-1} = carry): the FP64
+//        residual of the chunk's adjoint system, for refinement
+//   act  [pair][n+1+h1+1+h2+1] = (y, 1, a1, 1, a2, 1) and
+//   del  [pair][h1+h2+n] = dt_k (delta1, delta2, delta3): the factors of the
+//        parameter gradient dt_k (dh/dp)^T a_k
+// Grid: (ceil(L / TP), B).
+// ---------------------------------------------------------------------------
+struct VjpArgs {
+  MlpDims d;
+  int B, N, i0, L, c;
+  const double* times;
+  const int* lengths;
+  const double* params;
+  const double* ytraj;     // [B][N+1][n]
+  const double* g;         // [B][N+1][n]
+  const double* carry;     // [B][n]
+  const double* av;        // [B][c][n] adjoint by row
+  double* res;             // [B][c][n] or null
+  double* act;             // [B*c][n+h1+h2+3] or null
+  double* del;             // [B*c][h1+h2+n] or null
+};
+
+template <int KIND, int TP>
+__global__ void __launch_bounds__(kTileThreads) mlp_vjp_kernel(VjpArgs a) {
+  extern __shared__ double smem[];
+  const MlpDims d = a.d;
+  const int n = d.n, h1 = d.h1, h2 = d.h2;
+  const int b = blockIdx.y;
+  const int j0 = blockIdx.x * TP;
+  const int np = min(TP, a.L - j0);
+  double* sy = smem;               // [n][TP]
+  double* sa1 = sy + n * TP;       // [h1][TP]
+  double* sa2 = sa1 + h1 * TP;     // [h2][TP]
+  double* sd1 = sa2 + h2 * TP;     // [h1][TP] act'(z1), then delta1
+  double* sd2 = sd1 + h1 * TP;     // [h2][TP] act'(z2), then delta2
+  double* sz3 = sd2 + h2 * TP;     // [n][TP]  z3, then delta3
+  const MlpW w = mlp_split(a.params, d);
+  const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
+  const int len = a.lengths ? min(max(a.lengths[b], 0), a.N) : a.N;
+  for (int e = threadIdx.x; e < n * TP; e += kTileThreads) {
+    const int c = e / TP, p = e % TP;
+    sy[e] = (p < np) ? a.ytraj[(static_cast<size_t>(b) * (a.N + 1) +
+                                step_of(1, a.i0, a.L, j0 + p)) * n + c]
+                     : 0.0;
+  }
+  __syncthreads();
+  mlp_tile_forward<KIND, TP>(w, d, sy, sa1, sa2, sz3, sd1, sd2, np, nullptr, 0);
+  constexpr int G = kTileThreads / TP;
+  const int t = threadIdx.x, p = t % TP, g = t / TP;
+  const bool live = p < np;
+  const int j = j0 + p;
+  const double* avb = a.av + static_cast<size_t>(b) * a.c * n;
+  // delta3 = a * h'(z3)
+  for (int r = g; r < n; r += G) {
+    double h, dh;
+    act_out<KIND>(sz3[r * TP + p], h, dh);
+    sz3[r * TP + p] = live ? avb[j * n + r] * dh : 0.0;
+  }
+  __syncthreads();
+  // delta2 = (W3^T delta3) * act'(z2)
+  for (int c = g; c < h2; c += G) {
+    double acc = 0.0;
+    for (int r = 0; r < n; ++r) acc = fma(__ldg(w.W3 + r * h2 + c), sz3[r * TP + p], acc);
+    sd2[c * TP + p] *= acc;
+  }
+  __syncthreads();
+  // delta1 = (W2^T delta2) * act'(z1)
+  for (int c = g; c < h1; c += G) {
+    double acc = 0.0;
+    for (int r = 0; r < h2; ++r) acc = fma(__ldg(w.W2 + r * h1 + c), sd2[r * TP + p], acc);
+    sd1[c * TP + p] *= acc;
+  }
+  __syncthreads();
+  if (!live) return;
+  const int k = step_of(1, a.i0, a.L, j);
+  const double dt = step_dt(tb, len, k);
+  if (a.res) {
+    // r_j = g_k + a_{j-1} - a_j + dt (W1^T delta1)
+    for (int c = g; c < n; c += G) {
+      double acc = 0.0;
+      for (int r = 0; r < h1; ++r) acc = fma(__ldg(w.W1 + r * n + c), sd1[r * TP + p], acc);
+      const double prev = (j > 0) ? avb[(j - 1) * n + c] : a.carry[b * n + c];
+      const double gk = a.g[(static_cast<size_t>(b) * (a.N + 1) + k) * n + c];
+      a.res[(static_cast<size_t>(b) * a.c + j) * n + c] = fma(dt, acc, gk + prev - avb[j * n + c]);
+    }
+  }
+  if (a.act) {
+    const int aw = n + h1 + h2 + 3, dw = h1 + h2 + n;
+    double* ar = a.act + (static_cast<size_t>(b) * a.c + j) * aw;
+    double* dr = a.del + (static_cast<size_t>(b) * a.c + j) * dw;
+    for (int c = g; c < n; c += G) ar[c] = sy[c * TP + p];
+    for (int c = g; c < h1; c += G) ar[n + 1 + c] = sa1[c * TP + p];
+    for (int c = g; c < h2; c += G) ar[n + 1 + h1 + 1 + c] = sa2[c * TP + p];
+    if (g == 0) {
+      ar[n] = 1.0;
+      ar[n + 1 + h1] = 1.0;
+      ar[n + 1 + h1 + 1 + h2] = 1.0;
+    }
+    for (int c = g; c < h1; c += G) dr[c] = dt * sd1[c * TP + p];
+    for (int c = g; c < h2; c += G) dr[h1 + c] = dt * sd2[c * TP + p];
+    for (int c = g; c < n; c += G) dr[h1 + h2 + c] = dt * sz3[c * TP + p];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Parameter gradient of one chunk: for each layer l, the [rows][cols + 1] block
+// (weights and bias) += sum over the chunk's pairs of del_l[pair][row] *
+// act_l[pair][col] (act's extra column is 1 for the bias).  Each thread block
+// owns a 32 x 32 output tile (no atomics: a fixed summation order), stages 64
+// pairs at a time in shared memory, forms products in T and adds every
+// 64-pair partial sum into an FP64 accumulator.
+// ---------------------------------------------------------------------------
+struct ParamArgs {
+  MlpDims d;
+  int B, L, c;
+  const double* act;  // [B*c][n+h1+h2+3]
+  const double* del;  // [B*c][h1+h2+n]
+  double* acc;        // [P] FP64 accumulator (flat parameter layout)
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) mlp_param_grad_kernel(ParamArgs a) {
+  __shared__ T sX[64][33];
+  __shared__ T sY[64][33];
+  const MlpDims d = a.d;
+  const int n = d.n, h1 = d.h1, h2 = d.h2;
+  const int aw = n + h1 + h2 + 3, dw = h1 + h2 + n;
+  // layer geometry: rows, cols (incl. bias), del offset, act offset, W offset, bias offset
+  int rows[3] = {h1, h2, n}, cols[3] = {n + 1, h1 + 1, h2 + 1};
+  int doff[3] = {0, h1, h1 + h2}, aoff[3] = {0, n + 1, n + 1 + h1 + 1};
+  int woff[3] = {0, h1 * n + h1, h1 * n + h1 + h2 * h1 + h2};
+  int tiles[3];
+  for (int l = 0; l < 3; ++l) tiles[l] = ((rows[l] + 31) / 32) * ((cols[l] + 31) / 32);
+  int tile = blockIdx.x, l = 0;
+  while (l < 2 && tile >= tiles[l]) tile -= tiles[l++];
+  const int tcols = (cols[l] + 31) / 32;
+  const int r0 = (tile / tcols) * 32, c0 = (tile % tcols) * 32;
+  const int tid = threadIdx.x;
+  const int tr = tid / 8, tc = (tid % 8) * 4;  // 32 rows x (8 x 4) cols
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int npairs = a.B * a.L;
+  for (int p0 = 0; p0 < npairs; p0 += 64) {
+    for (int e = tid; e < 64 * 32; e += 256) {
+      const int pp = e / 32, q = e % 32;
+      const int pi = p0 + pp;
+      T xv = T(0), yv = T(0);
+      if (pi < npairs) {
+        const size_t row = static_cast<size_t>(pi / a.L) * a.c + (pi % a.L);
+        if (r0 + q < rows[l]) xv = static_cast<T>(a.del[row * dw + doff[l] + r0 + q]);
+        if (c0 + q < cols[l]) yv = static_cast<T>(a.act[row * aw + aoff[l] + c0 + q]);
+      }
+      sX[pp][q] = xv;
+      sY[pp][q] = yv;
+    }
+    __syncthreads();
+    T part[4] = {T(0), T(0), T(0), T(0)};
+    for (int pp = 0; pp < 64; ++pp) {
+      const T xv = sX[pp][tr];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) part[i] = fma(xv, sY[pp][tc + i], part[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] += static_cast<double>(part[i]);
+    __syncthreads();
+  }
+  const int r = r0 + tr;
+  if (r >= rows[l]) return;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int c = c0 + tc + i;
+    if (c >= cols[l]) continue;
+    const int idx = (c < cols[l] - 1) ? woff[l] + r * (cols[l] - 1) + c
+                                      : woff[l] + rows[l] * (cols[l] - 1) + r;
+    a.acc[idx] += acc[i];
+  }
+}
+
+int param_grad_tiles(const MlpDims& d) {
+  auto t = [](int r, int c) { return ((r + 31) / 32) * ((c + 31) / 32); };
+  return t(d.h1, d.n + 1) + t(d.h2, d.h1 + 1) + t(d.n, d.h2 + 1);
+}
+
+// ---------------------------------------------------------------------------
+// Small bookkeeping kernels.
+// ---------------------------------------------------------------------------
+__global__ void mlp_start_kernel(int B, int n, int Np1, const double* y0, double* y_out,
+                                 double* yi, int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < B * n) {
+    const int b = i / n, s = i % n;
+    y_out[static_cast<size_t>(b) * Np1 * n + s] = y0[i];
+    yi[i] = y0[i];
+  }
+  if (i < B) status[i] = 0;
+}
+
+__global__ void mlp_chunk_init_kernel(int B, int n, int c, double* dy, int* active,
+                                      unsigned long long* norm, int* iters) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < B * c * n) dy[i] = 0.0;  // Sec. 2.3 guess dy = 0
+  if (i < B) {
+    active[i] = 1;
+    norm[i] = 0ull;
+    iters[i] = 0;
+  }
+}
+
+// Write y_{i0+1..i0+L} = y_i + dy and carry y_{i0+L}; one block per series.
+__global__ void mlp_store_kernel(int n, int L, int c, int Np1, int i0, const double* dy,
+                                 double* yi, double* y_out, const int* iters, int* stats) {
+  const int b = blockIdx.x;
+  const double* dyb = dy + static_cast<size_t>(b) * c * n;
+  double* yb = y_out + static_cast<size_t>(b) * Np1 * n;
+  for (int e = threadIdx.x; e < L * n; e += blockDim.x) {
+    const int j = e / n, s = e % n;
+    yb[static_cast<size_t>(i0 + 1 + j) * n + s] = yi[b * n + s] + dyb[e];
+  }
+  __syncthreads();
+  if (threadIdx.x < n) yi[b * n + threadIdx.x] += dyb[(L - 1) * n + threadIdx.x];
+  if (threadIdx.x == 0 && stats) {
+    int* o = stats + b * 4;
+    o[0] += iters[b];
+    o[1] += 1;
+    o[3] = max(o[3], iters[b]);
+  }
+}
+
+__global__ void mlp_worst_kernel(int B, const int* status, int* series_status, int* worst) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  if (series_status) series_status[b] = status[b];
+  if (status[b]) atomicMax(worst, status[b]);
+}
+
+// carry a_{i0+1} (row L-1) to the next (earlier) chunk
+__global__ void mlp_carry_kernel(int B, int n, int L, int c, const double* av, double* carry) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < B * n) carry[i] = av[(static_cast<size_t>(i / n) * c + (L - 1)) * n + (i % n)];
+}
+
+__global__ void mlp_adjoint_end_kernel(int B, int n, int Np1, const double* carry, const double* g,
+                                       double* dy0, const double* acc, double* dparams, int P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (dy0 && i < B * n) dy0[i] = carry[i] + g[static_cast<size_t>(i / n) * Np1 * n + (i % n)];
+  if (i < P) dparams[i] = acc[i];
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+size_t al(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+struct Ws {
+  float* Wf;
+  double *yi, *dy, *R, *carry, *acc, *act, *del, *norm0;
+  double* dv;
+  void* M;
+  unsigned long long* norm;
+  int *active, *status, *iters, *remaining, *worst;
+  size_t total;
+};
+
+Ws carve(char* base, int B, int c, const MlpDims& d, int precision, bool adjoint_bufs) {
+  Ws w{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + off : nullptr;
+    off += al(bytes);
+    return p;
+  };
+  const size_t bc = static_cast<size_t>(B) * c;
+  const size_t tsz = precision == kPrecFp64 ? sizeof(double) : sizeof(float);
+  w.worst = reinterpret_cast<int*>(take(sizeof(int)));
+  w.remaining = reinterpret_cast<int*>(take(sizeof(int)));
+  w.Wf = reinterpret_cast<float*>(take(sizeof(float) * d.P));
+  w.yi = reinterpret_cast<double*>(take(sizeof(double) * B * d.n));
+  w.carry = reinterpret_cast<double*>(take(sizeof(double) * B * d.n));
+  w.norm = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * B));
+  w.norm0 = reinterpret_cast<double*>(take(sizeof(double) * B));
+  w.active = reinterpret_cast<int*>(take(sizeof(int) * B));
+  w.status = reinterpret_cast<int*>(take(sizeof(int) * B));
+  w.iters = reinterpret_cast<int*>(take(sizeof(int) * B));
+  w.dy = reinterpret_cast<double*>(take(sizeof(double) * bc * d.n));
+  w.R = reinterpret_cast<double*>(take(sizeof(double) * bc * d.n));
+  w.dv = reinterpret_cast<double*>(take(sizeof(double) * bc * (d.h1 + d.h2 + d.n)));
+  w.M = take(tsz * bc * d.n * d.n);
+  if (adjoint_bufs) {
+    w.acc = reinterpret_cast<double*>(take(sizeof(double) * d.P));
+    w.act = reinterpret_cast<double*>(take(sizeof(double) * bc * (d.n + d.h1 + d.h2 + 3)));
+    w.del = reinterpret_cast<double*>(take(sizeof(double) * bc * (d.h1 + d.h2 + d.n)));
+  }
+  w.total = off;
+  return w;
+}
+
+MlpDims dims_of(int n, int h1, int h2) {
+  MlpDims d;
+  d.n = n;
+  d.h1 = h1;
+  d.h2 = h2;
+  d.P = h1 * n + h1 + h2 * h1 + h2 + n * h2 + n;
+  return d;
+}
+
+constexpr int kResTP = 64;  // pairs per residual tile
+constexpr int kVjpTP = 32;  // pairs per vector-Jacobian tile
+
+size_t residual_smem(const MlpDims& d) {
+  return sizeof(double) * (2 * d.n + d.h1 + d.h2) * kResTP;
+}
+size_t vjp_smem(const MlpDims& d) {
+  return sizeof(double) * (2 * d.n + 2 * d.h1 + 2 * d.h2) * kVjpTP;
+}
+
+// pairs per Jacobian tile: about 32k bytes of U per block, at least 1
+int blocks_tp(const MlpDims& d, int precision) {
+  const int tsz = precision == kPrecFp64 ? 8 : 4;
+  const int hmax = d.h1 > d.h2 ? d.h1 : d.h2;
+  int nt = 32768 / (hmax * tsz);
+  int tp = nt / d.n;
+  return tp < 1 ? 1 : (tp > 64 ? 64 : tp);
+}
+size_t blocks_smem(const MlpDims& d, int precision, int tp) {
+  const size_t tsz = precision == kPrecFp64 ? 8 : 4;
+  return tsz * (static_cast<size_t>(d.h1 + d.h2) * tp * d.n + static_cast<size_t>(tp) * d.n * 2 * d.n + tp);
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(bytes));
+}
+
+template <int KIND>
+cudaError_t launch_residual(const ResidualArgs& r, cudaStream_t s) {
+  const size_t sm = residual_smem(r.d);
+  cudaError_t e = set_smem(mlp_residual_kernel<KIND, kResTP>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((r.L + kResTP - 1) / kResTP, r.B);
+  mlp_residual_kernel<KIND, kResTP><<<grid, kTileThreads, sm, s>>>(r);
+  return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch_vjp(const VjpArgs& v, cudaStream_t s) {
+  const size_t sm = vjp_smem(v.d);
+  cudaError_t e = set_smem(mlp_vjp_kernel<KIND, kVjpTP>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((v.L + kVjpTP - 1) / kVjpTP, v.B);
+  mlp_vjp_kernel<KIND, kVjpTP><<<grid, kTileThreads, sm, s>>>(v);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_blocks(const BlocksArgs& bk, int precision, cudaStream_t s) {
+  const int tp = blocks_tp(bk.d, precision);
+  const size_t sm = blocks_smem(bk.d, precision, tp);
+  cudaError_t e = set_smem(mlp_blocks_kernel<T>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((bk.L + tp - 1) / tp, bk.B);
+  mlp_blocks_kernel<T><<<grid, kTileThreads, sm, s>>>(bk, tp);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_chain(const ChainArgs& ch, cudaStream_t s) {
+  mlp_chain_kernel<T><<<(ch.B + 3) / 4, 128, 0, s>>>(ch);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool mlp_supported(int n, int h1, int h2) {
+  return n >= 4 && n <= 32 && n % 4 == 0 && h1 >= 4 && h1 <= 128 && h1 % 4 == 0 && h2 >= 4 &&
+         h2 <= 128 && h2 % 4 == 0;
+}
+
+size_t mlp_workspace_bytes(int n, int h1, int h2, int B, int chunk, int precision) {
+  return carve(nullptr, B, chunk, dims_of(n, h1, h2), precision, true).total;
+}
+
+#define TVI_TRY(x)                          \
+  do {                                      \
+    cudaError_t e_ = (x);                   \
+    if (e_ != cudaSuccess) return e_;       \
+  } while (0)
+
+cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const FwdArgs& a,
+                        void* workspace, cudaStream_t s, int* host_worst) {
+  const MlpDims d = dims_of(n, h1, h2);
+  const int B = a.B, N = a.N, c = a.chunk;
+  Ws w = carve(static_cast<char*>(workspace), B, c, d, precision, false);
+  TVI_TRY(cudaMemsetAsync(w.worst, 0, sizeof(int), s));
+  convert_weights_kernel<<<(d.P + 255) / 256, 256, 0, s>>>(a.params, w.Wf, d.P);
+  mlp_start_kernel<<<(B * n + 255) / 256, 256, 0, s>>>(B, n, N + 1, a.y0, a.y_out, w.yi, w.status);
+  TVI_TRY(cudaGetLastError());
+  if (a.stats) TVI_TRY(cudaMemsetAsync(a.stats, 0, sizeof(int) * 4 * B, s));
+  for (int i0 = 0; i0 < N; i0 += c) {
+    const int L = (N - i0 < c) ? N - i0 : c;
+    mlp_chunk_init_kernel<<<(B * c * n + 255) / 256, 256, 0, s>>>(B, n, c, w.dy, w.active, w.norm,
+                                                                   w.iters);
+    TVI_TRY(cudaGetLastError());
+    for (int it = 0;; ++it) {
+      ResidualArgs r{};
+      r.d = d; r.B = B; r.N = N; r.i0 = i0; r.L = L; r.c = c; r.reverse = 0;
+      r.times = a.times; r.lengths = a.lengths; r.params = a.params; r.yi = w.yi; r.dy = w.dy;
+      r.R = w.R; r.dv = w.dv; r.norm = w.norm; r.active = w.active;
+      TVI_TRY(kind == kKindMlpTanh ? launch_residual<kKindMlpTanh>(r, s)
+                                   : launch_residual<kKindMlpSilu>(r, s));
+      TVI_TRY(cudaMemsetAsync(w.remaining, 0, sizeof(int), s));
+      CheckArgs ck{B, it, a.max_iter, a.tol_abs, a.tol_rel, w.norm, w.norm0, w.active, w.status,
+                   w.iters, w.remaining};
+      mlp_check_kernel<<<(B + 127) / 128, 128, 0, s>>>(ck);
+      TVI_TRY(cudaGetLastError());
+      int remaining = 0;
+      TVI_TRY(cudaMemcpyAsync(&remaining, w.remaining, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TVI_TRY(cudaStreamSynchronize(s));
+      if (remaining == 0) break;
+      BlocksArgs bk{};
+      bk.d = d; bk.B = B; bk.N = N; bk.i0 = i0; bk.L = L; bk.c = c; bk.reverse = 0;
+      bk.times = a.times; bk.lengths = a.lengths; bk.Wf = w.Wf; bk.Wd = a.params; bk.dv = w.dv;
+      bk.active = w.active; bk.M = w.M;
+      ChainArgs ch{};
+      ch.B = B; ch.n = n; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 0; ch.M = w.M;
+      ch.rhs_buf = w.R; ch.active = w.active; ch.x = w.dy; ch.mode = 0;
+      if (precision == kPrecFp64) {
+        TVI_TRY(launch_blocks<double>(bk, precision, s));
+        TVI_TRY(launch_chain<double>(ch, s));
+      } else {
+        TVI_TRY(launch_blocks<float>(bk, precision, s));
+        TVI_TRY(launch_chain<float>(ch, s));
+      }
+    }
+    mlp_store_kernel<<<B, 128, 0, s>>>(n, L, c, N + 1, i0, w.dy, w.yi, a.y_out, w.iters, a.stats);
+    TVI_TRY(cudaGetLastError());
+  }
+  mlp_worst_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, w.status, a.series_status, w.worst);
+  TVI_TRY(cudaGetLastError());
+  if (host_worst) {
+    TVI_TRY(cudaMemcpyAsync(host_worst, w.worst, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TVI_TRY(cudaStreamSynchronize(s));
+  }
+  return cudaSuccess;
+}
+
+cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const AdjArgs& a,
+                        void* workspace, cudaStream_t s) {
+  const MlpDims d = dims_of(n, h1, h2);
+  const int B = a.B, N = a.N, c = a.chunk;
+  Ws w = carve(static_cast<char*>(workspace), B, c, d, precision, true);
+  convert_weights_kernel<<<(d.P + 255) / 256, 256, 0, s>>>(a.params, w.Wf, d.P);
+  TVI_TRY(cudaMemsetAsync(w.carry, 0, sizeof(double) * B * n, s));  // a_{N+1} = 0
+  TVI_TRY(cudaMemsetAsync(w.acc, 0, sizeof(double) * d.P, s));
+  const int refine = precision == kPrecFp64 ? 0 : a.refine;
+  const int nch = (N + c - 1) / c;
+  for (int ci = nch - 1; ci >= 0; --ci) {
+    const int i0 = ci * c;
+    const int L = (N - i0 < c) ? N - i0 : c;
+    // activation derivatives at the stored trajectory, rows in reverse step order
+    ResidualArgs r{};
+    r.d = d; r.B = B; r.N = N; r.i0 = i0; r.L = L; r.c = c; r.reverse = 1;
+    r.times = a.times; r.lengths = a.lengths; r.params = a.params; r.ytraj = a.y; r.dv = w.dv;
+    TVI_TRY(kind == kKindMlpTanh ? launch_residual<kKindMlpTanh>(r, s)
+                                 : launch_residual<kKindMlpSilu>(r, s));
+    BlocksArgs bk{};
+    bk.d = d; bk.B = B; bk.N = N; bk.i0 = i0; bk.L = L; bk.c = c; bk.reverse = 1;
+    bk.times = a.times; bk.lengths = a.lengths; bk.Wf = w.Wf; bk.Wd = a.params; bk.dv = w.dv;
+    bk.M = w.M;
+    // a_j = A^-T (a_{j-1} + g_k), a_{-1} = carry
+    ChainArgs ch{};
+    ch.B = B; ch.n = n; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 1; ch.M = w.M;
+    ch.rhs_traj = a.grad_out; ch.x_init = w.carry; ch.x = w.dy; ch.mode = 1;
+    if (precision == kPrecFp64) {
+      TVI_TRY(launch_blocks<double>(bk, precision, s));
+      TVI_TRY(launch_chain<double>(ch, s));
+    } else {
+      TVI_TRY(launch_blocks<float>(bk, precision, s));
+      TVI_TRY(launch_chain<float>(ch, s));
+    }
+    VjpArgs v{};
+    v.d = d; v.B = B; v.N = N; v.i0 = i0; v.L = L; v.c = c; v.times = a.times;
+    v.lengths = a.lengths; v.params = a.params; v.ytraj = a.y; v.g = a.grad_out;
+    v.carry = w.carry; v.av = w.dy;
+    for (int it = 0; it < refine; ++it) {
+      v.res = w.R;
+      v.act = nullptr;
+      v.del = nullptr;
+      TVI_TRY(kind == kKindMlpTanh ? launch_vjp<kKindMlpTanh>(v, s) : launch_vjp<kKindMlpSilu>(v, s));
+      ChainArgs cr = ch;
+      cr.rhs_traj = nullptr;
+      cr.rhs_buf = w.R;
+      cr.x_init = nullptr;
+      cr.mode = 2;  // a += correction
+      TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(cr, s) : launch_chain<float>(cr, s));
+    }
+    // parameter gradient factors at the final a, then the tiled sums
+    v.res = nullptr;
+    v.act = w.act;
+    v.del = w.del;
+    TVI_TRY(kind == kKindMlpTanh ? launch_vjp<kKindMlpTanh>(v, s) : launch_vjp<kKindMlpSilu>(v, s));
+    ParamArgs pa{d, B, L, c, w.act, w.del, w.acc};
+    if (precision == kPrecFp64)
+      mlp_param_grad_kernel<double><<<param_grad_tiles(d), 256, 0, s>>>(pa);
+    else
+      mlp_param_grad_kernel<float><<<param_grad_tiles(d), 256, 0, s>>>(pa);
+    TVI_TRY(cudaGetLastError());
+    mlp_carry_kernel<<<(B * n + 255) / 256, 256, 0, s>>>(B, n, L, c, w.dy, w.carry);
+    TVI_TRY(cudaGetLastError());
+  }
+  const int cnt = (B * n > d.P) ? B * n : d.P;
+  mlp_adjoint_end_kernel<<<(cnt + 255) / 256, 256, 0, s>>>(B, n, N + 1, w.carry, a.grad_out, a.dy0,
+                                                          w.acc, a.dparams, d.P);
+  return cudaGetLastError();
+}
+
+}  // namespace tvi

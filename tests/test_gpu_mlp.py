@@ -1,0 +1,142 @@
+"""GPU parity of the neural-ODE (MLP right-hand side) path with the CPU FP64
+oracle, through the C ABI.
+
+Gates (the benchmark spec): 1e-10 relative with FP64 blocks, 1e-5 with FP32 blocks,
+per series on the trajectory (max_k |y - y_ref|_inf / max_k |y_ref|_inf) and per
+tensor on the gradients.  The tanh/SiLU networks here are smooth and bounded,
+so the problems are well conditioned and the gates apply directly; the
+trajectories are compared at a tight Newton tolerance (1e-12) so that both
+sides solve the same discrete equations to well below the gate.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import Model as OModel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GATE = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def tvi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2310_08649_gb300 as tvi
+    from paper_2310_08649_gb300 import build
+    build.build()
+    return tvi
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def relerr_series(a, b):
+    return np.abs(a - b).max(axis=(1, 2)) / np.maximum(np.abs(b).max(axis=(1, 2)), 1e-300)
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def gpu_forward(tvi, w, chunk, precision, tol, lengths=None):
+    m = tvi.Model.from_spec(w["spec"])
+    o = tvi.Options(chunk=chunk, tol_abs=tol, precision=precision, max_iter=60)
+    lens = None if lengths is None else dev(lengths, torch.int32)
+    y, stats, st, rc = tvi.integrate(m, o, dev(w["y0"]), dev(w["times"]), dev(w["params"]), lens,
+                                     raise_on_status=False)
+    torch.cuda.synchronize()
+    return y.cpu().numpy(), stats.cpu().numpy(), st.cpu().numpy(), rc
+
+
+def gpu_adjoint(tvi, w, chunk, precision, y, g, lengths=None, refine=2):
+    m = tvi.Model.from_spec(w["spec"])
+    o = tvi.Options(chunk=chunk, precision=precision, adjoint_refine=refine)
+    lens = None if lengths is None else dev(lengths, torch.int32)
+    dp, dy0 = tvi.adjoint(m, o, dev(w["times"]), dev(w["params"]), dev(y), dev(g), lens)
+    torch.cuda.synchronize()
+    return dp.cpu().numpy(), dy0.cpu().numpy()
+
+
+@pytest.mark.parametrize("act", ["tanh", "silu"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("chunk", [1, 7, 40, 120, 500])
+def test_small_mlp_forward_and_adjoint(tvi, oracle_lib, act, precision, chunk):
+    w = workloads.mlp_ode(B=3, N=120, n=4, hidden=(8, 12), act=act, t_end=3.0, seed=61)
+    m = OModel.from_spec(w["spec"])
+    ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], tol_abs=1e-12)
+    assert not st.any()
+    y, stats, status, rc = gpu_forward(tvi, w, chunk, precision, 1e-12)
+    assert rc == 0 and not status.any()
+    assert relerr_series(y, ref).max() <= GATE[precision]
+    g = workloads.random_grad_out(62, 3, 120, 4)
+    dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g)
+    dp, dy0 = gpu_adjoint(tvi, w, chunk, precision, ref, g)
+    assert relerr(dp, dp_ref) <= GATE[precision]
+    assert relerr(dy0, dy0_ref) <= GATE[precision]
+
+
+@pytest.fixture(scope="module")
+def node16(oracle_lib):
+    """The n = 16 neural-ODE workload: MLP 16-64-64-16 tanh, 64 series x 2000 steps."""
+    w = workloads.mlp_ode()
+    m = OModel.from_spec(w["spec"])
+    ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], tol_abs=1e-12)
+    assert not st.any()
+    g = workloads.random_grad_out(63, 64, 2000, 16)
+    dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g)
+    # forward error that stopping Newton at residual 1e-12 can leave over 2000 steps
+    est = oracle_lib.forward_error_estimate(m, w["times"], w["params"], ref, 1e-12)
+    return w, ref, g, dp_ref, dy0_ref, est
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_node16_full_size(tvi, node16, precision):
+    w, ref, g, dp_ref, dy0_ref, est = node16
+    y, stats, status, rc = gpu_forward(tvi, w, 200, precision, 1e-12)
+    assert rc == 0 and not status.any()
+    err = relerr_series(y, ref)
+    assert np.all(err <= np.maximum(GATE[precision], 10.0 * est)), (err.max(), est.max())
+    dp, dy0 = gpu_adjoint(tvi, w, 200, precision, ref, g)
+    assert relerr(dp, dp_ref) <= GATE[precision]
+    assert relerr(dy0, dy0_ref) <= GATE[precision]
+
+
+def test_node32_silu_padded_lengths(tvi, oracle_lib):
+    """n = 32 SiLU network (MLP 32-128-128-32), per-series lengths padded into one
+    launch (dt = 0 past each length), reduced batch so the oracle stays quick."""
+    w = workloads.mlp_large(B=4, N=1200, lengths_range=(200, 1200))
+    m = OModel.from_spec(w["spec"])
+    lens = w["lengths"]
+    ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], lengths=lens,
+                                    tol_abs=1e-12)
+    assert not st.any()
+    g = workloads.random_grad_out(64, 4, 1200, 32)
+    for b, L in enumerate(lens):
+        g[b, L + 1:] = 0.0  # masked loss past each length
+    dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g, lengths=lens)
+    for precision in ("fp32", "fp64"):
+        y, _, status, rc = gpu_forward(tvi, w, 500, precision, 1e-12, lengths=lens)
+        assert rc == 0 and not status.any()
+        for b, L in enumerate(lens):
+            assert np.all(y[b, L + 1:] == y[b, L])
+        assert relerr_series(y, ref).max() <= GATE[precision]
+        dp, dy0 = gpu_adjoint(tvi, w, 500, precision, ref, g, lengths=lens)
+        assert relerr(dp, dp_ref) <= GATE[precision]
+        assert relerr(dy0, dy0_ref) <= GATE[precision]
+
+
+def test_mlp_status_and_rejections(tvi):
+    import paper_2310_08649_gb300._lib as L
+    w = workloads.mlp_ode(B=3, N=50, n=4, hidden=(8, 8), seed=65)
+    p = w["params"].copy()
+    p[5] = np.nan
+    _, _, status, rc = gpu_forward(tvi, dict(w, params=p), 10, "fp32", 1e-10)
+    assert rc == L.TVI_ENONFINITE and np.all(status == 2)
+    bad = workloads.mlp_ode(B=2, N=10, n=4, hidden=(6, 8), seed=66)
+    with pytest.raises(L.TviError):  # hidden width not a multiple of 4
+        tvi.integrate(tvi.Model.from_spec(bad["spec"]), tvi.Options(chunk=5), dev(bad["y0"]),
+                      dev(bad["times"]), dev(bad["params"]))
