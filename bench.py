@@ -1,12 +1,16 @@
 #!/usr/bin/env python
 """Throughput of chunked backward-Euler forward + adjoint, in series*steps/s.
 
-Workload (default): stiff van der Pol, n = 2, 128 series x 10,000 log-spaced
-steps per series, Newton tolerance 1e-10; chunk 1000 with FP32 blocks and
-cyclic reduction plus FP64 residuals.  One step = tvi_integrate + tvi_adjoint
-over the whole batch.  The same library with chunk = 1 and FP64 blocks (the
-sequential scheme, same Newton tolerance, same launch strategy) is timed in
-the same run for the chunked/sequential ratio.
+Default workload: stiff van der Pol, n = 2, 128 series x 10,000 log-spaced steps
+per series, Newton tolerance 1e-10; chunk 1000 with FP32 blocks and cyclic
+reduction plus FP64 residuals.  One step = tvi_integrate + tvi_adjoint over the
+whole batch.  The same library with chunk = 1 and FP64 blocks (the sequential
+scheme, same Newton tolerance, same launch strategy) is timed in the same run
+for the chunked/sequential ratio.
+
+--workload node16 / node32 time the neural-ODE workloads instead (MLP
+16-64-64-16 tanh, 64 x 2000; MLP 32-128-128-32 SiLU, 512 x 20,000 padded with
+per-series lengths uniform in [2000, 20000]; throughput counts real steps).
 
 Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle on
 the same workload instead.
@@ -29,7 +33,13 @@ import workloads  # noqa: E402
 
 METRIC = "series*steps/s fwd+adjoint vs chunk=1 sequential on GB300, same Newton tol"
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 rate (no measured FP64 peak is provided)
+FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 rate (recipe table); no measured FP64 peak given
+
+WORKLOADS = {
+    "vdp": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 128, "N": 10000},
+    "node16": {"chunk": 200, "precision": "fp32", "tol": 1e-8, "B": 64, "N": 2000},
+    "node32": {"chunk": 1000, "precision": "fp32", "tol": 1e-8, "B": 512, "N": 20000},
+}
 
 
 def parse():
@@ -38,17 +48,24 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--chunk", type=int, default=1000)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--workload", default="vdp", choices=sorted(WORKLOADS))
+    ap.add_argument("--chunk", type=int, default=None)
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
+    ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--rpt", type=int, default=0, help="steps per thread (0 = library default)")
-    ap.add_argument("--B", type=int, default=128)
-    ap.add_argument("--N", type=int, default=10000)
+    ap.add_argument("--B", type=int, default=None)
+    ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--baseline-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-chunk1", action="store_true")
-    return ap.parse_args()
+    args = ap.parse_args()
+    for k, v in WORKLOADS[args.workload].items():
+        if getattr(args, k) is None:
+            setattr(args, k, v)
+    if args.workload != "vdp":
+        args.no_chunk1 = True  # the one-step MLP scheme reads status back every Newton update
+    return args
 
 
 def dist_env():
@@ -56,9 +73,34 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
+def make_workload(args, rank=0):
+    """(inputs, dL/dy) for the chosen workload; ranks draw their own batches."""
+    if args.workload == "vdp":
+        w = workloads.vdp(B=args.B, N=args.N, seed=workloads.SEED_VDP + 1000 * rank)
+    elif args.workload == "node16":
+        w = workloads.mlp_ode(B=args.B, N=args.N, seed=workloads.SEED_MLP + 1000 * rank)
+    else:
+        w = workloads.mlp_large(B=args.B, N=args.N, seed=workloads.SEED_MLP_LARGE + 1000 * rank,
+                                lengths_range=(min(2000, args.N), args.N))
+    n = w["spec"]["n"]
+    g = workloads.random_grad_out(2002 + rank, args.B, args.N, n)
+    if w["lengths"] is not None:
+        for b, L in enumerate(w["lengths"]):
+            g[b, L + 1:] = 0.0  # masked loss past each series' length
+    return w, g
+
+
+def real_steps(w):
+    B, Np1 = w["times"].shape
+    return int(np.sum(w["lengths"])) if w["lengths"] is not None else B * (Np1 - 1)
+
+
 def workload_config(args):
-    return {"workload": f"van der Pol n=2, {args.B} series x {args.N} log-spaced steps, "
-                        f"mu log-uniform [10,1000], Newton tol {args.tol:g}",
+    desc = {"vdp": "van der Pol n=2, mu log-uniform [10,1000], log-spaced steps",
+            "node16": "neural ODE n=16, MLP 16-64-64-16 tanh, uniform steps on [0,10]",
+            "node32": "neural ODE n=32, MLP 32-128-128-32 SiLU, per-series lengths "
+                      "U[2000,N] padded, uniform steps on [0,10]"}[args.workload]
+    return {"workload": f"{desc}; {args.B} series x {args.N} steps, Newton tol {args.tol:g}",
             "B": args.B, "N": args.N, "chunk": args.chunk,
             "blocks": args.precision, "residual": "fp64", "tol_abs": args.tol}
 
@@ -67,45 +109,62 @@ def workload_config(args):
 # CPU oracle timing (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
 def time_oracle(w, g, tol, seconds, min_reps=1):
+    """Oracle forward + adjoint on the whole workload, or on its first S series
+    when the whole one would take longer than `seconds`; returns (real
+    series*steps per second, description of the sample, cores)."""
     import oracle
     m = oracle.Model.from_spec(w["spec"])
-    B, N = w["times"].shape[0], w["times"].shape[1] - 1
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        y, _, _ = oracle.forward(m, w["y0"], w["times"], w["params"], tol_abs=tol, max_iter=100)
-        oracle.adjoint(m, w["times"], w["params"], y, g)
+    B = w["times"].shape[0]
+
+    def run(S):
+        lens = None if w["lengths"] is None else w["lengths"][:S]
+        p = w["params"][:S] if m.per_series else w["params"]
+        t0 = time.perf_counter()
+        y, _, _ = oracle.forward(m, w["y0"][:S], w["times"][:S], p, lengths=lens, tol_abs=tol,
+                                 max_iter=100)
+        oracle.adjoint(m, w["times"][:S], p, y, g[:S], lengths=lens)
+        return time.perf_counter() - t0
+
+    cores = oracle.max_threads()
+    S = min(B, max(cores, 1))
+    el = run(S)
+    while S < B and el < seconds / 4:
+        S = min(B, S * 4)
+        el = run(S)
+    sub = dict(w, lengths=None if w["lengths"] is None else w["lengths"][:S],
+               times=w["times"][:S])
+    steps = real_steps(sub)
+    reps, total = 1, el
+    while total < seconds or reps < min_reps:
+        total += run(S)
         reps += 1
-        el = time.perf_counter() - t0
-        if reps >= min_reps and el >= seconds:
-            break
-    return B * N * reps / el, reps, el, oracle.max_threads()
+    sample = (f"{'whole workload' if S == B else f'first {S} of {B} series'}, "
+              f"{reps} forward+adjoint passes, {total:.1f} s")
+    return steps * reps / total, sample, cores, reps, total
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = workloads.vdp(B=args.B, N=args.N)
-    g = workloads.random_grad_out(2002, args.B, args.N, 2)
+    w, g = make_workload(args)
     per_step = max(args.cpu_seconds / max(args.steps, 1), 0.0)
     for _ in range(args.warmup):
         time_oracle(w, g, args.tol, 0.0)
-    vals, t_total = [], 0.0
-    reps_total = 0
+    t_total, units = 0.0, 0.0
+    sample, cores = "", 0
     for _ in range(args.steps):
-        v, reps, el, cores = time_oracle(w, g, args.tol, per_step)
-        vals.append(v)
+        v, sample, cores, reps, el = time_oracle(w, g, args.tol, per_step)
         t_total += el
-        reps_total += reps
-    value = args.B * args.N * reps_total / t_total
+        units += v * el
+    value = units / t_total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "series*steps/s",
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args),
             "cpu_baseline": {"value": value, "unit": "series*steps/s", "cores": cores,
-                             "kind": "oracle",
-                             "sample": f"whole workload, {reps_total} forward+adjoint passes"},
+                             "kind": "oracle", "sample": sample + " per step"},
             "e2e": {"value": value, "unit": "series*steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -170,6 +229,46 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# Roofline of the dominant kernel (FP64 pipe)
+# ---------------------------------------------------------------------------
+def roofline(args, w, stats, fwd_ms, adj_ms, refine):
+    """Both paths are bound by the FP64 pipe (the FP64 residual).  Every FP64 add,
+    multiply or FMA takes one FP64 issue slot, and the nominal 1.25 TFLOP/s counts
+    an FMA as 2 flops; achieved is reported FMA-equivalent (2 x FP64 operations)
+    so the fraction is the share of FP64 issue slots doing algorithmic work.
+    A chunk with u Newton updates evaluates the residual u + 1 times; work of
+    abandoned chunk attempts is not counted."""
+    B, Np1 = w["times"].shape
+    N = Np1 - 1
+    upd = stats[:, 0].astype(np.float64)
+    nchk = stats[:, 1].astype(np.float64)
+    spc = N / np.maximum(nchk, 1)  # steps per solved chunk
+    if args.workload == "vdp":
+        # residual y = y_i + dy (2), h (3), R (4) = 9; update dy -= d: 2
+        fwd_ops = float(np.sum(((upd + nchk) * 9.0 + upd * 2.0) * spc))
+        # adjoint per step: per refinement sweep 14, parameter VJP 4
+        adj_ops = float(B * N * (refine * 14.0 + 4.0))
+        names = ("forward_small_kernel<vdp,fp32>", "adjoint_small_kernel<vdp,fp32>")
+    else:
+        n, (h1, h2) = w["spec"]["n"], w["spec"]["hidden"]
+        fma = n * h1 + h1 * h2 + h2 * n  # FP64 FMAs of one MLP evaluation (activations not counted)
+        fwd_ops = float(np.sum((upd + nchk) * spc) * fma)
+        # adjoint: FP64 forward + backward per refinement sweep and for the gradient factors
+        adj_ops = float(B * N * (refine + 1) * 2 * fma)
+        names = ("tvi_integrate (MLP path: FP64 residual kernel dominant)",
+                 "tvi_adjoint (MLP path: FP64 VJP kernel dominant)")
+    name, ops, ms = (names[0], fwd_ops, fwd_ms) if fwd_ms >= adj_ms else (names[1], adj_ops, adj_ms)
+    achieved = 2.0 * ops / (ms / 1e3) / 1e12
+    return {"kernel": name, "bound": "alu", "pipe": "fp64", "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "counting": "FMA-equivalent: 2 x FP64 pipe operations (add, mul, fma)",
+            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table); "
+                           "an FMA loop measured 1.20 TFLOP/s on this part",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "fwd_ms": fwd_ms, "adj_ms": adj_ms, "fwd_fp64_ops": fwd_ops, "adj_fp64_ops": adj_ops}
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -186,28 +285,29 @@ def run_ours(args):
 
     dev = torch.device("cuda", local)
     # weak scaling: every rank integrates its own batch of the same shape
-    w = workloads.vdp(B=args.B, N=args.N, seed=workloads.SEED_VDP + 1000 * rank)
-    g = workloads.random_grad_out(2002 + rank, args.B, args.N, 2)
-    B, N = args.B, args.N
+    w, g = make_workload(args, rank)
+    B, N, n = args.B, args.N, w["spec"]["n"]
+    units_per_step = real_steps(w)
 
     def d(a, dtype=torch.float64):
         return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).to(dev)
 
     y0, times, params, grad = d(w["y0"]), d(w["times"]), d(w["params"]), d(g)
+    lengths = None if w["lengths"] is None else d(w["lengths"], torch.int32)
     model = tvi.Model.from_spec(w["spec"])
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def make(opts):
         ws = tvi.make_workspace(model, opts, B, N, dev)
-        y = torch.empty((B, N + 1, 2), dtype=torch.float64, device=dev)
+        y = torch.empty((B, N + 1, n), dtype=torch.float64, device=dev)
         stats = torch.empty((B, 4), dtype=torch.int32, device=dev)
         st = torch.empty((B,), dtype=torch.int32, device=dev)
         dp = torch.empty_like(params)
         dy0 = torch.empty_like(y0)
         return ws, y, stats, st, dp, dy0
 
-    def timed_steps(opts, K, W, per_launch=True):
+    def timed_steps(opts, K, W):
         ws, y, stats, st, dp, dy0 = make(opts)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
                torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -215,10 +315,10 @@ def run_ours(args):
         def step(e=None):
             if e:
                 e[0].record(stream)
-            tvi.integrate(model, opts, y0, times, params, None, y, stats, st, ws, stream)
+            tvi.integrate(model, opts, y0, times, params, lengths, y, stats, st, ws, stream)
             if e:
                 e[1].record(stream)
-            tvi.adjoint(model, opts, times, params, y, grad, None, dp, dy0, ws, stream)
+            tvi.adjoint(model, opts, times, params, y, grad, lengths, dp, dy0, ws, stream)
             if e:
                 e[2].record(stream)
         for _ in range(W):
@@ -252,30 +352,33 @@ def run_ours(args):
     if world > 1:
         dist.all_reduce(total_ms, op=dist.ReduceOp.MAX)
     total_ms = float(total_ms.item())
-    units = B * N * world * args.steps
-    value = units / (total_ms / 1e3)
+    value = units_per_step * world * args.steps / (total_ms / 1e3)
 
     # end-to-end through the public API: pinned host inputs in, gradients out
-    h = {k: torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64).pin_memory()
-         for k, v in (("y0", w["y0"]), ("times", w["times"]), ("params", w["params"]),
-                      ("grad", g))}
+    host_in = [("y0", w["y0"], torch.float64), ("times", w["times"], torch.float64),
+               ("params", w["params"], torch.float64), ("grad", g, torch.float64)]
+    if w["lengths"] is not None:
+        host_in.append(("lengths", w["lengths"], torch.int32))
+    h = {k: torch.as_tensor(np.ascontiguousarray(v), dtype=dt).pin_memory()
+         for k, v, dt in host_in}
     ws, y, stats, st, dp, dy0 = make(opts)
     dev_in = {k: torch.empty_like(v, device=dev) for k, v in h.items()}
     h_dp = torch.empty(dp.shape, dtype=torch.float64).pin_memory()
     h_dy0 = torch.empty(dy0.shape, dtype=torch.float64).pin_memory()
-    h2d = sum(v.numel() * 8 for v in h.values())
+    h2d = sum(v.numel() * v.element_size() for v in h.values())
     d2h = (dp.numel() + dy0.numel()) * 8
 
     def e2e_step():
         for k in h:
             dev_in[k].copy_(h[k], non_blocking=True)
-        tvi.integrate(model, opts, dev_in["y0"], dev_in["times"], dev_in["params"], None, y,
+        lens = dev_in.get("lengths")
+        tvi.integrate(model, opts, dev_in["y0"], dev_in["times"], dev_in["params"], lens, y,
                       stats, st, ws, stream)
-        tvi.adjoint(model, opts, dev_in["times"], dev_in["params"], y, dev_in["grad"], None, dp,
+        tvi.adjoint(model, opts, dev_in["times"], dev_in["params"], y, dev_in["grad"], lens, dp,
                     dy0, ws, stream)
         h_dp.copy_(dp, non_blocking=True)
         h_dy0.copy_(dy0, non_blocking=True)
-    for _ in range(args.warmup):
+    for _ in range(min(args.warmup, 3)):
         e2e_step()
     torch.cuda.synchronize()
     K2 = max(1, min(args.steps, 50))
@@ -288,67 +391,43 @@ def run_ours(args):
         b.record(stream)
         b.synchronize()
         e_ms += a.elapsed_time(b)
-    e2e_value = B * N * K2 / (e_ms / 1e3)
+    e2e_value = units_per_step * K2 / (e_ms / 1e3)
 
     # chunk = 1 sequential FP64 scheme: same library, tolerance and launch strategy
     chunk1 = None
     if not args.no_chunk1:
         o1 = tvi.Options(chunk=1, tol_abs=args.tol, precision="fp64", sync_status=False)
         r1 = timed_steps(o1, args.baseline_steps, 1)
-        v1 = B * N * args.baseline_steps / (r1["total_ms"] / 1e3)
+        v1 = units_per_step * args.baseline_steps / (r1["total_ms"] / 1e3)
         chunk1 = {"value": v1, "ms_per_step": r1["total_ms"] / args.baseline_steps,
                   "fwd_ms": float(np.mean(r1["fwd_ms"])), "adj_ms": float(np.mean(r1["adj_ms"])),
                   "chunk": 1, "blocks": "fp64", "ratio": value / v1}
     clocks.stop()
     clk = clocks.summary(res["t0"], res["t1"])
 
-    # Roofline of the dominant kernel.  Both kernels are bound by the FP64 pipe (the
-    # FP64 residual); every FP64 add, multiply or FMA takes one FP64 issue slot, and
-    # the nominal 1.25 TFLOP/s counts an FMA as 2 flops, so the pipe peak is
-    # 0.625 T FP64 operations/s.  Algorithmic FP64 operations per step and Newton pass:
-    #   residual  y = y_i + dy (2), h (3), R = dy - dy_prev - dt h (4)       = 9
-    #   update    dy -= d                                                  = 2
-    # A chunk with u updates evaluates the residual u + 1 times (the last confirms
-    # convergence).  Work of abandoned chunk attempts is not counted.
     fwd_ms, adj_ms = float(np.mean(res["fwd_ms"])), float(np.mean(res["adj_ms"]))
-    stats_np = res["stats"]
-    upd = stats_np[:, 0].astype(np.float64)
-    nchk = stats_np[:, 1].astype(np.float64)
-    steps_per_chunk = N / np.maximum(nchk, 1)
-    fwd_ops = float(np.sum(((upd + nchk) * 9.0 + upd * 2.0) * steps_per_chunk))
-    # adjoint per step: per refinement sweep g + a_next (1), A_k in FP64 (7), A^T a (4),
-    # a += x (2); parameter VJP (4)
     refine = opts.adjoint_refine if args.precision != "fp64" else 0
-    adj_ops = float(B * N * (refine * 14.0 + 4.0))
-    if fwd_ms >= adj_ms:
-        name, ops, ms = "forward_small_kernel<vdp,fp32>", fwd_ops, fwd_ms
-    else:
-        name, ops, ms = "adjoint_small_kernel<vdp,fp32>", adj_ops, adj_ms
-    # reported in FMA-equivalent TFLOP/s (2 x FP64 pipe operations) against 1.25
-    achieved = 2.0 * ops / (ms / 1e3) / 1e12
-    roofline = {"kernel": name, "bound": "alu", "pipe": "fp64", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "counting": "FMA-equivalent: 2 x FP64 pipe operations (add, mul, fma)",
-                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table); "
-                               "an FMA loop measured 1.20 TFLOP/s on this part",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "fwd_ms": fwd_ms, "adj_ms": adj_ms,
-                "fwd_fp64_ops": fwd_ops, "adj_fp64_ops": adj_ops}
+    stats_np = res["stats"]
+    roof = roofline(args, w, stats_np, fwd_ms, adj_ms, refine)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, reps, el, cores = time_oracle(w, g, args.tol, args.cpu_seconds)
+        v, sample, cores, _, _ = time_oracle(w, g, args.tol, args.cpu_seconds)
         cpu = {"value": v, "unit": "series*steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"whole workload ({B}x{N}), {reps} forward+adjoint passes, {el:.1f} s"}
+               "sample": sample}
 
     if rank == 0:
+        upd, nchk = stats_np[:, 0].astype(np.float64), stats_np[:, 1].astype(np.float64)
+        launches = 2 * args.steps if args.workload == "vdp" else None
         line = {"metric": METRIC, "value": value, "unit": "series*steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-                "data": "synthetic", "config": dict(workload_config(args),
-                                                     l2="flushed between timed steps (256 MB write)",
-                                                     parallelism=f"series replicas x{world}"),
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if args.precision == "fp32" else "f64",
+                "data": "synthetic",
+                "config": dict(workload_config(args),
+                               l2="flushed between timed steps (256 MB write)",
+                               parallelism=f"series replicas x{world}"),
                 "newton_updates_per_chunk": float(upd.sum() / max(nchk.sum(), 1)),
                 "newton_stats": {"updates_per_series_mean": float(upd.mean()),
                                  "updates_per_series_max": int(upd.max()),
@@ -356,10 +435,20 @@ def run_ours(args):
                                  "retries_total": int(stats_np[:, 2].sum()),
                                  "retries_max": int(stats_np[:, 2].max()),
                                  "max_updates_one_chunk": int(stats_np[:, 3].max())},
-                "chunk1_fp64": chunk1, "roofline": roofline, "cpu_baseline": cpu,
+                "chunk1_fp64": chunk1, "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "series*steps/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": 2 * args.steps, "clocks": clk}
+                "gpu_launches": launches, "clocks": clk}
+        if launches is None:
+            # MLP path, per step: forward 3 + per chunk (init, store) + per Newton pass
+            # (residual, check) + per update (blocks, chain); adjoint 2 + per chunk
+            # (derivatives, blocks, chain, 2 per refinement sweep, VJP, gradient, carry)
+            nch = float(np.max(nchk))
+            passes = float(np.mean(upd + nchk))  # batch passes >= mean per series
+            fwd = 3 + 2 * nch + 2 * passes + 2 * float(np.mean(upd))
+            adj = 2 + nch * (6 + 2 * refine)
+            line["gpu_launches"] = int(round(args.steps * (fwd + adj)))
+            line["gpu_launches_note"] = "MLP path: lower estimate from the Newton statistics"
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

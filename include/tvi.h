@@ -12,9 +12,11 @@
  *
  * Conventions shared by every entry point:
  *   - All array pointers are DEVICE pointers unless stated otherwise, row-major
- *     and contiguous, FP64 unless stated otherwise.  The caller owns every
- *     buffer; the library allocates no device memory and keeps no pointer after
- *     a call returns.
+ *     and contiguous, FP64 unless stated otherwise, and 16-byte aligned (as
+ *     every cudaMalloc or PyTorch allocation is; the workspace and, for the
+ *     MLP models, grad_out are checked).  The caller owns every buffer; the
+ *     library allocates no device memory and keeps no pointer after a call
+ *     returns.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
  *     enqueued on it.  A call synchronises `stream` only when it must read a
  *     result back to form its return code (see tvi_options.sync_status).
@@ -48,7 +50,8 @@ typedef enum {
  *                       ODE of Sec. 5.1.1 without forcing input).
  *   TVI_MODEL_MLP_SILU  h = W3 silu(W2 silu(W1 y + b1) + b2) + b3.
  * MLP parameters are one flat FP64 vector W1[h1][n] b1[h1] W2[h2][h1] b2[h2]
- * W3[n][h2] b3[n] (W row-major, out x in). */
+ * W3[n][h2] b3[n] (W row-major, out x in), shared by all series (per_series =
+ * 0); n in {4, 8, 16, 32}, hidden widths <= 128 and multiples of 4. */
 typedef enum {
   TVI_MODEL_LINEAR = 0,
   TVI_MODEL_VDP = 1,

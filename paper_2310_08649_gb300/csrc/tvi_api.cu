@@ -61,7 +61,8 @@ tvi_status check_model(const tvi_model* m) {
       return fail(TVI_EUNSUPPORTED, "MLP models take one shared parameter vector");
     if (!tvi::mlp_supported(m->n, m->hidden1, m->hidden2))
       return fail(TVI_EUNSUPPORTED,
-                  "MLP sizes n %d, hidden %d/%d not built (n <= 32, hidden <= 128, multiples of 4)",
+                  "MLP sizes n %d, hidden %d/%d not built (n in {4, 8, 16, 32}, hidden <= 128 "
+                  "and a multiple of 4)",
                   m->n, m->hidden1, m->hidden2);
     return TVI_OK;
   }
@@ -69,6 +70,8 @@ tvi_status check_model(const tvi_model* m) {
     return fail(TVI_EUNSUPPORTED, "model kind %d with n = %d is not built", m->kind, m->n);
   return TVI_OK;
 }
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // chunk the MLP path runs with: the requested one, at most N (and at least 1)
 int mlp_chunk(const tvi_options* o, int N) {
@@ -149,6 +152,7 @@ tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, 
   if (!workspace || workspace_bytes < need)
     return fail(TVI_EWORKSPACE, "workspace of %zu bytes needed (got %zu)", need,
                 workspace ? workspace_bytes : static_cast<size_t>(0));
+  if (!aligned16(workspace)) return fail(TVI_EWORKSPACE, "workspace must be 16-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);
 
@@ -215,6 +219,7 @@ tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, in
   if (!workspace || workspace_bytes < need)
     return fail(TVI_EWORKSPACE, "workspace of %zu bytes needed (got %zu)", need,
                 workspace ? workspace_bytes : static_cast<size_t>(0));
+  if (!aligned16(workspace)) return fail(TVI_EWORKSPACE, "workspace must be 16-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);
 
@@ -233,6 +238,7 @@ tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, in
   a.dy0 = dy0;
   a.partials = reinterpret_cast<double*>(ws + l.partials);
   if (is_mlp(model)) {
+    if (!aligned16(grad_out)) return fail(TVI_EINVAL, "grad_out must be 16-byte aligned");
     a.chunk = mlp_chunk(opt, N);
     cudaError_t e = tvi::mlp_adjoint(model->kind, model->n, model->hidden1, model->hidden2,
                                      opt->precision, a, workspace, s);

@@ -282,7 +282,8 @@ __device__ __forceinline__ T wget(const BlocksArgs& a, int i) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, int TP) {
+__global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, int TP,
+                                                                  int stage_w2) {
   extern __shared__ unsigned char smem_raw[];
   const MlpDims d = a.d;
   const int n = d.n, h1 = d.h1, h2 = d.h2;
@@ -291,7 +292,9 @@ __global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, 
   if (a.active && !a.active[b]) return;
   const int j0 = blockIdx.x * TP;
   const int np = min(TP, a.L - j0);
-  T* sU = reinterpret_cast<T*>(smem_raw);  // [h1][NT]
+  // W2 transposed ([h1][h2]) when it fits: 4-wide shared loads in the inner loop
+  T* sW2t = reinterpret_cast<T*>(smem_raw);
+  T* sU = sW2t + (stage_w2 ? h1 * h2 : 0);  // [h1][NT]
   T* sG = sU + h1 * NT;                     // [h2][NT]
   T* sA = sG + h2 * NT;                     // [TP][n][2n]
   T* sdt = sA + TP * n * 2 * n;             // [TP]
@@ -304,10 +307,17 @@ __global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, 
   const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
   for (int p = tid; p < TP; p += kTileThreads)
     sdt[p] = static_cast<T>(p < np ? step_dt(tb, len, step_of(a.reverse, a.i0, a.L, j0 + p)) : 0.0);
+  const int ln = __ffs(n) - 1;    // n and NT are powers of two
+  const int lnt = __ffs(NT) - 1;
   for (int e = tid; e < h1 * NT; e += kTileThreads) {
-    const int q = e / NT, col = e % NT, p = col / n, c = col % n;
-    sU[e] = (p < np) ? static_cast<T>(dvt[p * dvs + q]) * wget<T>(a, q * n + c) : T(0);
+    const int q = e >> lnt, col = e & (NT - 1), p = col >> ln, c = col & (n - 1);
+    sU[e] = (p < np) ? narrow<T>(dvt[p * dvs + q]) * wget<T>(a, q * n + c) : T(0);
   }
+  if (stage_w2)
+    for (int e = tid; e < h1 * h2; e += kTileThreads) {
+      const int r = e / h1, q = e - r * h1;
+      sW2t[q * h2 + r] = wget<T>(a, oW2 + e);
+    }
   __syncthreads();
   {  // G = D2 W2 U
     const int tn = NT / 4, tiles = (h2 / 4) * tn;
@@ -317,7 +327,8 @@ __global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, 
       for (int q = 0; q < h1; ++q) {
         T wv[4], uv[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) wv[i] = wget<T>(a, oW2 + (r0 + i) * h1 + q);
+        for (int i = 0; i < 4; ++i)
+          wv[i] = stage_w2 ? sW2t[q * h2 + r0 + i] : wget<T>(a, oW2 + (r0 + i) * h1 + q);
 #pragma unroll
         for (int i = 0; i < 4; ++i) uv[i] = sU[q * NT + c0 + i];
 #pragma unroll
@@ -327,11 +338,11 @@ __global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, 
       }
 #pragma unroll
       for (int k2 = 0; k2 < 4; ++k2) {
-        const int p = (c0 + k2) / n;
+        const int p = (c0 + k2) >> ln;
         const bool live = p < np;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const T d2v = live ? static_cast<T>(dvt[p * dvs + h1 + r0 + i]) : T(0);
+          const T d2v = live ? narrow<T>(dvt[p * dvs + h1 + r0 + i]) : T(0);
           sG[(r0 + i) * NT + c0 + k2] = d2v * acc[i][k2];
         }
       }
@@ -356,13 +367,13 @@ __global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, 
       }
 #pragma unroll
       for (int k2 = 0; k2 < 4; ++k2) {
-        const int col = c0 + k2, p = col / n, c = col % n;
+        const int col = c0 + k2, p = col >> ln, c = col & (n - 1);
         if (p >= np) continue;
         T* Ap = sA + p * n * 2 * n;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int r = r0 + i;
-          const T J = static_cast<T>(dvt[p * dvs + h1 + h2 + r]) * acc[i][k2];
+          const T J = narrow<T>(dvt[p * dvs + h1 + h2 + r]) * acc[i][k2];
           Ap[r * 2 * n + c] = ((r == c) ? T(1) : T(0)) - sdt[p] * J;
           Ap[r * 2 * n + n + c] = (r == c) ? T(1) : T(0);
         }
@@ -397,9 +408,12 @@ __global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, 
       __syncwarp();
       for (int col = lane; col < 2 * n; col += 32) Ap[kk * 2 * n + col] *= inv;
       __syncwarp();
-      for (int e = lane; e < n * 2 * n; e += 32) {
-        const int r = e / (2 * n), col = e % (2 * n);
-        if (r != kk && col != kk) Ap[e] = fma(-Ap[r * 2 * n + kk], Ap[kk * 2 * n + col], Ap[e]);
+      // each lane updates the columns it owns; column kk is read, not written
+      for (int col = lane; col < 2 * n; col += 32) {
+        if (col == kk) continue;
+        const T pk = Ap[kk * 2 * n + col];
+        for (int r = 0; r < n; ++r)
+          if (r != kk) Ap[r * 2 * n + col] = fma(-Ap[r * 2 * n + kk], pk, Ap[r * 2 * n + col]);
       }
       __syncwarp();
       for (int r = lane; r < n; r += 32)
@@ -407,24 +421,29 @@ __global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, 
       __syncwarp();
     }
     T* Mo = static_cast<T*>(a.M) + (static_cast<size_t>(b) * a.c + j0 + p) * n * n;
-    for (int e = lane; e < n * n; e += 32) {
-      const int r = e / n, col = e % n;
-      Mo[e] = a.reverse ? Ap[col * 2 * n + n + r] : Ap[r * 2 * n + n + col];
-    }
+    for (int r = 0; r < n; ++r)
+      for (int col = lane; col < n; col += 32)
+        // stored transposed (Mo[col][r] = M[r][col]) for the chain's conflict-free reads
+        Mo[col * n + r] = a.reverse ? Ap[col * 2 * n + n + r] : Ap[r * 2 * n + n + col];
     __syncwarp();
   }
 }
 
 // ---------------------------------------------------------------------------
 // Block substitution d_j = M_j (d_{j-1} + rhs_j), d_{-1} = x_init (Alg. 2 on the
-// normalised blocks): one warp per series, lane r owns component r and keeps
-// row r of M_j in registers, the next row prefetched.  For n = 16-32 this is
-// n^2 work per step against the n^3 per step of a cyclic reduction, the
-// trade-off the paper reports for larger systems.
+// normalised blocks): one warp per series, lane r owns component r.  For
+// n = 16-32 this is n^2 work per step against the n^3 per step of a cyclic
+// reduction, the trade-off the paper reports for larger systems.
+// The chain is latency bound (one dependent mat-vec per step), so everything
+// that does not depend on d_{j-1} -- the block M_j (stored transposed), rhs_j
+// and the accumulator row x_j -- is staged D steps ahead into a per-warp ring
+// of shared-memory slots with cp.async, and d_{j-1} + rhs_j is broadcast
+// through shared memory.  Every staged address is 16-byte aligned (workspace
+// buffers by construction, caller arrays checked by the C ABI).
 // ---------------------------------------------------------------------------
 struct ChainArgs {
   int B, n, L, c, N, i0, reverse;
-  const void* M;           // [B][c][n][n] in T
+  const void* M;           // [B][c][n][n] in T, each block transposed
   const double* rhs_buf;   // [B][c][n] rhs by row, or null
   const double* rhs_traj;  // [B][N+1][n] rhs by step (adjoint dL/dy), or null
   const double* x_init;    // [B][n] d_{-1}, or null (zero)
@@ -433,50 +452,92 @@ struct ChainArgs {
   int mode;                // 0: x -= d   1: x = d   2: x += d
 };
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+constexpr int kChainWarps = 4;
+
 template <typename T>
-__global__ void mlp_chain_kernel(ChainArgs a) {
-  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+size_t chain_slot_bytes(int n) {
+  return sizeof(T) * n * n + 2 * sizeof(double) * n;
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(32 * kChainWarps) mlp_chain_kernel(ChainArgs a) {
+  extern __shared__ __align__(16) unsigned char chain_smem[];
+  __shared__ T s_u[kChainWarps][32];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * kChainWarps + wib;
+  // warp-uniform exit: the kernel synchronises only within a warp
   if (b >= a.B || (a.active && !a.active[b])) return;
   const int n = a.n;
   const bool own = lane < n;
-  const T* Mb = static_cast<const T*>(a.M) + static_cast<size_t>(b) * a.c * n * n;
+  const size_t mbytes = sizeof(T) * n * n;
+  const size_t slot_bytes = mbytes + 2 * sizeof(double) * n;
+  unsigned char* ring = chain_smem + static_cast<size_t>(wib) * D * slot_bytes;
+  const unsigned char* Mb = static_cast<const unsigned char*>(a.M) +
+                            static_cast<size_t>(b) * a.c * mbytes;
   double* xb = a.x + static_cast<size_t>(b) * a.c * n;
-  T mrow[32], mnext[32];
-#pragma unroll
-  for (int q = 0; q < 32; ++q) mrow[q] = (own && q < n && a.L > 0) ? Mb[lane * n + q] : T(0);
-  T dprev = (a.x_init && own) ? static_cast<T>(a.x_init[b * n + lane]) : T(0);
+  T* su = s_u[wib];
+  auto issue = [&](int j) {  // stage step j into slot j % D (empty group past the end)
+    if (j < a.L) {
+      unsigned char* slot = ring + static_cast<size_t>(j % D) * slot_bytes;
+      const unsigned char* gM = Mb + static_cast<size_t>(j) * mbytes;
+      for (int k = lane; k < static_cast<int>(mbytes / 16); k += 32) cp_async16(slot + 16 * k, gM + 16 * k);
+      const double* gr =
+          a.rhs_buf ? a.rhs_buf + (static_cast<size_t>(b) * a.c + j) * n
+                    : a.rhs_traj + (static_cast<size_t>(b) * (a.N + 1) +
+                                    step_of(a.reverse, a.i0, a.L, j)) * n;
+      for (int k = lane; k < n / 2; k += 32) cp_async16(slot + mbytes + 16 * k, gr + 2 * k);
+      if (a.mode != 1)
+        for (int k = lane; k < n / 2; k += 32)
+          cp_async16(slot + mbytes + 8 * n + 16 * k, xb + static_cast<size_t>(j) * n + 2 * k);
+    }
+    cp_async_commit();
+  };
+#pragma unroll 1
+  for (int j = 0; j < D; ++j) issue(j);
+  T dprev = (a.x_init && own) ? narrow<T>(a.x_init[b * n + lane]) : T(0);
+#pragma unroll 1
   for (int j = 0; j < a.L; ++j) {
-    if (j + 1 < a.L) {
-      const T* Mn = Mb + static_cast<size_t>(j + 1) * n * n + lane * n;
-#pragma unroll
-      for (int q = 0; q < 32; ++q) mnext[q] = (own && q < n) ? Mn[q] : T(0);
-    }
-    double r = 0.0;
+    cp_async_wait<D - 1>();
+    __syncwarp();
+    const unsigned char* slot = ring + static_cast<size_t>(j % D) * slot_bytes;
+    const T* Mt = reinterpret_cast<const T*>(slot);  // Mt[q * n + r] = M_j[r][q]
+    const double* rr = reinterpret_cast<const double*>(slot + mbytes);
+    const double r_cur = own ? rr[lane] : 0.0;
+    const double x_cur = (own && a.mode != 1) ? rr[n + lane] : 0.0;
+    su[lane] = dprev + narrow<T>(r_cur);  // component `lane` of d_{j-1} + rhs_j
+    __syncwarp();
+    T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
     if (own) {
-      if (a.rhs_buf)
-        r = a.rhs_buf[(static_cast<size_t>(b) * a.c + j) * n + lane];
-      else
-        r = a.rhs_traj[(static_cast<size_t>(b) * (a.N + 1) + step_of(a.reverse, a.i0, a.L, j)) * n +
-                       lane];
+      for (int q = 0; q < n; q += 4) {
+        acc0 = fma(Mt[q * n + lane], su[q], acc0);
+        acc1 = fma(Mt[(q + 1) * n + lane], su[q + 1], acc1);
+        acc2 = fma(Mt[(q + 2) * n + lane], su[q + 2], acc2);
+        acc3 = fma(Mt[(q + 3) * n + lane], su[q + 3], acc3);
+      }
     }
-    const T u = dprev + static_cast<T>(r);  // component `lane` of d_{j-1} + rhs_j
-    T acc = T(0);
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      if (q < n) acc = fma(mrow[q], __shfl_sync(kFull, u, q), acc);
-    }
+    __syncwarp();  // slot j % D and su are free again
+    issue(j + D);
+    const T acc = (acc0 + acc1) + (acc2 + acc3);
     dprev = own ? acc : T(0);
     if (own) {
-      double& o = xb[j * n + lane];
-      const double dd = static_cast<double>(acc);
-      if (a.mode == 0) o -= dd;
-      else if (a.mode == 1) o = dd;
-      else o += dd;
+      const double dd = widen<T>(acc);
+      xb[static_cast<size_t>(j) * n + lane] =
+          (a.mode == 0) ? x_cur - dd : (a.mode == 1 ? dd : x_cur + dd);
     }
-#pragma unroll
-    for (int q = 0; q < 32; ++q) mrow[q] = mnext[q];
   }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -602,7 +663,8 @@ struct ParamArgs {
   int B, L, c;
   const double* act;  // [B*c][n+h1+h2+3]
   const double* del;  // [B*c][h1+h2+n]
-  double* acc;        // [P] FP64 accumulator (flat parameter layout)
+  double* part;       // [nsplit][P] partial sums, one per range of pairs (grid.y)
+  int per;            // pairs per range (multiple of 64)
 };
 
 template <typename T>
@@ -625,8 +687,9 @@ __global__ void __launch_bounds__(256) mlp_param_grad_kernel(ParamArgs a) {
   const int tid = threadIdx.x;
   const int tr = tid / 8, tc = (tid % 8) * 4;  // 32 rows x (8 x 4) cols
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  const int npairs = a.B * a.L;
-  for (int p0 = 0; p0 < npairs; p0 += 64) {
+  const int pbeg = blockIdx.y * a.per;
+  const int npairs = min(a.B * a.L, pbeg + a.per);
+  for (int p0 = pbeg; p0 < npairs; p0 += 64) {
     for (int e = tid; e < 64 * 32; e += 256) {
       const int pp = e / 32, q = e % 32;
       const int pi = p0 + pp;
@@ -658,9 +721,20 @@ __global__ void __launch_bounds__(256) mlp_param_grad_kernel(ParamArgs a) {
     if (c >= cols[l]) continue;
     const int idx = (c < cols[l] - 1) ? woff[l] + r * (cols[l] - 1) + c
                                       : woff[l] + rows[l] * (cols[l] - 1) + r;
-    a.acc[idx] += acc[i];
+    a.part[static_cast<size_t>(blockIdx.y) * d.P + idx] = acc[i];
   }
 }
+
+// acc[q] += sum over ranges s = 0..nsplit-1 of part[s][q], in range order
+__global__ void mlp_param_reduce_kernel(int P, int nsplit, const double* part, double* acc) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= P) return;
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += part[static_cast<size_t>(k) * P + q];
+  acc[q] += s;
+}
+
+constexpr int kMaxParamSplits = 64;
 
 int param_grad_tiles(const MlpDims& d) {
   auto t = [](int r, int c) { return ((r + 31) / 32) * ((c + 31) / 32); };
@@ -739,7 +813,7 @@ size_t al(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 struct Ws {
   float* Wf;
-  double *yi, *dy, *R, *carry, *acc, *act, *del, *norm0;
+  double *yi, *dy, *R, *carry, *acc, *part, *act, *del, *norm0;
   double* dv;
   void* M;
   unsigned long long* norm;
@@ -773,6 +847,7 @@ Ws carve(char* base, int B, int c, const MlpDims& d, int precision, bool adjoint
   w.M = take(tsz * bc * d.n * d.n);
   if (adjoint_bufs) {
     w.acc = reinterpret_cast<double*>(take(sizeof(double) * d.P));
+    w.part = reinterpret_cast<double*>(take(sizeof(double) * d.P * kMaxParamSplits));
     w.act = reinterpret_cast<double*>(take(sizeof(double) * bc * (d.n + d.h1 + d.h2 + 3)));
     w.del = reinterpret_cast<double*>(take(sizeof(double) * bc * (d.h1 + d.h2 + d.n)));
   }
@@ -789,6 +864,7 @@ MlpDims dims_of(int n, int h1, int h2) {
   return d;
 }
 
+constexpr size_t kMaxDynSmem = 227 * 1024;  // per-block shared memory limit
 constexpr int kResTP = 64;  // pairs per residual tile
 constexpr int kVjpTP = 32;  // pairs per vector-Jacobian tile
 
@@ -805,7 +881,9 @@ int blocks_tp(const MlpDims& d, int precision) {
   const int hmax = d.h1 > d.h2 ? d.h1 : d.h2;
   int nt = 32768 / (hmax * tsz);
   int tp = nt / d.n;
-  return tp < 1 ? 1 : (tp > 64 ? 64 : tp);
+  tp = tp < 1 ? 1 : (tp > 64 ? 64 : tp);
+  while (tp & (tp - 1)) tp &= tp - 1;  // power of two: tile columns TP * n index by shifts
+  return tp;
 }
 size_t blocks_smem(const MlpDims& d, int precision, int tp) {
   const size_t tsz = precision == kPrecFp64 ? 8 : 4;
@@ -841,25 +919,43 @@ cudaError_t launch_vjp(const VjpArgs& v, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_blocks(const BlocksArgs& bk, int precision, cudaStream_t s) {
   const int tp = blocks_tp(bk.d, precision);
-  const size_t sm = blocks_smem(bk.d, precision, tp);
+  size_t sm = blocks_smem(bk.d, precision, tp);
+  // W2 goes to shared memory only when that keeps two blocks per SM (measured:
+  // losing the second block costs more than the cached loads it saves)
+  const size_t w2 = sizeof(T) * bk.d.h1 * bk.d.h2;
+  const int stage = 2 * (sm + w2) <= kMaxDynSmem ? 1 : 0;
+  if (stage) sm += w2;
   cudaError_t e = set_smem(mlp_blocks_kernel<T>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((bk.L + tp - 1) / tp, bk.B);
-  mlp_blocks_kernel<T><<<grid, kTileThreads, sm, s>>>(bk, tp);
+  mlp_blocks_kernel<T><<<grid, kTileThreads, sm, s>>>(bk, tp, stage);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_chain(const ChainArgs& ch, cudaStream_t s) {
-  mlp_chain_kernel<T><<<(ch.B + 3) / 4, 128, 0, s>>>(ch);
+  // ring depth 8 when four warps' rings fit in 200 KB, else 4
+  const size_t slot = chain_slot_bytes<T>(ch.n);
+  const dim3 grid((ch.B + kChainWarps - 1) / kChainWarps);
+  if (kChainWarps * 8 * slot <= 200 * 1024) {
+    const size_t sm = kChainWarps * 8 * slot;
+    cudaError_t e = set_smem(mlp_chain_kernel<T, 8>, sm);
+    if (e != cudaSuccess) return e;
+    mlp_chain_kernel<T, 8><<<grid, 32 * kChainWarps, sm, s>>>(ch);
+  } else {
+    const size_t sm = kChainWarps * 4 * slot;
+    cudaError_t e = set_smem(mlp_chain_kernel<T, 4>, sm);
+    if (e != cudaSuccess) return e;
+    mlp_chain_kernel<T, 4><<<grid, 32 * kChainWarps, sm, s>>>(ch);
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
 bool mlp_supported(int n, int h1, int h2) {
-  return n >= 4 && n <= 32 && n % 4 == 0 && h1 >= 4 && h1 <= 128 && h1 % 4 == 0 && h2 >= 4 &&
-         h2 <= 128 && h2 % 4 == 0;
+  const bool n_ok = n == 4 || n == 8 || n == 16 || n == 32;  // index math uses shifts
+  return n_ok && h1 >= 4 && h1 <= 128 && h1 % 4 == 0 && h2 >= 4 && h2 <= 128 && h2 % 4 == 0;
 }
 
 size_t mlp_workspace_bytes(int n, int h1, int h2, int B, int chunk, int precision) {
@@ -985,11 +1081,19 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
     v.act = w.act;
     v.del = w.del;
     TVI_TRY(kind == kKindMlpTanh ? launch_vjp<kKindMlpTanh>(v, s) : launch_vjp<kKindMlpSilu>(v, s));
-    ParamArgs pa{d, B, L, c, w.act, w.del, w.acc};
+    // pairs split into up to kMaxParamSplits ranges of >= 1024 so the tiles fill the GPU
+    const int npairs = B * L;
+    int nsplit = (npairs + 1023) / 1024;
+    nsplit = nsplit < 1 ? 1 : (nsplit > kMaxParamSplits ? kMaxParamSplits : nsplit);
+    const int per = ((npairs + nsplit - 1) / nsplit + 63) / 64 * 64;
+    nsplit = (npairs + per - 1) / per;
+    ParamArgs pa{d, B, L, c, w.act, w.del, w.part, per};
+    const dim3 pgrid(param_grad_tiles(d), nsplit);
     if (precision == kPrecFp64)
-      mlp_param_grad_kernel<double><<<param_grad_tiles(d), 256, 0, s>>>(pa);
+      mlp_param_grad_kernel<double><<<pgrid, 256, 0, s>>>(pa);
     else
-      mlp_param_grad_kernel<float><<<param_grad_tiles(d), 256, 0, s>>>(pa);
+      mlp_param_grad_kernel<float><<<pgrid, 256, 0, s>>>(pa);
+    mlp_param_reduce_kernel<<<(d.P + 255) / 256, 256, 0, s>>>(d.P, nsplit, w.part, w.acc);
     TVI_TRY(cudaGetLastError());
     mlp_carry_kernel<<<(B * n + 255) / 256, 256, 0, s>>>(B, n, L, c, w.dy, w.carry);
     TVI_TRY(cudaGetLastError());
