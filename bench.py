@@ -8,6 +8,11 @@ whole batch.  The same library with chunk = 1 and FP64 blocks (the sequential
 scheme, same Newton tolerance, same launch strategy) is timed in the same run
 for the chunked/sequential ratio.
 
+--workload vdp_pred: the same van der Pol setup at chunk 100 and tolerance 1e-8
+with the learned Newton predictor (trained before timing on 51,200 solver chunks
+of training seeds 3000-3003; timed on held-out seed 4000); the same steps with
+the dy = 0 guess are timed beside it.
+
 --workload node16 / node32 time the neural-ODE workloads instead (MLP
 16-64-64-16 tanh, 64 x 2000; MLP 32-128-128-32 SiLU, 512 x 20,000 padded with
 per-series lengths uniform in [2000, 20000]; throughput counts real steps).
@@ -37,9 +42,14 @@ FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 rate (recipe table); no measure
 
 WORKLOADS = {
     "vdp": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 128, "N": 10000},
+    "vdp_pred": {"chunk": 100, "precision": "fp32", "tol": 1e-8, "B": 128, "N": 10000},
     "node16": {"chunk": 200, "precision": "fp32", "tol": 1e-8, "B": 64, "N": 2000},
     "node32": {"chunk": 1000, "precision": "fp32", "tol": 1e-8, "B": 512, "N": 20000},
 }
+
+
+PRED_TRAIN_SEEDS = range(3000, 3004)  # 4 x 128 series x 100 chunks = 51,200 samples
+PRED_EVAL_SEED = 4000                  # held out
 
 
 def parse():
@@ -63,7 +73,7 @@ def parse():
     for k, v in WORKLOADS[args.workload].items():
         if getattr(args, k) is None:
             setattr(args, k, v)
-    if args.workload != "vdp":
+    if not args.workload.startswith("vdp"):
         args.no_chunk1 = True  # the one-step MLP scheme reads status back every Newton update
     return args
 
@@ -77,6 +87,8 @@ def make_workload(args, rank=0):
     """(inputs, dL/dy) for the chosen workload; ranks draw their own batches."""
     if args.workload == "vdp":
         w = workloads.vdp(B=args.B, N=args.N, seed=workloads.SEED_VDP + 1000 * rank)
+    elif args.workload == "vdp_pred":
+        w = workloads.vdp(B=args.B, N=args.N, seed=PRED_EVAL_SEED + rank)
     elif args.workload == "node16":
         w = workloads.mlp_ode(B=args.B, N=args.N, seed=workloads.SEED_MLP + 1000 * rank)
     else:
@@ -97,6 +109,8 @@ def real_steps(w):
 
 def workload_config(args):
     desc = {"vdp": "van der Pol n=2, mu log-uniform [10,1000], log-spaced steps",
+            "vdp_pred": "van der Pol n=2 (held-out seed) with the learned Newton predictor "
+                        "(MLP 103-256-256-200)",
             "node16": "neural ODE n=16, MLP 16-64-64-16 tanh, uniform steps on [0,10]",
             "node32": "neural ODE n=32, MLP 32-128-128-32 SiLU, per-series lengths "
                       "U[2000,N] padded, uniform steps on [0,10]"}[args.workload]
@@ -243,7 +257,7 @@ def roofline(args, w, stats, fwd_ms, adj_ms, refine):
     upd = stats[:, 0].astype(np.float64)
     nchk = stats[:, 1].astype(np.float64)
     spc = N / np.maximum(nchk, 1)  # steps per solved chunk
-    if args.workload == "vdp":
+    if args.workload.startswith("vdp"):
         # residual y = y_i + dy (2), h (3), R (4) = 9; update dy -= d: 2
         fwd_ops = float(np.sum(((upd + nchk) * 9.0 + upd * 2.0) * spc))
         # adjoint per step: per refinement sweep 14, parameter VJP 4
@@ -301,7 +315,7 @@ def run_ours(args):
     def make(opts):
         ws = tvi.make_workspace(model, opts, B, N, dev)
         y = torch.empty((B, N + 1, n), dtype=torch.float64, device=dev)
-        stats = torch.empty((B, 4), dtype=torch.int32, device=dev)
+        stats = torch.empty((B, 6), dtype=torch.int32, device=dev)
         st = torch.empty((B,), dtype=torch.int32, device=dev)
         dp = torch.empty_like(params)
         dy0 = torch.empty_like(y0)
@@ -343,11 +357,39 @@ def run_ours(args):
         return {"fwd_ms": fwd, "adj_ms": adj, "total_ms": float(np.sum(fwd) + np.sum(adj)),
                 "stats": stats.cpu().numpy(), "t0": t0, "t1": t1}
 
+    pred_info, pred_opts = None, {}
+    if args.workload == "vdp_pred":
+        from paper_2310_08649_gb300.predictor import Predictor, PredictorSpec, solver_dataset
+        spec = PredictorSpec()
+        t_train = time.perf_counter()
+        px, pt = solver_dataset(lambda s: workloads.vdp(seed=s, B=args.B, N=args.N),
+                                PRED_TRAIN_SEEDS, spec, tol=args.tol)
+        predictor = Predictor(spec, seed=0)
+        predictor.set_normalisation(px, pt)
+        losses = predictor.fit(px, pt, epochs=200, batch=512, lr=1e-3, lr_end=1e-5, seed=1)
+        torch.cuda.synchronize()
+        pred_opts = predictor.options()
+        pred_info = {"train_samples": int(px.shape[0]), "epochs": 200,
+                     "train_s": time.perf_counter() - t_train,
+                     "final_loss": losses[-1], "first_epoch_loss": losses[0]}
+
     clocks = ClockSampler(local)
     clocks.start()
     opts = tvi.Options(chunk=args.chunk, tol_abs=args.tol, precision=args.precision,
-                       rows_per_thread=args.rpt, sync_status=False)
+                       rows_per_thread=args.rpt, sync_status=False, **pred_opts)
     res = timed_steps(opts, args.steps, args.warmup)
+    if pred_info is not None:
+        o0 = tvi.Options(chunk=args.chunk, tol_abs=args.tol, precision=args.precision,
+                         rows_per_thread=args.rpt, sync_status=False)
+        r0 = timed_steps(o0, args.steps, 1)
+        s1, s0 = res["stats"], r0["stats"]
+        v0 = units_per_step * args.steps / (r0["total_ms"] / 1e3)
+        pred_info.update({
+            "newton_updates_per_chunk": float(s1[:, 0].sum() / max(s1[:, 1].sum(), 1)),
+            "newton_updates_per_chunk_zero_guess": float(s0[:, 0].sum() / max(s0[:, 1].sum(), 1)),
+            "guesses_used": int(s1[:, 4].sum()), "fallbacks": int(s1[:, 5].sum()),
+            "fwd_ms": float(np.mean(res["fwd_ms"])), "fwd_ms_zero_guess": float(np.mean(r0["fwd_ms"])),
+            "value_zero_guess": v0})
     total_ms = torch.tensor([res["total_ms"]], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(total_ms, op=dist.ReduceOp.MAX)
@@ -418,7 +460,7 @@ def run_ours(args):
 
     if rank == 0:
         upd, nchk = stats_np[:, 0].astype(np.float64), stats_np[:, 1].astype(np.float64)
-        launches = 2 * args.steps if args.workload == "vdp" else None
+        launches = 2 * args.steps if args.workload.startswith("vdp") else None
         line = {"metric": METRIC, "value": value, "unit": "series*steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -439,6 +481,8 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": "series*steps/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clk}
+        if pred_info is not None:
+            line["predictor"] = pred_info
         if launches is None:
             # MLP path, per step: forward 3 + per chunk (init, store) + per Newton pass
             # (residual, check) + per update (blocks, chain); adjoint 2 + per chunk

@@ -94,10 +94,16 @@ typedef struct {
   int sync_status;    /* 1: synchronise `stream` and fold per-series status into the
                          return code; 0: return TVI_OK after enqueueing (status only
                          in the series_status array) */
+  const float* predictor;  /* learned Newton predictor (van der Pol model only), packed
+                              as tvi_predictor_* describe, device; NULL = dy = 0 guess */
+  int predictor_chunk;     /* steps the predictor proposes (its output is 2 x this);
+                              used for chunk attempts of exactly this length */
+  int predictor_hidden;    /* hidden width of the predictor MLP (even, <= 256) */
 } tvi_options;
 
 /* Fill *opt with defaults: chunk 1, tol_abs 1e-8, tol_rel 0, max_iter 50, FP64,
- * retry_halving 1, adjoint_refine 2, rows_per_thread 0, sync_status 1. */
+ * retry_halving 1, adjoint_refine 2, rows_per_thread 0, sync_status 1, no
+ * predictor. */
 void tvi_default_options(tvi_options* opt);
 
 /* Number of parameters P of one parameter vector, or -1 for a bad model. */
@@ -117,12 +123,18 @@ size_t tvi_workspace_bytes(const tvi_model* model, const tvi_options* opt, int B
  *               y_k = y_{k-1} exactly.
  *   params      [B][P] or [P] (tvi_model.per_series).
  *   y_out       [B][N+1][n]  trajectory; y_out[b][0] = y0[b] (like scipy odeint).
- *   stats       [B][4] int32 or NULL: total Newton updates, chunks solved,
- *               chunk retries (halvings), largest Newton count of one chunk.
+ *   stats       [B][6] int32 or NULL: total Newton updates, chunks solved,
+ *               chunk retries (halvings), largest Newton count of one chunk,
+ *               chunks started from the predictor's guess, predictor guesses
+ *               rejected because their residual was not below the dy = 0 one.
  *   series_status [B] int32 or NULL: 0 ok, 1 Newton limit, 2 non-finite residual.
  *   workspace   >= tvi_workspace_bytes(model, opt, B, N) bytes of device memory.
  * Newton starts every chunk from dy = 0 (Sec. 2.3) and stops per series (Alg. 1,
- * converged series are frozen).  A failed chunk is retried by halving when
+ * converged series are frozen).  With opt->predictor, a chunk attempt of
+ * predictor_chunk steps starts from the predictor's guess instead when the
+ * guess's FP64 residual infinity-norm is below that of dy = 0; after k
+ * rejected guesses in a row (k <= 5) the series skips the predictor on its next
+ * 2^k - 1 eligible chunks, and an accepted guess resets k.  A failed chunk is retried by halving when
  * opt->retry_halving; otherwise, or on a one-step chunk, the series' status is
  * set and its integration continues from the unconverged iterate.
  * Returns TVI_OK, an argument error, or (sync_status = 1) TVI_ENOTCONV /
@@ -174,6 +186,46 @@ tvi_status tvi_adjoint_noalloc(const tvi_model* model, const tvi_options* opt, i
                                const double* times, const int* lengths, const double* params,
                                const double* y, const double* grad_out, double* dparams,
                                double* dy0, void* stream);
+
+/*
+ * Learned Newton predictor (an MLP over the chunk-start state, the model
+ * parameter and the chunk's step sizes that proposes the chunk's increments
+ * dy_1..dy_c as Newton's starting guess).  Newton still runs to the same
+ * tolerance from that guess, so results do not change; only the iteration
+ * count does.  The paper starts every chunk at dy = 0 (Sec. 2.3); it has no
+ * predictor.
+ *
+ * Packed FP32 vector (in features, H hidden, out outputs):
+ *   mean[in] std[in] scale[out] W1[H][in] b1[H] W2[H][H] b2[H] W3[out][H] b3[out]
+ * network(x) = W3 silu(W2 silu(W1 (x - mean) / std + b1) + b2) + b3, and the
+ * predictor's output is network(x) * scale.  For the van der Pol model with a
+ * c-step predictor: in = 3 + c with x = (y1, y2, log10 mu, log10 dt_1..dt_c)
+ * (dt floored at 1e-30), out = 2 c slopes s_j = (out[2(j-1)], out[2(j-1)+1]),
+ * and the guess is dy_j = sum_{l <= j} dt_l s_l.
+ */
+
+/* Floats in the packed vector, or -1 for bad sizes (H even, <= 1024). */
+int tvi_predictor_size(int in, int hidden, int out);
+
+/* Batched inference: x [M][in] raw features -> y [M][out] outputs (device). */
+tvi_status tvi_predictor_forward(const float* packed, int in, int hidden, int out, int M,
+                                 const float* x, float* y, void* stream);
+
+/* Device workspace for tvi_predictor_train_step with batch M. */
+size_t tvi_predictor_workspace_bytes(int in, int hidden, int out, int M);
+
+/*
+ * One Adam step (Kingma & Ba 2015: beta1 0.9, beta2 0.999, eps 1e-8, bias
+ * correction with step >= 1) on the trained part (W1..b3) of `packed`, for the
+ * mean squared error between network(x) and target / scale over a batch of M
+ * samples: sample m is row rows[m] of x [*][in] and target [*][out] (rows NULL:
+ * row m).  adam_m, adam_v: moment vectors, size tvi_predictor_size - (2 in +
+ * out), zeroed before step 1.  loss: device float receiving the batch loss.
+ */
+tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v, int in, int hidden,
+                                    int out, int M, const float* x, const float* target,
+                                    const int* rows, float lr, int step, float* loss,
+                                    void* workspace, size_t workspace_bytes, void* stream);
 
 /* Text of the last error on the calling host thread ("" if none). */
 const char* tvi_last_error(void);

@@ -19,7 +19,10 @@ TVI_ENOTCONV, TVI_ENONFINITE = -4, -5
 
 # every symbol include/tvi.h declares
 EXPORTS = ("tvi_default_options", "tvi_param_count", "tvi_workspace_bytes", "tvi_integrate",
-           "tvi_adjoint", "tvi_adjoint_noalloc", "tvi_last_error", "tvi_version")
+           "tvi_adjoint", "tvi_adjoint_noalloc", "tvi_predictor_size", "tvi_predictor_forward",
+           "tvi_predictor_workspace_bytes", "tvi_predictor_train_step", "tvi_last_error",
+           "tvi_version")
+STATS = 6  # per-series statistics columns of tvi_integrate
 
 
 class TviModel(ctypes.Structure):
@@ -32,7 +35,8 @@ class TviOptions(ctypes.Structure):
                 ("tol_rel", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("retry_halving", ctypes.c_int),
                 ("adjoint_refine", ctypes.c_int), ("rows_per_thread", ctypes.c_int),
-                ("sync_status", ctypes.c_int)]
+                ("sync_status", ctypes.c_int), ("predictor", ctypes.c_void_p),
+                ("predictor_chunk", ctypes.c_int), ("predictor_hidden", ctypes.c_int)]
 
 
 class TviError(RuntimeError):
@@ -71,6 +75,16 @@ def load():
             lib.tvi_adjoint_noalloc.argtypes = [mp, op, ctypes.c_int, ctypes.c_int, vp, vp, vp,
                                                 vp, vp, vp, vp, vp]
             lib.tvi_adjoint_noalloc.restype = ctypes.c_int
+            ci = ctypes.c_int
+            lib.tvi_predictor_size.argtypes = [ci, ci, ci]
+            lib.tvi_predictor_size.restype = ci
+            lib.tvi_predictor_forward.argtypes = [vp, ci, ci, ci, ci, vp, vp, vp]
+            lib.tvi_predictor_forward.restype = ci
+            lib.tvi_predictor_workspace_bytes.argtypes = [ci, ci, ci, ci]
+            lib.tvi_predictor_workspace_bytes.restype = sz
+            lib.tvi_predictor_train_step.argtypes = [vp, vp, vp, ci, ci, ci, ci, vp, vp, vp,
+                                                     ctypes.c_float, ci, vp, vp, sz, vp]
+            lib.tvi_predictor_train_step.restype = ci
             lib.tvi_last_error.argtypes = []
             lib.tvi_last_error.restype = ctypes.c_char_p
             lib.tvi_version.argtypes = []

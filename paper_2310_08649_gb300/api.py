@@ -50,14 +50,22 @@ class Options:
     adjoint_refine: int = 2
     rows_per_thread: int = 0
     sync_status: bool = True
+    predictor: object = None      # packed predictor: CUDA float32 tensor, or None
+    predictor_chunk: int = 0
+    predictor_hidden: int = 0
 
     def c(self):
         if self.precision not in _lib.PRECISIONS:
             raise ValueError(f"unknown precision {self.precision!r}")
+        pred = None
+        if self.predictor is not None:
+            _check(self.predictor, "predictor", torch.float32, tuple(self.predictor.shape))
+            pred = self.predictor.data_ptr()
         return _lib.TviOptions(int(self.chunk), float(self.tol_abs), float(self.tol_rel),
                                int(self.max_iter), _lib.PRECISIONS[self.precision],
                                int(bool(self.retry_halving)), int(self.adjoint_refine),
-                               int(self.rows_per_thread), int(bool(self.sync_status)))
+                               int(self.rows_per_thread), int(bool(self.sync_status)), pred,
+                               int(self.predictor_chunk), int(self.predictor_hidden))
 
 
 def _check(t, name, dtype, shape, allow_none=False):
@@ -105,7 +113,7 @@ def integrate(model, opts, y0, times, params, lengths=None, y_out=None, stats=No
               series_status=None, workspace=None, stream=None, raise_on_status=True):
     """Chunked backward-Euler integration (tvi_integrate).
 
-    Returns (y [B][N+1][n], stats [B][4] int32, series_status [B] int32, rc)."""
+    Returns (y [B][N+1][n], stats [B][6] int32, series_status [B] int32, rc)."""
     lib = _lib.load()
     B, n = y0.shape
     N = times.shape[1] - 1
@@ -118,7 +126,7 @@ def integrate(model, opts, y0, times, params, lengths=None, y_out=None, stats=No
         y_out = torch.empty((B, N + 1, n), dtype=torch.float64, device=dev)
     _check(y_out, "y_out", torch.float64, (B, N + 1, n))
     if stats is None:
-        stats = torch.empty((B, 4), dtype=torch.int32, device=dev)
+        stats = torch.empty((B, _lib.STATS), dtype=torch.int32, device=dev)
     if series_status is None:
         series_status = torch.empty((B,), dtype=torch.int32, device=dev)
     if workspace is None:

@@ -87,6 +87,12 @@ tvi_status check_opt(const tvi_options* o) {
     return fail(TVI_EINVAL, "tolerances must be >= 0");
   if (o->precision != tvi::kPrecFp64 && o->precision != tvi::kPrecFp32)
     return fail(TVI_EUNSUPPORTED, "precision %d is not built for small state sizes", o->precision);
+  if (o->predictor &&
+      (o->predictor_chunk < 1 || o->predictor_chunk > tvi::kPredMaxChunk ||
+       o->predictor_hidden < 2 || o->predictor_hidden > tvi::kPredMaxHidden ||
+       o->predictor_hidden % 2 != 0))
+    return fail(TVI_EINVAL, "predictor needs 1 <= predictor_chunk <= %d and an even "
+                "predictor_hidden <= %d", tvi::kPredMaxChunk, tvi::kPredMaxHidden);
   if (o->adjoint_refine < 0 || o->adjoint_refine > 16)
     return fail(TVI_EINVAL, "adjoint_refine must be in [0, 16]");
   return TVI_OK;
@@ -107,6 +113,9 @@ void tvi_default_options(tvi_options* opt) {
   opt->adjoint_refine = 2;
   opt->rows_per_thread = 0;
   opt->sync_status = 1;
+  opt->predictor = nullptr;
+  opt->predictor_chunk = 0;
+  opt->predictor_hidden = 0;
 }
 
 int tvi_param_count(const tvi_model* m) {
@@ -173,6 +182,11 @@ tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, 
   a.stats = stats;
   a.series_status = series_status;
   a.worst = reinterpret_cast<int*>(ws + l.worst);
+  a.pred = opt->predictor;
+  a.pred_chunk = opt->predictor_chunk;
+  a.pred_hid = opt->predictor_hidden;
+  if (a.pred && model->kind != TVI_MODEL_VDP)
+    return fail(TVI_EUNSUPPORTED, "the Newton predictor is built for the van der Pol model");
 
   if (is_mlp(model)) {
     a.chunk = mlp_chunk(opt, N);
@@ -189,6 +203,8 @@ tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, 
   if (e != cudaSuccess) return cuda_fail(e, "tvi_integrate: clearing the status word");
   int rpt, threads;
   tvi::small_launch_shape(a.chunk, opt->rows_per_thread, &rpt, &threads);
+  // the predictor's layers are latency-bound GEMVs: give them every warp the block can hold
+  if (a.pred) threads = tvi::small_max_threads(rpt);
   e = tvi::small_forward(model->kind, model->n, opt->precision, rpt, threads, a, s);
   if (e != cudaSuccess) return cuda_fail(e, "tvi_integrate: kernel launch");
   if (!opt->sync_status) return TVI_OK;

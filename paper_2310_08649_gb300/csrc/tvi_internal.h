@@ -28,10 +28,18 @@ struct FwdArgs {
   const int* lengths;
   const double* params;
   double* y_out;
-  int* stats;          // [B][4] or null
+  int* stats;          // [B][kStats] or null
   int* series_status;  // [B] or null
   int* worst;          // device word: max status over series
+  const float* pred;   // packed Newton predictor or null
+  int pred_chunk, pred_hid;
 };
+
+// per-series statistics: updates, chunks, retries, max updates of a chunk,
+// chunks started from the predictor, predictor guesses rejected
+constexpr int kStats = 6;
+constexpr int kPredMaxChunk = 128;
+constexpr int kPredMaxHidden = 256;
 
 struct AdjArgs {
   int B, N, chunk, refine, per_series;

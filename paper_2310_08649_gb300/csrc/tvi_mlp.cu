@@ -779,7 +779,7 @@ __global__ void mlp_store_kernel(int n, int L, int c, int Np1, int i0, const dou
   __syncthreads();
   if (threadIdx.x < n) yi[b * n + threadIdx.x] += dyb[(L - 1) * n + threadIdx.x];
   if (threadIdx.x == 0 && stats) {
-    int* o = stats + b * 4;
+    int* o = stats + b * kStats;
     o[0] += iters[b];
     o[1] += 1;
     o[3] = max(o[3], iters[b]);
@@ -977,7 +977,7 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
   convert_weights_kernel<<<(d.P + 255) / 256, 256, 0, s>>>(a.params, w.Wf, d.P);
   mlp_start_kernel<<<(B * n + 255) / 256, 256, 0, s>>>(B, n, N + 1, a.y0, a.y_out, w.yi, w.status);
   TVI_TRY(cudaGetLastError());
-  if (a.stats) TVI_TRY(cudaMemsetAsync(a.stats, 0, sizeof(int) * 4 * B, s));
+  if (a.stats) TVI_TRY(cudaMemsetAsync(a.stats, 0, sizeof(int) * kStats * B, s));
   for (int i0 = 0; i0 < N; i0 += c) {
     const int L = (N - i0 < c) ? N - i0 : c;
     mlp_chunk_init_kernel<<<(B * c * n + 255) / 256, 256, 0, s>>>(B, n, c, w.dy, w.active, w.norm,

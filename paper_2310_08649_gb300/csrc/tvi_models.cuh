@@ -19,7 +19,10 @@ namespace tvi {
 struct ModelVdp {
   static constexpr int NS = 2;
   static constexpr int NP = 1;
+  static constexpr bool kPredictable = true;  // learned Newton predictor available
   double mu;
+  // predictor feature of the parameter
+  __device__ __forceinline__ float param_feature() const { return log10f(static_cast<float>(mu)); }
 
   __device__ __forceinline__ void load(const double* params, int b, int per_series) {
     mu = params[per_series ? b : 0];
@@ -49,7 +52,9 @@ template <int N_>
 struct ModelLinear {
   static constexpr int NS = N_;
   static constexpr int NP = N_ * N_;
+  static constexpr bool kPredictable = false;
   double A[N_][N_];
+  __device__ __forceinline__ float param_feature() const { return 0.0f; }
 
   __device__ __forceinline__ void load(const double* params, int b, int per_series) {
     const double* p = params + (per_series ? static_cast<size_t>(b) * NP : 0);

@@ -20,10 +20,51 @@
 #include "tvi_device.cuh"
 #include "tvi_internal.h"
 #include "tvi_models.cuh"
+#include "tvi_predictor.cuh"
 
 namespace tvi {
 
 namespace {
+
+// Infinity norm of the chunk residual R_j = dy_j - dy_{j-1} - dt_j h(y_i + dy_j)
+// for increments dyv, over the whole block (every thread calls it; full-block
+// barriers).  Returns the FP64 bit pattern of the max (NaN/Inf compare high).
+template <class Model, int RPT>
+__device__ __forceinline__ unsigned long long residual_norm_block(
+    const Model& mdl, const double (&yi)[Model::NS], const double (&dyv)[RPT][Model::NS],
+    const double (&dt)[RPT], const bool (&act)[RPT], double (*s_wlast)[Model::NS],
+    unsigned long long* s_red, int lane, int warp) {
+  constexpr int NS = Model::NS;
+  const int nwarps = static_cast<int>(blockDim.x >> 5);
+  double prev[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) prev[s] = __shfl_up_sync(kFull, dyv[RPT - 1][s], 1);
+  if (lane == 31) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) s_wlast[warp][s] = dyv[RPT - 1][s];
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) prev[s] = (warp > 0) ? s_wlast[warp - 1][s] : 0.0;
+  }
+  unsigned long long mx = 0ull;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    double y[NS], h[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) y[s] = yi[s] + dyv[r][s];
+    mdl.rhs(y, h);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const double pv = (r == 0) ? prev[s] : dyv[r - 1][s];
+      if (act[r]) mx = umax64(mx, abs_bits(fma(-dt[r], h[s], dyv[r][s] - pv)));
+    }
+  }
+  const unsigned long long nb = block_max_u64(mx, s_red, lane, warp, nwarps);
+  __syncthreads();  // s_wlast and s_red are reused by the next call
+  return nb;
+}
 
 // Newton outcome of one chunk attempt.
 enum { kConv = 0, kMaxIter = 1, kNonFinite = 2, kDiverged = 3 };
@@ -37,9 +78,15 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
   __shared__ unsigned long long s_red[32];
   __shared__ double s_carry[NS];
   __shared__ int s_ctl[2];  // outcome and Newton updates of the last attempt
+  // predictor features, hidden activations and outputs (van der Pol only)
+  __shared__ float s_pred[Model::kPredictable
+                              ? (NS + 1 + kPredMaxChunk) + 2 * kPredMaxHidden + NS * kPredMaxChunk
+                              : 1];
 
   const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int pred_used = 0, pred_rejected = 0;
+  int pred_wait = 0, pred_streak = 0;  // back-off after rejected guesses
   const int N = a.N;
   const double* tb = a.times + static_cast<size_t>(b) * (N + 1);
   double* yb = a.y_out + static_cast<size_t>(b) * (N + 1) * NS;
@@ -81,6 +128,98 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
       for (int s = 0; s < NS; ++s) {
         dy[r][s] = 0.0;  // Sec. 2.3 guess: dy = 0
         dyT[r][s] = T(0);
+      }
+    }
+
+    // ---- learned Newton predictor: replace dy = 0 by the proposed increments
+    // when their FP64 residual is smaller (results unchanged: Newton still runs
+    // to the tolerance) ----
+    if constexpr (Model::kPredictable) {
+      const bool pred_try = a.pred && L == a.pred_chunk && pred_wait == 0;
+      if (a.pred && L == a.pred_chunk && pred_wait > 0) --pred_wait;
+      if (pred_try) {
+        const PredDims pd{NS + 1 + L, a.pred_hid, NS * L};
+        float* feat = s_pred;
+        float* h1 = feat + pd.in;
+        float* h2 = h1 + pd.hid;
+        float* outv = h2 + pd.hid;
+        if (tid < NS) feat[tid] = static_cast<float>(yi[tid]);
+        if (tid == 0) feat[NS] = mdl.param_feature();
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+          if (act[r]) feat[NS + 1 + tid * RPT + r] = log10f(fmaxf(static_cast<float>(dt[r]), 1e-30f));
+        __syncthreads();
+        pred_infer_block(a.pred, pd, feat, h1, h2, outv);
+        // the network proposes per-step slopes s_j; the guess is their running
+        // sum dy_j = sum_{l <= j} dt_l s_l (warp 0 scans, FP64 sums)
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+          if (act[r])
+#pragma unroll
+            for (int s = 0; s < NS; ++s) outv[(tid * RPT + r) * NS + s] *= static_cast<float>(dt[r]);
+        __syncthreads();
+        if (warp == 0) {
+          constexpr int kPer = (kPredMaxChunk + 31) / 32;
+          const int j0 = lane * kPer;
+          double own[NS], incl[NS];
+#pragma unroll
+          for (int s = 0; s < NS; ++s) own[s] = 0.0;
+#pragma unroll
+          for (int q = 0; q < kPer; ++q)
+            if (j0 + q < L)
+#pragma unroll
+              for (int s = 0; s < NS; ++s) own[s] += outv[(j0 + q) * NS + s];
+#pragma unroll
+          for (int s = 0; s < NS; ++s) incl[s] = own[s];
+#pragma unroll
+          for (int off = 1; off < 32; off <<= 1)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+              const double v = __shfl_up_sync(0xffffffffu, incl[s], off);
+              if (lane >= off) incl[s] += v;
+            }
+#pragma unroll
+          for (int s = 0; s < NS; ++s) {
+            const double prev = __shfl_up_sync(0xffffffffu, incl[s], 1);
+            own[s] = lane > 0 ? prev : 0.0;  // sum over the lanes before this one
+          }
+#pragma unroll
+          for (int q = 0; q < kPer; ++q)
+            if (j0 + q < L)
+#pragma unroll
+              for (int s = 0; s < NS; ++s) {
+                own[s] += outv[(j0 + q) * NS + s];
+                outv[(j0 + q) * NS + s] = static_cast<float>(own[s]);
+              }
+        }
+        __syncthreads();
+        double dyp[RPT][NS];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+          for (int s = 0; s < NS; ++s)
+            dyp[r][s] = act[r] ? static_cast<double>(outv[(tid * RPT + r) * NS + s]) : 0.0;
+        const unsigned long long n_zero =
+            residual_norm_block<Model, RPT>(mdl, yi, dy, dt, act, s_wlast, s_red, lane, warp);
+        const unsigned long long n_pred =
+            residual_norm_block<Model, RPT>(mdl, yi, dyp, dt, act, s_wlast, s_red, lane, warp);
+        if (n_pred < n_zero) {  // both finite bit patterns compare as values
+#pragma unroll
+          for (int r = 0; r < RPT; ++r)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+              dy[r][s] = dyp[r][s];
+              dyT[r][s] = narrow<T>(dyp[r][s]);
+            }
+          ++pred_used;
+          pred_streak = 0;
+        } else {
+          // k rejections in a row: skip the predictor on the next 2^k - 1 eligible
+          // chunks (k <= 5); n_pred and n_zero are block-wide, so all threads agree
+          ++pred_rejected;
+          pred_streak = min(pred_streak + 1, 5);
+          pred_wait = (1 << pred_streak) - 1;
+        }
       }
     }
 
@@ -227,11 +366,13 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
 
   if (tid == 0) {
     if (a.stats) {
-      int* o = a.stats + static_cast<size_t>(b) * 4;
+      int* o = a.stats + static_cast<size_t>(b) * kStats;
       o[0] = tot_iters;
       o[1] = n_chunks;
       o[2] = retries;
       o[3] = max_it;
+      o[4] = pred_used;
+      o[5] = pred_rejected;
     }
     if (a.series_status) a.series_status[b] = st;
     if (st) atomicMax(a.worst, st);

@@ -1,7 +1,7 @@
 """GPU parity of the neural-ODE (MLP right-hand side) path with the CPU FP64
 oracle, through the C ABI.
 
-Gates (the benchmark spec): 1e-10 relative with FP64 blocks, 1e-5 with FP32 blocks,
+Gates: 1e-10 relative with FP64 blocks, 1e-5 with FP32 blocks,
 per series on the trajectory (max_k |y - y_ref|_inf / max_k |y_ref|_inf) and per
 tensor on the gradients.  The tanh/SiLU networks here are smooth and bounded,
 so the problems are well conditioned and the gates apply directly; the

@@ -135,7 +135,7 @@ def vdp_reference(oracle_lib, tol):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("chunk", [1000, 100, 10, 1])
 def test_vdp_forward_parity_full_size(tvi, oracle_lib, precision, chunk, tol):
-    """Gate per series: max(spec gate, 10 x the forward error that residuals of
+    """Gate per series: max(parity gate, 10 x the forward error that residuals of
     size tol leave after propagation through the linearised recursion)."""
     w, ref, est = vdp_reference(oracle_lib, tol)
     y, stats, status, rc = run_gpu(tvi, w, chunk, precision, tol)
