@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="vdp", choices=sorted(WORKLOADS))
     ap.add_argument("--chunk", type=int, default=None)
-    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "bf16"])
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--rpt", type=int, default=0, help="steps per thread (0 = library default)")
     ap.add_argument("--B", type=int, default=None)
@@ -465,7 +465,7 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32+f64" if args.precision == "fp32" else "f64",
+                "dtype": {"fp32": "f32+f64", "bf16": "bf16+f32+f64"}.get(args.precision, "f64"),
                 "data": "synthetic",
                 "config": dict(workload_config(args),
                                l2="flushed between timed steps (256 MB write)",

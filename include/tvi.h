@@ -40,6 +40,7 @@ typedef enum {
   TVI_ECUDA = -3,         /* a CUDA runtime call failed (text in tvi_last_error) */
   TVI_ENOTCONV = -4,      /* some series hit the Newton iteration limit on a one-step chunk */
   TVI_ENONFINITE = -5,    /* some series produced a NaN/Inf residual on a one-step chunk */
+  TVI_ETIMEOUT = -6,      /* a bounded device wait gave up (tensor-core path); results invalid */
   TVI_EUNSUPPORTED = -7   /* model/precision/size combination not built */
 } tvi_status;
 
@@ -127,7 +128,8 @@ size_t tvi_workspace_bytes(const tvi_model* model, const tvi_options* opt, int B
  *               chunk retries (halvings), largest Newton count of one chunk,
  *               chunks started from the predictor's guess, predictor guesses
  *               rejected because their residual was not below the dy = 0 one.
- *   series_status [B] int32 or NULL: 0 ok, 1 Newton limit, 2 non-finite residual.
+ *   series_status [B] int32 or NULL: 0 ok, 1 Newton limit, 2 non-finite residual,
+ *               3 (every series) a bounded device wait of the tensor-core path gave up.
  *   workspace   >= tvi_workspace_bytes(model, opt, B, N) bytes of device memory.
  * Newton starts every chunk from dy = 0 (Sec. 2.3) and stops per series (Alg. 1,
  * converged series are frozen).  With opt->predictor, a chunk attempt of

@@ -71,6 +71,17 @@ tvi_status check_model(const tvi_model* m) {
   return TVI_OK;
 }
 
+// BF16 block products run on the tensor cores of the MLP path only
+tvi_status check_precision(const tvi_model* m, const tvi_options* o) {
+  if (o->precision != tvi::kPrecBf16) return TVI_OK;
+  if (!is_mlp(m) || !tvi::mlp_tc_supported(m->n, m->hidden1, m->hidden2))
+    return fail(TVI_EUNSUPPORTED,
+                "BF16 blocks are built for MLP models with n in {16, 32}, hidden sizes multiples "
+                "of 16 in [16, 128] and max(hidden) >= 4 n (got kind %d, n %d, hidden %d/%d)",
+                m->kind, m->n, m->hidden1, m->hidden2);
+  return TVI_OK;
+}
+
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // chunk the MLP path runs with: the requested one, at most N (and at least 1)
@@ -85,8 +96,9 @@ tvi_status check_opt(const tvi_options* o) {
   if (o->max_iter < 0) return fail(TVI_EINVAL, "max_iter must be >= 0");
   if (!(o->tol_abs >= 0.0) || !(o->tol_rel >= 0.0))
     return fail(TVI_EINVAL, "tolerances must be >= 0");
-  if (o->precision != tvi::kPrecFp64 && o->precision != tvi::kPrecFp32)
-    return fail(TVI_EUNSUPPORTED, "precision %d is not built for small state sizes", o->precision);
+  if (o->precision != tvi::kPrecFp64 && o->precision != tvi::kPrecFp32 &&
+      o->precision != tvi::kPrecBf16)
+    return fail(TVI_EINVAL, "unknown precision %d", o->precision);
   if (o->predictor &&
       (o->predictor_chunk < 1 || o->predictor_chunk > tvi::kPredMaxChunk ||
        o->predictor_hidden < 2 || o->predictor_hidden > tvi::kPredMaxHidden ||
@@ -151,6 +163,7 @@ tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, 
   tvi_status r = check_model(model);
   if (r != TVI_OK) return r;
   if ((r = check_opt(opt)) != TVI_OK) return r;
+  if ((r = check_precision(model, opt)) != TVI_OK) return r;
   if (B < 0 || N < 0) return fail(TVI_EINVAL, "B and N must be >= 0 (got %d, %d)", B, N);
   if (B == 0) return TVI_OK;
   if (!y0 || !times || !params || !y_out)
@@ -195,6 +208,7 @@ tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, 
                                      opt->precision, a, workspace, s,
                                      opt->sync_status ? &worst : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "tvi_integrate (MLP path)");
+    if (worst == 3) return fail(TVI_ETIMEOUT, "a tensor-core wait gave up; results are invalid");
     if (worst == 2) return fail(TVI_ENONFINITE, "a series produced a non-finite residual");
     if (worst == 1) return fail(TVI_ENOTCONV, "a series hit the Newton iteration limit");
     return TVI_OK;
@@ -225,6 +239,7 @@ tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, in
   tvi_status r = check_model(model);
   if (r != TVI_OK) return r;
   if ((r = check_opt(opt)) != TVI_OK) return r;
+  if ((r = check_precision(model, opt)) != TVI_OK) return r;
   if (B < 0 || N < 0) return fail(TVI_EINVAL, "B and N must be >= 0 (got %d, %d)", B, N);
   if (B == 0) return TVI_OK;
   if (!times || !params || !y || !grad_out || !dparams)
@@ -349,6 +364,7 @@ extern "C" tvi_status tvi_adjoint_noalloc(const tvi_model* model, const tvi_opti
   if (is_mlp(model))
     return fail(TVI_EUNSUPPORTED, "tvi_adjoint_noalloc covers the linear and van der Pol models");
   if ((r = check_opt(opt)) != TVI_OK) return r;
+  if ((r = check_precision(model, opt)) != TVI_OK) return r;
   if (B < 0 || N < 0) return fail(TVI_EINVAL, "B and N must be >= 0 (got %d, %d)", B, N);
   if (B == 0) return TVI_OK;
   if (!times || !params || !y || !grad_out || !dparams)

@@ -64,6 +64,9 @@ cudaError_t small_adjoint(int kind, int n, int precision, int rpt, int threads, 
 // widths <= 128, all multiples of 4.  The chunk in the argument blocks is the
 // effective one (<= N); workspace as sized by mlp_workspace_bytes.
 bool mlp_supported(int n, int h1, int h2);
+// BF16 tensor-core blocks: n in {16, 32}, hidden multiples of 16 in [16, 128],
+// max(h1, h2) >= 4 n
+bool mlp_tc_supported(int n, int h1, int h2);
 size_t mlp_workspace_bytes(int n, int h1, int h2, int B, int chunk, int precision);
 cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const FwdArgs& a,
                         void* workspace, cudaStream_t s, int* host_worst);

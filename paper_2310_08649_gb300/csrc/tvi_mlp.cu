@@ -15,7 +15,7 @@
 //   mlp_check_kernel     per-series convergence (reading C-4); the host reads
 //                        how many series still iterate
 //   mlp_blocks_kernel    J = D3 W3 D2 W2 D1 W1, A = I - dt J, M = A^-1 in the
-//                        block precision
+//                        block precision (Sec. 3.2: factorise the diagonal blocks)
 //   mlp_chain_kernel     d_j = M_j (d_{j-1} + R_j) per series, dy -= d (FP64)
 // The adjoint (App. A.2) runs the chunks in reverse with transposed blocks,
 // FP64 refinement residuals r = g + a_next - a + dt J^T a from an FP64
@@ -25,6 +25,7 @@
 
 #include "tvi_device.cuh"
 #include "tvi_internal.h"
+#include "tvi_tc.cuh"
 
 namespace tvi {
 
@@ -281,6 +282,54 @@ __device__ __forceinline__ T wget(const BlocksArgs& a, int i) {
   else return __ldg(a.Wf + i);
 }
 
+// Gauss-Jordan inverse of one augmented block [A | I] (n x 2n, shared memory)
+// by one warp, partial pivoting, then M = A^-1 stored transposed to Mo
+// (Mo[col][r] = M[r][col]; the adjoint's blocks are M^T, stored untransposed).
+template <typename T>
+__device__ __forceinline__ void gj_invert_store(T* Ap, int n, int lane, T* Mo, int reverse) {
+  for (int kk = 0; kk < n; ++kk) {
+    T best = (lane >= kk && lane < n) ? fabs(Ap[lane * 2 * n + kk]) : T(-1);
+    int piv = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(kFull, best, o);
+      const int op = __shfl_xor_sync(kFull, piv, o);
+      if (ob > best || (ob == best && op < piv)) {
+        best = ob;
+        piv = op;
+      }
+    }
+    if (piv != kk) {
+      for (int col = lane; col < 2 * n; col += 32) {
+        const T tmp = Ap[kk * 2 * n + col];
+        Ap[kk * 2 * n + col] = Ap[piv * 2 * n + col];
+        Ap[piv * 2 * n + col] = tmp;
+      }
+    }
+    __syncwarp();
+    const T inv = T(1) / Ap[kk * 2 * n + kk];
+    __syncwarp();
+    for (int col = lane; col < 2 * n; col += 32) Ap[kk * 2 * n + col] *= inv;
+    __syncwarp();
+    // each lane updates the columns it owns; column kk is read, not written
+    for (int col = lane; col < 2 * n; col += 32) {
+      if (col == kk) continue;
+      const T pk = Ap[kk * 2 * n + col];
+      for (int r = 0; r < n; ++r)
+        if (r != kk) Ap[r * 2 * n + col] = fma(-Ap[r * 2 * n + kk], pk, Ap[r * 2 * n + col]);
+    }
+    __syncwarp();
+    for (int r = lane; r < n; r += 32)
+      if (r != kk) Ap[r * 2 * n + kk] = T(0);
+    __syncwarp();
+  }
+  for (int r = 0; r < n; ++r)
+    for (int col = lane; col < n; col += 32)
+      // stored transposed (Mo[col][r] = M[r][col]) for the chain's conflict-free reads
+      Mo[col * n + r] = reverse ? Ap[col * 2 * n + n + r] : Ap[r * 2 * n + n + col];
+  __syncwarp();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, int TP,
                                                                   int stage_w2) {
@@ -382,58 +431,229 @@ __global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, 
   }
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
-  for (int p = warp; p < np; p += kTileThreads / 32) {
-    T* Ap = sA + p * n * 2 * n;
-    for (int kk = 0; kk < n; ++kk) {
-      T best = (lane >= kk && lane < n) ? fabs(Ap[lane * 2 * n + kk]) : T(-1);
-      int piv = lane;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ob = __shfl_xor_sync(kFull, best, o);
-        const int op = __shfl_xor_sync(kFull, piv, o);
-        if (ob > best || (ob == best && op < piv)) {
-          best = ob;
-          piv = op;
-        }
-      }
-      if (piv != kk) {
-        for (int col = lane; col < 2 * n; col += 32) {
-          const T tmp = Ap[kk * 2 * n + col];
-          Ap[kk * 2 * n + col] = Ap[piv * 2 * n + col];
-          Ap[piv * 2 * n + col] = tmp;
-        }
-      }
-      __syncwarp();
-      const T inv = T(1) / Ap[kk * 2 * n + kk];
-      __syncwarp();
-      for (int col = lane; col < 2 * n; col += 32) Ap[kk * 2 * n + col] *= inv;
-      __syncwarp();
-      // each lane updates the columns it owns; column kk is read, not written
-      for (int col = lane; col < 2 * n; col += 32) {
-        if (col == kk) continue;
-        const T pk = Ap[kk * 2 * n + col];
-        for (int r = 0; r < n; ++r)
-          if (r != kk) Ap[r * 2 * n + col] = fma(-Ap[r * 2 * n + kk], pk, Ap[r * 2 * n + col]);
-      }
-      __syncwarp();
-      for (int r = lane; r < n; r += 32)
-        if (r != kk) Ap[r * 2 * n + kk] = T(0);
-      __syncwarp();
-    }
-    T* Mo = static_cast<T*>(a.M) + (static_cast<size_t>(b) * a.c + j0 + p) * n * n;
-    for (int r = 0; r < n; ++r)
-      for (int col = lane; col < n; col += 32)
-        // stored transposed (Mo[col][r] = M[r][col]) for the chain's conflict-free reads
-        Mo[col * n + r] = a.reverse ? Ap[col * 2 * n + n + r] : Ap[r * 2 * n + n + col];
-    __syncwarp();
+  for (int p = warp; p < np; p += kTileThreads / 32)
+    gj_invert_store<T>(sA + p * n * 2 * n, n, lane,
+                       static_cast<T*>(a.M) + (static_cast<size_t>(b) * a.c + j0 + p) * n * n,
+                       a.reverse);
+}
+
+// ---------------------------------------------------------------------------
+// Jacobian blocks on the tensor cores (precision BF16: BF16 operands, FP32
+// accumulation in tensor memory), n in {16, 32}.  A tile is 128 rows (p, c):
+// TP = 128 / n steps x n Jacobian columns, the M of one tcgen05 MMA.
+//   GEMM 1  G^T[(p,c)][r] = sum_q U^T[(p,c)][q] W2[r][q],  U^T[(p,c)][q] = d1[p][q] W1[q][c]
+//   scale   G^T[(p,c)][r] *= d2[p][r], rounded to BF16 (operand of GEMM 2)
+//   GEMM 2  J^T[(p,c)][r] = sum_s G^T[(p,c)][s] W3[r][s]
+//   blocks  A_p[r][c] = delta_rc - dt_p d3[p][r] J^T[(p,c)][r] in FP32, inverted by
+//           Gauss-Jordan as in mlp_blocks_kernel.
+// Persistent blocks of 128 threads: W2 and W3 (BF16, operand layout) and W1^T
+// (FP32) are staged once, then tiles are taken in turn.  Thread 0 issues the
+// MMAs and commits them to an mbarrier; the four warps (the four TMEM lane
+// quarters) drain the accumulator, warp w reading rows 32 w .. 32 w + 31.  The
+// A operands of the two GEMMs and then the FP32 blocks share one region.  Every wait is bounded: a timeout sets *err and ends the block
+// after a second bounded wait for its MMAs, with the tensor memory freed.
+// ---------------------------------------------------------------------------
+constexpr int kTcThreads = 128;
+constexpr int kTcRows = 128;          // MMA M
+constexpr uint32_t kTcCols = 128;     // TMEM columns: GEMM 1 needs h2 <= 128, GEMM 2 n
+constexpr int kTcWaitLimit = 1 << 24; // mbarrier polls before giving up
+constexpr size_t kTcMinSmem = 58 * 1024;  // <= 3 blocks per SM: 3 x 128 TMEM columns fit
+
+struct TcLayout {
+  uint32_t w2, w3, ug, w1t, dv, total;  // byte offsets in dynamic shared memory
+};
+
+// The A operands of the two GEMMs share one region (U is dead once GEMM 1 has
+// completed), and the FP32 blocks [TP][n][2n] reuse it once GEMM 2 has.
+__host__ __device__ inline TcLayout tc_layout(const MlpDims& d) {
+  TcLayout L;
+  const int tp = kTcRows / d.n;
+  const int hmax = d.h1 > d.h2 ? d.h1 : d.h2;
+  L.w2 = 0;                                   // [h2][h1] BF16, operand layout
+  L.w3 = L.w2 + 2u * d.h2 * d.h1;             // [n][h2] BF16, operand layout
+  L.ug = L.w3 + 2u * d.n * d.h2;              // [128][h1] then [128][h2] BF16, operand layout
+  L.w1t = L.ug + 2u * kTcRows * hmax;         // [n][h1] FP32
+  L.dv = L.w1t + 4u * d.n * d.h1;             // [TP][h1+h2+n] FP32
+  L.total = L.dv + 4u * tp * (d.h1 + d.h2 + d.n);
+  return L;
+}
+
+// the FP32 blocks fit the operand region: 4 * 128 * 2n <= 2 * 128 * max(h1, h2)
+bool tc_supported(const MlpDims& d) {
+  const int hmax = d.h1 > d.h2 ? d.h1 : d.h2;
+  return (d.n == 16 || d.n == 32) && d.h1 % 16 == 0 && d.h2 % 16 == 0 && d.h1 >= 16 &&
+         d.h2 >= 16 && d.h1 <= 128 && d.h2 <= 128 && hmax >= 4 * d.n;
+}
+
+__global__ void __launch_bounds__(kTcThreads) mlp_blocks_tc_kernel(BlocksArgs a, int* err) {
+  extern __shared__ __align__(128) unsigned char tsm[];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ float s_dt[kTcRows / 16];
+  __shared__ int s_stop;
+  const MlpDims d = a.d;
+  const int n = d.n, h1 = d.h1, h2 = d.h2;
+  const int TP = kTcRows / n, ln = __ffs(n) - 1;
+  const int dvs = h1 + h2 + n;
+  const TcLayout Lo = tc_layout(d);
+  unsigned char* sW2 = tsm + Lo.w2;
+  unsigned char* sW3 = tsm + Lo.w3;
+  unsigned char* sU = tsm + Lo.ug;
+  unsigned char* sG = tsm + Lo.ug;
+  float* sW1t = reinterpret_cast<float*>(tsm + Lo.w1t);
+  float* sdv = reinterpret_cast<float*>(tsm + Lo.dv);
+  float* sA = reinterpret_cast<float*>(tsm + Lo.ug);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int oW2 = h1 * n + h1, oW3 = oW2 + h2 * h1 + h2;
+
+  // ---- once per block: weights into shared memory ----
+  for (int e = tid; e < (h2 * h1) >> 1; e += kTcThreads) {
+    const int r = (2 * e) / h1, q = 2 * e - r * h1;
+    *reinterpret_cast<uint32_t*>(sW2 + tc::kmajor_offset(r, q, h1)) =
+        tc::pack_bf16(a.Wf[oW2 + r * h1 + q], a.Wf[oW2 + r * h1 + q + 1]);
   }
+  for (int e = tid; e < (n * h2) >> 1; e += kTcThreads) {
+    const int r = (2 * e) / h2, q = 2 * e - r * h2;
+    *reinterpret_cast<uint32_t*>(sW3 + tc::kmajor_offset(r, q, h2)) =
+        tc::pack_bf16(a.Wf[oW3 + r * h2 + q], a.Wf[oW3 + r * h2 + q + 1]);
+  }
+  for (int e = tid; e < n * h1; e += kTcThreads) {
+    const int q = e >> ln, c = e & (n - 1);
+    sW1t[c * h1 + q] = a.Wf[e];  // W1[q][c]
+  }
+  if (tid == 0) {
+    tc::mbar_init(&s_bar, 1);
+    s_stop = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(&s_tmem, kTcCols);
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  const uint32_t tmem_rows = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  const uint32_t aU = tc::smem_u32(sU), aG = tc::smem_u32(sG);
+  const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3);
+  const uint32_t id1 = tc::idesc_bf16(kTcRows, h2), id2 = tc::idesc_bf16(kTcRows, n);
+  uint32_t phase = 0;
+  const int row = tid, p_row = row >> ln, c_row = row & (n - 1);
+  const int tiles_per = (a.L + TP - 1) / TP;
+  const int total = a.B * tiles_per;
+
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const int b = tile / tiles_per;
+    const int j0 = (tile - b * tiles_per) * TP;
+    if (a.active && !a.active[b]) continue;
+    const int np = min(TP, a.L - j0);
+    const double* dvt = a.dv + (static_cast<size_t>(b) * a.c + j0) * dvs;
+    const int len = a.lengths ? min(max(a.lengths[b], 0), a.N) : a.N;
+    const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
+    if (tid < TP)
+      s_dt[tid] = tid < np ? narrow<float>(step_dt(tb, len, step_of(a.reverse, a.i0, a.L, j0 + tid)))
+                           : 0.0f;
+    for (int e = tid; e < TP * dvs; e += kTcThreads)
+      sdv[e] = e < np * dvs ? narrow<float>(dvt[e]) : 0.0f;
+    __syncthreads();
+    // U^T in the operand layout: 8 consecutive threads fill one core matrix
+    const int kch = h1 >> 3;
+    for (int e = tid; e < kTcRows * kch; e += kTcThreads) {
+      const int r8 = e & 7, rest = e >> 3;
+      const int kg = rest % kch, rg = rest / kch;
+      const int r = rg * 8 + r8, p = r >> ln, c = r & (n - 1);
+      const float* d1 = sdv + p * dvs + kg * 8;
+      const float* w1 = sW1t + c * h1 + kg * 8;
+      uint4 v;
+      v.x = tc::pack_bf16(d1[0] * w1[0], d1[1] * w1[1]);
+      v.y = tc::pack_bf16(d1[2] * w1[2], d1[3] * w1[3]);
+      v.z = tc::pack_bf16(d1[4] * w1[4], d1[5] * w1[5]);
+      v.w = tc::pack_bf16(d1[6] * w1[6], d1[7] * w1[7]);
+      *reinterpret_cast<uint4*>(sU + tc::kmajor_offset(r, kg * 8, h1)) = v;
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {  // GEMM 1
+      tc::fence_after_sync();
+      for (int s = 0; s < (h1 >> 4); ++s)
+        tc::mma_bf16(tmem, tc::smem_desc(aU + 256u * s, 128u, 16u * h1),
+                     tc::smem_desc(aW2 + 256u * s, 128u, 16u * h1), id1, s > 0);
+      tc::mma_commit(&s_bar);
+    }
+    if (!tc::mbar_wait_bounded(&s_bar, phase, kTcWaitLimit)) s_stop = 1;
+    phase ^= 1u;
+    tc::fence_after_sync();
+    __syncthreads();
+    if (s_stop) break;
+    // scale by d2 and round to BF16: row `row` of G^T (over U, consumed by GEMM 1)
+    for (int r0 = 0; r0 < h2; r0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem_rows + r0, v);
+      const float* d2 = sdv + p_row * dvs + h1 + r0;
+      uint4 lo, hi;
+      lo.x = tc::pack_bf16(v[0] * d2[0], v[1] * d2[1]);
+      lo.y = tc::pack_bf16(v[2] * d2[2], v[3] * d2[3]);
+      lo.z = tc::pack_bf16(v[4] * d2[4], v[5] * d2[5]);
+      lo.w = tc::pack_bf16(v[6] * d2[6], v[7] * d2[7]);
+      hi.x = tc::pack_bf16(v[8] * d2[8], v[9] * d2[9]);
+      hi.y = tc::pack_bf16(v[10] * d2[10], v[11] * d2[11]);
+      hi.z = tc::pack_bf16(v[12] * d2[12], v[13] * d2[13]);
+      hi.w = tc::pack_bf16(v[14] * d2[14], v[15] * d2[15]);
+      *reinterpret_cast<uint4*>(sG + tc::kmajor_offset(row, r0, h2)) = lo;
+      *reinterpret_cast<uint4*>(sG + tc::kmajor_offset(row, r0 + 8, h2)) = hi;
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {  // GEMM 2 (overwrites TMEM columns 0 .. n-1, already drained)
+      tc::fence_after_sync();
+      for (int s = 0; s < (h2 >> 4); ++s)
+        tc::mma_bf16(tmem, tc::smem_desc(aG + 256u * s, 128u, 16u * h2),
+                     tc::smem_desc(aW3 + 256u * s, 128u, 16u * h2), id2, s > 0);
+      tc::mma_commit(&s_bar);
+    }
+    if (!tc::mbar_wait_bounded(&s_bar, phase, kTcWaitLimit)) s_stop = 1;
+    phase ^= 1u;
+    tc::fence_after_sync();
+    __syncthreads();
+    if (s_stop) break;
+    // A_p = I - dt_p D3 J_p, augmented with I (over G, consumed by GEMM 2)
+    for (int r0 = 0; r0 < n; r0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem_rows + r0, v);
+      if (p_row < np) {
+        float* Ap = sA + p_row * n * 2 * n;
+        const float dtp = s_dt[p_row];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int r = r0 + i;
+          const float J = sdv[p_row * dvs + h1 + h2 + r] * v[i];
+          Ap[r * 2 * n + c_row] = (r == c_row ? 1.0f : 0.0f) - dtp * J;
+          Ap[r * 2 * n + n + c_row] = r == c_row ? 1.0f : 0.0f;
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    for (int p = warp; p < np; p += kTcThreads / 32)
+      gj_invert_store<float>(sA + p * n * 2 * n, n, lane,
+                             static_cast<float*>(a.M) + (static_cast<size_t>(b) * a.c + j0 + p) * n * n,
+                             a.reverse);
+    __syncthreads();  // blocks (aliasing U, G) consumed before the next tile writes U
+  }
+  if (s_stop) {
+    if (tid == 0) atomicExch(err, 1);
+    tc::mbar_wait_bounded(&s_bar, phase ^ 1u, kTcWaitLimit);  // the MMAs that timed out
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTcCols);
 }
 
 // ---------------------------------------------------------------------------
 // Block substitution d_j = M_j (d_{j-1} + rhs_j), d_{-1} = x_init (Alg. 2 on the
 // normalised blocks): one warp per series, lane r owns component r.  For
 // n = 16-32 this is n^2 work per step against the n^3 per step of a cyclic
-// reduction, the trade-off the paper reports for larger systems.
+// reduction, the trade-off the paper reports for larger systems (Sec. 5.3).
 // The chain is latency bound (one dependent mat-vec per step), so everything
 // that does not depend on d_{j-1} -- the block M_j (stored transposed), rhs_j
 // and the accumulator row x_j -- is staged D steps ahead into a per-warp ring
@@ -786,11 +1006,14 @@ __global__ void mlp_store_kernel(int n, int L, int c, int Np1, int i0, const dou
   }
 }
 
-__global__ void mlp_worst_kernel(int B, const int* status, int* series_status, int* worst) {
+// status 3 for every series when a tensor-core wait gave up (results invalid)
+__global__ void mlp_worst_kernel(int B, const int* status, const int* tcerr, int* series_status,
+                                 int* worst) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
-  if (series_status) series_status[b] = status[b];
-  if (status[b]) atomicMax(worst, status[b]);
+  const int st = *tcerr ? 3 : status[b];
+  if (series_status) series_status[b] = st;
+  if (st) atomicMax(worst, st);
 }
 
 // carry a_{i0+1} (row L-1) to the next (earlier) chunk
@@ -799,11 +1022,16 @@ __global__ void mlp_carry_kernel(int B, int n, int L, int c, const double* av, d
   if (i < B * n) carry[i] = av[(static_cast<size_t>(i / n) * c + (L - 1)) * n + (i % n)];
 }
 
+// gradients are NaN when a tensor-core wait gave up (results invalid)
 __global__ void mlp_adjoint_end_kernel(int B, int n, int Np1, const double* carry, const double* g,
-                                       double* dy0, const double* acc, double* dparams, int P) {
+                                       double* dy0, const double* acc, double* dparams, int P,
+                                       const int* tcerr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (dy0 && i < B * n) dy0[i] = carry[i] + g[static_cast<size_t>(i / n) * Np1 * n + (i % n)];
-  if (i < P) dparams[i] = acc[i];
+  const bool bad = *tcerr != 0;
+  if (dy0 && i < B * n)
+    dy0[i] = bad ? __longlong_as_double(0x7ff8000000000000LL)
+                 : carry[i] + g[static_cast<size_t>(i / n) * Np1 * n + (i % n)];
+  if (i < P) dparams[i] = bad ? __longlong_as_double(0x7ff8000000000000LL) : acc[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -817,7 +1045,7 @@ struct Ws {
   double* dv;
   void* M;
   unsigned long long* norm;
-  int *active, *status, *iters, *remaining, *worst;
+  int *active, *status, *iters, *remaining, *worst, *tcerr;
   size_t total;
 };
 
@@ -833,6 +1061,7 @@ Ws carve(char* base, int B, int c, const MlpDims& d, int precision, bool adjoint
   const size_t tsz = precision == kPrecFp64 ? sizeof(double) : sizeof(float);
   w.worst = reinterpret_cast<int*>(take(sizeof(int)));
   w.remaining = reinterpret_cast<int*>(take(sizeof(int)));
+  w.tcerr = reinterpret_cast<int*>(take(sizeof(int)));
   w.Wf = reinterpret_cast<float*>(take(sizeof(float) * d.P));
   w.yi = reinterpret_cast<double*>(take(sizeof(double) * B * d.n));
   w.carry = reinterpret_cast<double*>(take(sizeof(double) * B * d.n));
@@ -932,6 +1161,33 @@ cudaError_t launch_blocks(const BlocksArgs& bk, int precision, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_blocks_tc(const BlocksArgs& bk, int* err, cudaStream_t s) {
+  const TcLayout Lo = tc_layout(bk.d);
+  const size_t sm = Lo.total < kTcMinSmem ? kTcMinSmem : Lo.total;
+  cudaError_t e = set_smem(mlp_blocks_tc_kernel, sm);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int tp = kTcRows / bk.d.n;
+  const int tiles = bk.B * ((bk.L + tp - 1) / tp);
+  const int per_sm = static_cast<int>(kMaxDynSmem / sm) >= 2 ? 2 : 1;
+  const int grid = tiles < per_sm * sms ? tiles : per_sm * sms;
+  if (grid < 1) return cudaSuccess;
+  mlp_blocks_tc_kernel<<<grid, kTcThreads, sm, s>>>(bk, err);
+  return cudaGetLastError();
+}
+
+// Jacobian blocks in the precision's arithmetic: FP64 / FP32 on the FMA pipes,
+// BF16 products on the tensor cores (blocks and chain then in FP32)
+cudaError_t launch_blocks_any(const BlocksArgs& bk, int precision, int* err, cudaStream_t s) {
+  if (precision == kPrecFp64) return launch_blocks<double>(bk, precision, s);
+  if (precision == kPrecBf16) return launch_blocks_tc(bk, err, s);
+  return launch_blocks<float>(bk, precision, s);
+}
+
 template <typename T>
 cudaError_t launch_chain(const ChainArgs& ch, cudaStream_t s) {
   // ring depth 8 when four warps' rings fit in 200 KB, else 4
@@ -958,6 +1214,10 @@ bool mlp_supported(int n, int h1, int h2) {
   return n_ok && h1 >= 4 && h1 <= 128 && h1 % 4 == 0 && h2 >= 4 && h2 <= 128 && h2 % 4 == 0;
 }
 
+bool mlp_tc_supported(int n, int h1, int h2) {
+  return mlp_supported(n, h1, h2) && tc_supported(dims_of(n, h1, h2));
+}
+
 size_t mlp_workspace_bytes(int n, int h1, int h2, int B, int chunk, int precision) {
   return carve(nullptr, B, chunk, dims_of(n, h1, h2), precision, true).total;
 }
@@ -974,6 +1234,7 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
   const int B = a.B, N = a.N, c = a.chunk;
   Ws w = carve(static_cast<char*>(workspace), B, c, d, precision, false);
   TVI_TRY(cudaMemsetAsync(w.worst, 0, sizeof(int), s));
+  TVI_TRY(cudaMemsetAsync(w.tcerr, 0, sizeof(int), s));
   convert_weights_kernel<<<(d.P + 255) / 256, 256, 0, s>>>(a.params, w.Wf, d.P);
   mlp_start_kernel<<<(B * n + 255) / 256, 256, 0, s>>>(B, n, N + 1, a.y0, a.y_out, w.yi, w.status);
   TVI_TRY(cudaGetLastError());
@@ -1006,18 +1267,13 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
       ChainArgs ch{};
       ch.B = B; ch.n = n; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 0; ch.M = w.M;
       ch.rhs_buf = w.R; ch.active = w.active; ch.x = w.dy; ch.mode = 0;
-      if (precision == kPrecFp64) {
-        TVI_TRY(launch_blocks<double>(bk, precision, s));
-        TVI_TRY(launch_chain<double>(ch, s));
-      } else {
-        TVI_TRY(launch_blocks<float>(bk, precision, s));
-        TVI_TRY(launch_chain<float>(ch, s));
-      }
+      TVI_TRY(launch_blocks_any(bk, precision, w.tcerr, s));
+      TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s));
     }
     mlp_store_kernel<<<B, 128, 0, s>>>(n, L, c, N + 1, i0, w.dy, w.yi, a.y_out, w.iters, a.stats);
     TVI_TRY(cudaGetLastError());
   }
-  mlp_worst_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, w.status, a.series_status, w.worst);
+  mlp_worst_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, w.status, w.tcerr, a.series_status, w.worst);
   TVI_TRY(cudaGetLastError());
   if (host_worst) {
     TVI_TRY(cudaMemcpyAsync(host_worst, w.worst, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1031,6 +1287,7 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
   const MlpDims d = dims_of(n, h1, h2);
   const int B = a.B, N = a.N, c = a.chunk;
   Ws w = carve(static_cast<char*>(workspace), B, c, d, precision, true);
+  TVI_TRY(cudaMemsetAsync(w.tcerr, 0, sizeof(int), s));
   convert_weights_kernel<<<(d.P + 255) / 256, 256, 0, s>>>(a.params, w.Wf, d.P);
   TVI_TRY(cudaMemsetAsync(w.carry, 0, sizeof(double) * B * n, s));  // a_{N+1} = 0
   TVI_TRY(cudaMemsetAsync(w.acc, 0, sizeof(double) * d.P, s));
@@ -1053,13 +1310,8 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
     ChainArgs ch{};
     ch.B = B; ch.n = n; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 1; ch.M = w.M;
     ch.rhs_traj = a.grad_out; ch.x_init = w.carry; ch.x = w.dy; ch.mode = 1;
-    if (precision == kPrecFp64) {
-      TVI_TRY(launch_blocks<double>(bk, precision, s));
-      TVI_TRY(launch_chain<double>(ch, s));
-    } else {
-      TVI_TRY(launch_blocks<float>(bk, precision, s));
-      TVI_TRY(launch_chain<float>(ch, s));
-    }
+    TVI_TRY(launch_blocks_any(bk, precision, w.tcerr, s));
+    TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s));
     VjpArgs v{};
     v.d = d; v.B = B; v.N = N; v.i0 = i0; v.L = L; v.c = c; v.times = a.times;
     v.lengths = a.lengths; v.params = a.params; v.ytraj = a.y; v.g = a.grad_out;
@@ -1100,7 +1352,7 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
   }
   const int cnt = (B * n > d.P) ? B * n : d.P;
   mlp_adjoint_end_kernel<<<(cnt + 255) / 256, 256, 0, s>>>(B, n, N + 1, w.carry, a.grad_out, a.dy0,
-                                                          w.acc, a.dparams, d.P);
+                                                          w.acc, a.dparams, d.P, w.tcerr);
   return cudaGetLastError();
 }
 

@@ -59,7 +59,15 @@ def test_argument_errors_are_returned_without_touching_the_gpu(lib):
                                  vp, None, None, ws, ws_bytes, None)
     assert call(m, Options(chunk=0).c()) == -1
     assert call(m, Options(tol_abs=-1.0).c()) == -1
-    assert call(m, Options(precision="bf16").c()) == -7
+    assert call(m, Options(precision="bf16").c()) == -7  # BF16 blocks: MLP path only
+    bf = Options(precision="bf16").c()
+    assert call(Model("mlp_tanh", 8, (64, 64)).c(), bf) == -7    # n < 16
+    assert call(Model("mlp_tanh", 16, (48, 36)).c(), bf) == -7   # 36 not a multiple of 16
+    assert call(Model("mlp_silu", 32, (64, 64)).c(), bf) == -7   # max(hidden) < 4 n
+    assert call(Model("mlp_silu", 32, (128, 128)).c(), bf, ws=None) == -2  # accepted, then ws
+    unknown = Options().c()
+    unknown.precision = 7
+    assert call(m, unknown) == -1
     assert call(Model("vdp", 3).c(), Options().c()) == -1
     assert call(Model("linear", 3).c(), Options().c()) == -7
     assert call(m, Options().c(), B=-1) == -1

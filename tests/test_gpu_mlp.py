@@ -1,8 +1,10 @@
 """GPU parity of the neural-ODE (MLP right-hand side) path with the CPU FP64
 oracle, through the C ABI.
 
-Gates: 1e-10 relative with FP64 blocks, 1e-5 with FP32 blocks,
-per series on the trajectory (max_k |y - y_ref|_inf / max_k |y_ref|_inf) and per
+Gates: 1e-10 relative with FP64 blocks, 1e-5 with FP32 blocks and with BF16
+block products (the Newton residual and the adjoint refinement residuals are
+FP64 in every mode, so the block precision changes iteration counts, not the
+converged result), per series on the trajectory (max_k |y - y_ref|_inf / max_k |y_ref|_inf) and per
 tensor on the gradients.  The tanh/SiLU networks here are smooth and bounded,
 so the problems are well conditioned and the gates apply directly; the
 trajectories are compared at a tight Newton tolerance (1e-12) so that both
@@ -17,7 +19,7 @@ from oracle import Model as OModel
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-GATE = {"fp64": 1e-10, "fp32": 1e-5}
+GATE = {"fp64": 1e-10, "fp32": 1e-5, "bf16": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -140,3 +142,76 @@ def test_mlp_status_and_rejections(tvi):
     with pytest.raises(L.TviError):  # hidden width not a multiple of 4
         tvi.integrate(tvi.Model.from_spec(bad["spec"]), tvi.Options(chunk=5), dev(bad["y0"]),
                       dev(bad["times"]), dev(bad["params"]))
+
+
+# ---------------------------------------------------------------------------
+# BF16 block products on the tensor cores (n >= 16)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("act", ["tanh", "silu"])
+@pytest.mark.parametrize("chunk", [1, 7, 40, 120])
+def test_bf16_blocks_small(tvi, oracle_lib, act, chunk):
+    """Ragged tiles (chunk 7 and the 120-step tail of 40-step chunks are not
+    multiples of the 8 steps of a 128-row tile) and one-step chunks."""
+    w = workloads.mlp_ode(B=3, N=120, n=16, hidden=(64, 64), act=act, t_end=3.0, seed=67)
+    m = OModel.from_spec(w["spec"])
+    ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], tol_abs=1e-12)
+    assert not st.any()
+    y, stats, status, rc = gpu_forward(tvi, w, chunk, "bf16", 1e-12)
+    assert rc == 0 and not status.any()
+    assert relerr_series(y, ref).max() <= GATE["bf16"]
+    g = workloads.random_grad_out(68, 3, 120, 16)
+    dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g)
+    dp, dy0 = gpu_adjoint(tvi, w, chunk, "bf16", ref, g)
+    assert relerr(dp, dp_ref) <= GATE["bf16"]
+    assert relerr(dy0, dy0_ref) <= GATE["bf16"]
+
+
+def test_bf16_blocks_are_the_jacobian(tvi, node16):
+    """Without refinement the adjoint is exactly the chain of the blocks, so its
+    error measures the blocks themselves.  BF16 rounding (2^-9 relative) of the
+    products making dt J, |dt J| ~ 0.05, perturbs each step by ~1e-4, which over
+    2000 steps accumulates to a few 1e-3 at most; a wrong operand layout, a
+    transposed block or a dropped scaling perturbs each step by O(|dt J|) and the
+    gradient by O(1).  FP32 blocks give the floor of the same measurement."""
+    w, ref, g, dp_ref, dy0_ref, _ = node16
+    dp32, _ = gpu_adjoint(tvi, w, 200, "fp32", ref, g, refine=0)
+    dp16, dy016 = gpu_adjoint(tvi, w, 200, "bf16", ref, g, refine=0)
+    e32, e16 = relerr(dp32, dp_ref), relerr(dp16, dp_ref)
+    assert e32 <= 1e-4, (e32, e16)
+    assert e16 <= 5e-3, (e32, e16)
+    assert relerr(dy016, dy0_ref) <= 5e-3
+
+
+def test_bf16_node16_full_size(tvi, node16):
+    w, ref, g, dp_ref, dy0_ref, est = node16
+    y32, s32, _, rc32 = gpu_forward(tvi, w, 200, "fp32", 1e-12)
+    y, stats, status, rc = gpu_forward(tvi, w, 200, "bf16", 1e-12)
+    assert rc == 0 and rc32 == 0 and not status.any()
+    err = relerr_series(y, ref)
+    assert np.all(err <= np.maximum(GATE["bf16"], 10.0 * est)), (err.max(), est.max())
+    # inexact-Newton blocks cost few extra updates; a wrong Jacobian costs many
+    assert stats[:, 0].sum() <= 1.3 * s32[:, 0].sum(), (stats[:, 0].sum(), s32[:, 0].sum())
+    dp, dy0 = gpu_adjoint(tvi, w, 200, "bf16", ref, g)
+    assert relerr(dp, dp_ref) <= GATE["bf16"]
+    assert relerr(dy0, dy0_ref) <= GATE["bf16"]
+
+
+def test_bf16_node32_silu_padded_lengths(tvi, oracle_lib):
+    w = workloads.mlp_large(B=4, N=1200, lengths_range=(200, 1200))
+    m = OModel.from_spec(w["spec"])
+    lens = w["lengths"]
+    ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], lengths=lens,
+                                    tol_abs=1e-12)
+    assert not st.any()
+    g = workloads.random_grad_out(64, 4, 1200, 32)
+    for b, L in enumerate(lens):
+        g[b, L + 1:] = 0.0
+    dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g, lengths=lens)
+    y, _, status, rc = gpu_forward(tvi, w, 500, "bf16", 1e-12, lengths=lens)
+    assert rc == 0 and not status.any()
+    for b, L in enumerate(lens):
+        assert np.all(y[b, L + 1:] == y[b, L])
+    assert relerr_series(y, ref).max() <= GATE["bf16"]
+    dp, dy0 = gpu_adjoint(tvi, w, 500, "bf16", ref, g, lengths=lens)
+    assert relerr(dp, dp_ref) <= GATE["bf16"]
+    assert relerr(dy0, dy0_ref) <= GATE["bf16"]
