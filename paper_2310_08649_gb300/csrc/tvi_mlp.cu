@@ -485,15 +485,40 @@ bool tc_supported(const MlpDims& d) {
          d.h2 >= 16 && d.h1 <= 128 && d.h2 <= 128 && hmax >= 4 * d.n;
 }
 
+constexpr float kNeumannMaxNorm = 0.125f;
+
+// The NN x NN diagonal block of a 128 x 128 accumulator for row `32 warp + lane`:
+// columns NN p .. NN p + NN - 1 of its step p.  A warp's rows cover columns
+// 32 warp .. 32 warp + 31; for NN = 16 the two half-warps take one half each.
+template <int NN>
+__device__ __forceinline__ void tmem_diag_block(uint32_t tmem_rows, int warp, int lane,
+                                                float (&q)[NN]) {
+  float lo[16], hi[16];
+  tc::tmem_ld16(tmem_rows + 32u * warp, lo);
+  tc::tmem_ld16(tmem_rows + 32u * warp + 16u, hi);
+  if constexpr (NN == 32) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      q[i] = lo[i];
+      q[16 + i] = hi[i];
+    }
+  } else {
+    const bool upper = lane >= 16;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) q[i] = upper ? hi[i] : lo[i];
+  }
+}
+
+template <int NN>
 __global__ void __launch_bounds__(kTcThreads) mlp_blocks_tc_kernel(BlocksArgs a, int* err) {
   extern __shared__ __align__(128) unsigned char tsm[];
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_tmem;
-  __shared__ float s_dt[kTcRows / 16];
+  __shared__ float s_dt[kTcRows / NN];
   __shared__ int s_stop;
   const MlpDims d = a.d;
-  const int n = d.n, h1 = d.h1, h2 = d.h2;
-  const int TP = kTcRows / n, ln = __ffs(n) - 1;
+  constexpr int n = NN, TP = kTcRows / NN, ln = NN == 16 ? 4 : 5;
+  const int h1 = d.h1, h2 = d.h2;
   const int dvs = h1 + h2 + n;
   const TcLayout Lo = tc_layout(d);
   unsigned char* sW2 = tsm + Lo.w2;
@@ -535,6 +560,7 @@ __global__ void __launch_bounds__(kTcThreads) mlp_blocks_tc_kernel(BlocksArgs a,
   const uint32_t aU = tc::smem_u32(sU), aG = tc::smem_u32(sG);
   const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3);
   const uint32_t id1 = tc::idesc_bf16(kTcRows, h2), id2 = tc::idesc_bf16(kTcRows, n);
+  const uint32_t id3 = tc::idesc_bf16(kTcRows, kTcRows);
   uint32_t phase = 0;
   const int row = tid, p_row = row >> ln, c_row = row & (n - 1);
   const int tiles_per = (a.L + TP - 1) / TP;
@@ -616,28 +642,128 @@ __global__ void __launch_bounds__(kTcThreads) mlp_blocks_tc_kernel(BlocksArgs a,
     tc::fence_after_sync();
     __syncthreads();
     if (s_stop) break;
-    // A_p = I - dt_p D3 J_p, augmented with I (over G, consumed by GEMM 2)
-    for (int r0 = 0; r0 < n; r0 += 16) {
+    // X_p = dt_p D3 J_p; thread (p, c) holds column c of X_p in FP32
+    float x[NN];
+#pragma unroll
+    for (int r0 = 0; r0 < NN; r0 += 16) {
       float v[16];
       tc::tmem_ld16(tmem_rows + r0, v);
+      const float dtp = s_dt[p_row];
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        x[r0 + i] = p_row < np ? dtp * (sdv[p_row * dvs + h1 + h2 + r0 + i] * v[i]) : 0.0f;
+    }
+    // ||X_p||_1 (largest column sum) over the NN lanes holding step p
+    float cs = 0.0f;
+#pragma unroll
+    for (int r = 0; r < NN; ++r) cs += fabsf(x[r]);
+#pragma unroll
+    for (int o = NN / 2; o > 0; o >>= 1) cs = fmaxf(cs, __shfl_xor_sync(kFull, cs, o));
+    tc::fence_before_sync();
+    if (__syncthreads_or(!(cs <= kNeumannMaxNorm))) {
+      // a step with ||X||_1 > 1/8 (or not finite): Gauss-Jordan on A = I - X for the tile
       if (p_row < np) {
         float* Ap = sA + p_row * n * 2 * n;
-        const float dtp = s_dt[p_row];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int r = r0 + i;
-          const float J = sdv[p_row * dvs + h1 + h2 + r] * v[i];
-          Ap[r * 2 * n + c_row] = (r == c_row ? 1.0f : 0.0f) - dtp * J;
+        for (int r = 0; r < NN; ++r) {
+          Ap[r * 2 * n + c_row] = (r == c_row ? 1.0f : 0.0f) - x[r];
           Ap[r * 2 * n + n + c_row] = r == c_row ? 1.0f : 0.0f;
+        }
+      }
+      __syncthreads();
+      for (int p = warp; p < np; p += kTcThreads / 32)
+        gj_invert_store<float>(sA + p * n * 2 * n, n, lane,
+                               static_cast<float*>(a.M) + (static_cast<size_t>(b) * a.c + j0 + p) * n * n,
+                               a.reverse);
+      __syncthreads();
+      continue;
+    }
+    // Neumann series A^-1 = I + X + X^2 + X^3 + O(||X||^4) (<= 2.9e-4 at ||X||_1 <= 1/8),
+    // in the transposed form Y = X^T so that every thread keeps its column of X:
+    //   P1 = Y Y, P2 = Y^2 (I + Y) on the tensor cores (block-diagonal parts of
+    //   128 x 128 products), then column c of M = e_c + X[.][c] + row c of P2.
+    unsigned char* sAY = tsm + Lo.ug;         // rows (p, c): Y_p[c][k] = X_p[k][c]
+    unsigned char* sBX = sAY + 256 * NN;      // rows (p, j): X_p[j][k]       (B of P1)
+    unsigned char* sBIX = sBX + 256 * NN;     // rows (p, j): (I + X_p)[j][k] (B of P2)
+    unsigned char* sAY2 = sBIX + 256 * NN;    // rows (p, c): (Y_p^2)[c][k]   (A of P2)
+#pragma unroll
+    for (int k0 = 0; k0 < NN; k0 += 8) {
+      uint4 v;
+      v.x = tc::pack_bf16(x[k0], x[k0 + 1]);
+      v.y = tc::pack_bf16(x[k0 + 2], x[k0 + 3]);
+      v.z = tc::pack_bf16(x[k0 + 4], x[k0 + 5]);
+      v.w = tc::pack_bf16(x[k0 + 6], x[k0 + 7]);
+      *reinterpret_cast<uint4*>(sAY + tc::kmajor_offset(row, k0, NN)) = v;
+    }
+#pragma unroll
+    for (int j = 0; j < NN; ++j) {
+      const int rj = p_row * NN + j;
+      const uint32_t two = tc::pack_bf16(x[j], x[j] + (j == c_row ? 1.0f : 0.0f));
+      *reinterpret_cast<uint16_t*>(sBX + tc::kmajor_offset(rj, c_row, NN)) =
+          static_cast<uint16_t>(two & 0xFFFFu);
+      *reinterpret_cast<uint16_t*>(sBIX + tc::kmajor_offset(rj, c_row, NN)) =
+          static_cast<uint16_t>(two >> 16);
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {  // P1 = Y Y
+      tc::fence_after_sync();
+#pragma unroll
+      for (int s = 0; s < NN / 16; ++s)
+        tc::mma_bf16(tmem, tc::smem_desc(tc::smem_u32(sAY) + 256u * s, 128u, 16u * NN),
+                     tc::smem_desc(tc::smem_u32(sBX) + 256u * s, 128u, 16u * NN), id3, s > 0);
+      tc::mma_commit(&s_bar);
+    }
+    if (!tc::mbar_wait_bounded(&s_bar, phase, kTcWaitLimit)) s_stop = 1;
+    phase ^= 1u;
+    tc::fence_after_sync();
+    __syncthreads();
+    if (s_stop) break;
+    {  // row c of Y^2 -> A operand of P2
+      float q[NN];
+      tmem_diag_block<NN>(tmem_rows, warp, lane, q);
+#pragma unroll
+      for (int k0 = 0; k0 < NN; k0 += 8) {
+        uint4 v;
+        v.x = tc::pack_bf16(q[k0], q[k0 + 1]);
+        v.y = tc::pack_bf16(q[k0 + 2], q[k0 + 3]);
+        v.z = tc::pack_bf16(q[k0 + 4], q[k0 + 5]);
+        v.w = tc::pack_bf16(q[k0 + 6], q[k0 + 7]);
+        *reinterpret_cast<uint4*>(sAY2 + tc::kmajor_offset(row, k0, NN)) = v;
+      }
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {  // P2 = Y^2 (I + Y)
+      tc::fence_after_sync();
+#pragma unroll
+      for (int s = 0; s < NN / 16; ++s)
+        tc::mma_bf16(tmem, tc::smem_desc(tc::smem_u32(sAY2) + 256u * s, 128u, 16u * NN),
+                     tc::smem_desc(tc::smem_u32(sBIX) + 256u * s, 128u, 16u * NN), id3, s > 0);
+      tc::mma_commit(&s_bar);
+    }
+    if (!tc::mbar_wait_bounded(&s_bar, phase, kTcWaitLimit)) s_stop = 1;
+    phase ^= 1u;
+    tc::fence_after_sync();
+    __syncthreads();
+    if (s_stop) break;
+    {  // column c of M: M[j][c] = delta_jc + X[j][c] + (X^2 (I + X))[j][c]
+      float q[NN];
+      tmem_diag_block<NN>(tmem_rows, warp, lane, q);
+      if (p_row < np) {
+        float* Mo = static_cast<float*>(a.M) + (static_cast<size_t>(b) * a.c + j0 + p_row) * n * n;
+#pragma unroll
+        for (int j = 0; j < NN; ++j) {
+          const float m = (j == c_row ? 1.0f : 0.0f) + x[j] + q[j];
+          // forward blocks stored transposed (Mo[c][j] = M[j][c]); adjoint blocks M^T
+          if (a.reverse) Mo[j * n + c_row] = m;
+          else Mo[c_row * n + j] = m;
         }
       }
     }
     tc::fence_before_sync();
-    __syncthreads();
-    for (int p = warp; p < np; p += kTcThreads / 32)
-      gj_invert_store<float>(sA + p * n * 2 * n, n, lane,
-                             static_cast<float*>(a.M) + (static_cast<size_t>(b) * a.c + j0 + p) * n * n,
-                             a.reverse);
     __syncthreads();  // blocks (aliasing U, G) consumed before the next tile writes U
   }
   if (s_stop) {
@@ -1164,7 +1290,8 @@ cudaError_t launch_blocks(const BlocksArgs& bk, int precision, cudaStream_t s) {
 cudaError_t launch_blocks_tc(const BlocksArgs& bk, int* err, cudaStream_t s) {
   const TcLayout Lo = tc_layout(bk.d);
   const size_t sm = Lo.total < kTcMinSmem ? kTcMinSmem : Lo.total;
-  cudaError_t e = set_smem(mlp_blocks_tc_kernel, sm);
+  cudaError_t e = bk.d.n == 16 ? set_smem(mlp_blocks_tc_kernel<16>, sm)
+                                : set_smem(mlp_blocks_tc_kernel<32>, sm);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   e = cudaGetDevice(&dev);
@@ -1176,7 +1303,10 @@ cudaError_t launch_blocks_tc(const BlocksArgs& bk, int* err, cudaStream_t s) {
   const int per_sm = static_cast<int>(kMaxDynSmem / sm) >= 2 ? 2 : 1;
   const int grid = tiles < per_sm * sms ? tiles : per_sm * sms;
   if (grid < 1) return cudaSuccess;
-  mlp_blocks_tc_kernel<<<grid, kTcThreads, sm, s>>>(bk, err);
+  if (bk.d.n == 16)
+    mlp_blocks_tc_kernel<16><<<grid, kTcThreads, sm, s>>>(bk, err);
+  else
+    mlp_blocks_tc_kernel<32><<<grid, kTcThreads, sm, s>>>(bk, err);
   return cudaGetLastError();
 }
 
