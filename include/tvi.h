@@ -67,7 +67,10 @@ typedef enum {
 typedef enum {
   TVI_PREC_FP64 = 0,
   TVI_PREC_FP32 = 1,
-  TVI_PREC_BF16 = 2       /* BF16 block products, FP32 accumulation (n >= 16) */
+  TVI_PREC_BF16 = 2       /* MLP models with n in {16, 32}: Jacobian products on the
+                             tensor cores in BF16 with FP32 accumulation, block inverse
+                             by a tensor-core Neumann series (Gauss-Jordan when
+                             ||dt D3 J||_1 > 1/8), chain in FP32 */
 } tvi_precision;
 
 typedef struct {
