@@ -43,8 +43,8 @@ FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 rate (recipe table); no measure
 WORKLOADS = {
     "vdp": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 128, "N": 10000},
     "vdp_pred": {"chunk": 100, "precision": "fp32", "tol": 1e-8, "B": 128, "N": 10000},
-    "node16": {"chunk": 200, "precision": "fp32", "tol": 1e-8, "B": 64, "N": 2000},
-    "node32": {"chunk": 1000, "precision": "fp32", "tol": 1e-8, "B": 512, "N": 20000},
+    "node16": {"chunk": 200, "precision": "bf16", "tol": 1e-8, "B": 64, "N": 2000},
+    "node32": {"chunk": 1000, "precision": "bf16", "tol": 1e-8, "B": 512, "N": 20000},
 }
 
 
@@ -245,6 +245,11 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # Roofline of the dominant kernel (FP64 pipe)
 # ---------------------------------------------------------------------------
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu --set full capture
+# of the default van der Pol workload (forward, adjoint); other workloads: not captured
+NCU_TRAFFIC = {("vdp", 1000, "fp32", 128, 10000): (10312448 + 1024, 51243520 + 26368)}
+
+
 def roofline(args, w, stats, fwd_ms, adj_ms, refine):
     """Both paths are bound by the FP64 pipe (the FP64 residual).  Every FP64 add,
     multiply or FMA takes one FP64 issue slot, and the nominal 1.25 TFLOP/s counts
@@ -265,20 +270,25 @@ def roofline(args, w, stats, fwd_ms, adj_ms, refine):
         names = ("forward_small_kernel<vdp,fp32>", "adjoint_small_kernel<vdp,fp32>")
     else:
         n, (h1, h2) = w["spec"]["n"], w["spec"]["hidden"]
-        fma = n * h1 + h1 * h2 + h2 * n  # FP64 FMAs of one MLP evaluation (activations not counted)
+        fma = n * h1 + h1 * h2 + h2 * n  # FMAs of one MLP evaluation (activations not counted)
+        # forward: one FP64 MLP evaluation per pair per Newton pass (the residual)
         fwd_ops = float(np.sum((upd + nchk) * spc) * fma)
-        # adjoint: FP64 forward + backward per refinement sweep and for the gradient factors
-        adj_ops = float(B * N * (refine + 1) * 2 * fma)
+        # adjoint: a derivative pass and refine + 1 backward passes per pair, in FP64
+        # with FP64 blocks; in FP32 with FP32 / BF16 blocks (no FP64 roof)
+        adj_ops = float(B * N * (refine + 2) * fma) if args.precision == "fp64" else 0.0
         names = ("tvi_integrate (MLP path: FP64 residual kernel dominant)",
-                 "tvi_adjoint (MLP path: FP64 VJP kernel dominant)")
-    name, ops, ms = (names[0], fwd_ops, fwd_ms) if fwd_ms >= adj_ms else (names[1], adj_ops, adj_ms)
+                 "tvi_adjoint (MLP path: FP64 derivative and VJP kernels)")
+    fwd_first = fwd_ms >= adj_ms or adj_ops == 0.0
+    name, ops, ms = (names[0], fwd_ops, fwd_ms) if fwd_first else (names[1], adj_ops, adj_ms)
     achieved = 2.0 * ops / (ms / 1e3) / 1e12
+    cap = NCU_TRAFFIC.get((args.workload, args.chunk, args.precision, args.B, args.N))
+    traffic = None if cap is None else (cap[0] if fwd_first else cap[1])
     return {"kernel": name, "bound": "alu", "pipe": "fp64", "achieved": achieved,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "counting": "FMA-equivalent: 2 x FP64 pipe operations (add, mul, fma)",
             "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table); "
                            "an FMA loop measured 1.20 TFLOP/s on this part",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
             "fwd_ms": fwd_ms, "adj_ms": adj_ms, "fwd_fp64_ops": fwd_ops, "adj_fp64_ops": adj_ops}
 
 

@@ -154,8 +154,9 @@ __device__ __forceinline__ void block_inverse(const T (&A)[NS][NS], T (&X)[NS][N
 // to_f32_trunc rounds toward zero (drops the low 29 fraction bits); values
 // below the normal binary32 range become signed zero, above it signed
 // infinity; NaN stays NaN.  to_f64 is exact for normal floats and maps
-// subnormal floats to signed zero.  Both feed only the FP32 block algebra of
-// an inexact Newton iteration, whose FP64 residual decides convergence.
+// subnormal floats to signed zero.  Both feed only FP32 work -- the block
+// algebra of an inexact Newton iteration, whose FP64 residual decides
+// convergence, and the FP32 passes of the mixed-precision adjoint.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float to_f32_trunc(double x) {
   const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(x));

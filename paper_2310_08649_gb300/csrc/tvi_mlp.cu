@@ -17,10 +17,15 @@
 //   mlp_blocks_kernel    J = D3 W3 D2 W2 D1 W1, A = I - dt J, M = A^-1 in the
 //                        block precision (Sec. 3.2: factorise the diagonal blocks)
 //   mlp_chain_kernel     d_j = M_j (d_{j-1} + R_j) per series, dy -= d (FP64)
-// The adjoint (App. A.2) runs the chunks in reverse with transposed blocks,
-// FP64 refinement residuals r = g + a_next - a + dt J^T a from an FP64
+// The adjoint (App. A.2) runs the chunks in reverse with transposed blocks: a
+// derivative pass at the stored trajectory (mlp_residual_kernel in reverse
+// mode, which also keeps the activations), refinement residuals
+// r = g + a_next - a + dt J^T a assembled in FP64 around a backward-only
 // vector-Jacobian product (mlp_vjp_kernel), and the parameter gradient
 // sum_k dt_k (dh/dp)^T a_k as tiled outer-product sums (mlp_param_grad_kernel).
+// With FP64 blocks every MLP pass is FP64; with FP32 / BF16 blocks the
+// adjoint's MLP passes run in FP32 (64x the FP64 rate on this part), which
+// bounds the gradient's relative error near 1e-7 instead of 1e-15.
 #include <cuda_runtime.h>
 
 #include "tvi_device.cuh"
@@ -37,12 +42,14 @@ struct MlpDims {
   int n, h1, h2, P;
 };
 
+template <typename T>
 struct MlpW {
-  const double *W1, *b1, *W2, *b2, *W3, *b3;
+  const T *W1, *b1, *W2, *b2, *W3, *b3;
 };
 
-__device__ __forceinline__ MlpW mlp_split(const double* p, const MlpDims& d) {
-  MlpW w;
+template <typename T>
+__device__ __forceinline__ MlpW<T> mlp_split(const T* p, const MlpDims& d) {
+  MlpW<T> w;
   w.W1 = p;
   w.b1 = w.W1 + d.h1 * d.n;
   w.W2 = w.b1 + d.h1;
@@ -52,27 +59,32 @@ __device__ __forceinline__ MlpW mlp_split(const double* p, const MlpDims& d) {
   return w;
 }
 
-// activation and its derivative (FP64)
-template <int KIND>
-__device__ __forceinline__ void act_hidden(double z, double& a, double& da) {
+// activation and its derivative, in the arithmetic of T (FP64 or FP32)
+__device__ __forceinline__ double tanh_t(double z) { return tanh(z); }
+__device__ __forceinline__ float tanh_t(float z) { return tanhf(z); }
+__device__ __forceinline__ double exp_t(double z) { return exp(z); }
+__device__ __forceinline__ float exp_t(float z) { return expf(z); }
+
+template <int KIND, typename T>
+__device__ __forceinline__ void act_hidden(T z, T& a, T& da) {
   if constexpr (KIND == kKindMlpTanh) {
-    a = tanh(z);
-    da = 1.0 - a * a;
+    a = tanh_t(z);
+    da = T(1) - a * a;
   } else {
-    const double s = 1.0 / (1.0 + exp(-z));
+    const T s = T(1) / (T(1) + exp_t(-z));
     a = z * s;
-    da = s + z * s * (1.0 - s);
+    da = s + z * s * (T(1) - s);
   }
 }
 
-template <int KIND>
-__device__ __forceinline__ void act_out(double z, double& a, double& da) {
+template <int KIND, typename T>
+__device__ __forceinline__ void act_out(T z, T& a, T& da) {
   if constexpr (KIND == kKindMlpTanh) {
-    a = tanh(z);
-    da = 1.0 - a * a;
+    a = tanh_t(z);
+    da = T(1) - a * a;
   } else {
     a = z;
-    da = 1.0;
+    da = T(1);
   }
 }
 
@@ -85,47 +97,44 @@ __device__ __forceinline__ double step_dt(const double* tb, int len, int k) {
 }
 
 // ---------------------------------------------------------------------------
-// FP64 forward pass for a tile of TP pairs held in shared memory.  Thread t
-// takes pair p = t % TP and every G-th output row (G = threads / TP), so the
-// lanes of a warp read the same weight row (broadcast through the read-only
-// cache).  Layouts [row][TP] keep the pairs contiguous (no bank conflicts).
+// Forward pass (in T: FP64, or FP32 for the mixed-precision adjoint) for a tile
+// of TP pairs held in shared memory.  Thread t takes pair p = t % TP and every
+// G-th output row (G = threads / TP), so the lanes of a warp read the same
+// weight row (broadcast through the read-only cache).  Layouts [row][TP] keep
+// the pairs contiguous (no bank conflicts).
 //   sy [n][TP] in; sa1 [h1][TP], sa2 [h2][TP], sz3 [n][TP] out;
-//   sd1, sd2 (optional) receive act'(z) of the hidden layers (FP64);
-//   dv_tile (optional) receives act'(z) of the hidden layers ([pair][dvs]).
+//   dv_tile (optional) receives act'(z) of the hidden layers ([pair][dvs], FP64).
 // ---------------------------------------------------------------------------
-template <int KIND, int TP>
-__device__ __forceinline__ void mlp_tile_forward(const MlpW& w, const MlpDims& d, const double* sy,
-                                                 double* sa1, double* sa2, double* sz3,
-                                                 double* sd1, double* sd2, int np,
-                                                 double* dv_tile, int dvs) {
+template <int KIND, int TP, typename T>
+__device__ __forceinline__ void mlp_tile_forward(const MlpW<T>& w, const MlpDims& d, const T* sy,
+                                                 T* sa1, T* sa2, T* sz3, int np, double* dv_tile,
+                                                 int dvs) {
   constexpr int G = kTileThreads / TP;
   const int t = threadIdx.x, p = t % TP, g = t / TP;
   const bool live = p < np;
   for (int r = g; r < d.h1; r += G) {
-    double acc = w.b1[r];
-    const double* wr = w.W1 + r * d.n;
+    T acc = w.b1[r];
+    const T* wr = w.W1 + r * d.n;
     for (int c = 0; c < d.n; ++c) acc = fma(__ldg(wr + c), sy[c * TP + p], acc);
-    double a, da;
+    T a, da;
     act_hidden<KIND>(acc, a, da);
     sa1[r * TP + p] = a;
-    if (sd1) sd1[r * TP + p] = da;
-    if (dv_tile && live) dv_tile[p * dvs + r] = da;
+    if (dv_tile && live) dv_tile[p * dvs + r] = static_cast<double>(da);
   }
   __syncthreads();
   for (int r = g; r < d.h2; r += G) {
-    double acc = w.b2[r];
-    const double* wr = w.W2 + r * d.h1;
+    T acc = w.b2[r];
+    const T* wr = w.W2 + r * d.h1;
     for (int c = 0; c < d.h1; ++c) acc = fma(__ldg(wr + c), sa1[c * TP + p], acc);
-    double a, da;
+    T a, da;
     act_hidden<KIND>(acc, a, da);
     sa2[r * TP + p] = a;
-    if (sd2) sd2[r * TP + p] = da;
-    if (dv_tile && live) dv_tile[p * dvs + d.h1 + r] = da;
+    if (dv_tile && live) dv_tile[p * dvs + d.h1 + r] = static_cast<double>(da);
   }
   __syncthreads();
   for (int r = g; r < d.n; r += G) {
-    double acc = w.b3[r];
-    const double* wr = w.W3 + r * d.h2;
+    T acc = w.b3[r];
+    const T* wr = w.W3 + r * d.h2;
     for (int c = 0; c < d.h2; ++c) acc = fma(__ldg(wr + c), sa2[c * TP + p], acc);
     sz3[r * TP + p] = acc;
   }
@@ -147,7 +156,8 @@ struct ResidualArgs {
   int reverse;               // 1: adjoint -- y from the trajectory at step i0 + L - j, no R
   const double* times;
   const int* lengths;
-  const double* params;
+  const double* params;      // FP64 parameters (T = double)
+  const float* Wf;           // FP32 copy (T = float: the mixed-precision adjoint)
   const double* yi;          // [B][n] chunk start (forward)
   const double* dy;          // [B][c][n] (forward)
   const double* ytraj;       // [B][N+1][n] (adjoint)
@@ -155,9 +165,12 @@ struct ResidualArgs {
   double* dv;                // [B][c][h1+h2+n]
   unsigned long long* norm;  // [B] max |R| bits (forward)
   const int* active;         // [B] or null
+  double* act;               // [B][c][n+h1+h2+3] (y, 1, a1, 1, a2, 1) or null (adjoint)
 };
 
-template <int KIND, int TP>
+// T = double: the Newton residual (forward) or the FP64 adjoint's derivative
+// pass; T = float: the derivative pass of the mixed-precision adjoint.
+template <int KIND, int TP, typename T>
 __global__ void __launch_bounds__(kTileThreads) mlp_residual_kernel(ResidualArgs a) {
   extern __shared__ double smem[];
   const int b = blockIdx.y;
@@ -165,11 +178,13 @@ __global__ void __launch_bounds__(kTileThreads) mlp_residual_kernel(ResidualArgs
   const MlpDims d = a.d;
   const int j0 = blockIdx.x * TP;
   const int np = min(TP, a.L - j0);
-  double* sy = smem;
-  double* sa1 = sy + d.n * TP;
-  double* sa2 = sa1 + d.h1 * TP;
-  double* sz3 = sa2 + d.h2 * TP;
-  const MlpW w = mlp_split(a.params, d);
+  T* sy = reinterpret_cast<T*>(smem);
+  T* sa1 = sy + d.n * TP;
+  T* sa2 = sa1 + d.h1 * TP;
+  T* sz3 = sa2 + d.h2 * TP;
+  MlpW<T> w;
+  if constexpr (sizeof(T) == sizeof(double)) w = mlp_split(a.params, d);
+  else w = mlp_split(a.Wf, d);
   const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
   const int len = a.lengths ? min(max(a.lengths[b], 0), a.N) : a.N;
   const double* dyb = a.dy ? a.dy + static_cast<size_t>(b) * a.c * d.n : nullptr;
@@ -183,27 +198,43 @@ __global__ void __launch_bounds__(kTileThreads) mlp_residual_kernel(ResidualArgs
       else
         v = a.yi[b * d.n + c] + dyb[j * d.n + c];
     }
-    sy[e] = v;
+    sy[e] = narrow<T>(v);
   }
   __syncthreads();
   const int dvs = d.h1 + d.h2 + d.n;
   double* dv_tile = a.dv + (static_cast<size_t>(b) * a.c + j0) * dvs;
-  mlp_tile_forward<KIND, TP>(w, d, sy, sa1, sa2, sz3, nullptr, nullptr, np, dv_tile, dvs);
+  mlp_tile_forward<KIND, TP, T>(w, d, sy, sa1, sa2, sz3, np, dv_tile, dvs);
   constexpr int G = kTileThreads / TP;
   const int t = threadIdx.x, p = t % TP, g = t / TP;
+  if (a.act && p < np) {  // activations for the parameter gradient (adjoint)
+    const int aw = d.n + d.h1 + d.h2 + 3;
+    double* ar = a.act + (static_cast<size_t>(b) * a.c + j0 + p) * aw;
+    const double* yt = a.ytraj + (static_cast<size_t>(b) * (a.N + 1) +
+                                  step_of(1, a.i0, a.L, j0 + p)) * d.n;
+    for (int c = g; c < d.n; c += G) ar[c] = yt[c];
+    for (int c = g; c < d.h1; c += G) ar[d.n + 1 + c] = widen(sa1[c * TP + p]);
+    for (int c = g; c < d.h2; c += G) ar[d.n + 1 + d.h1 + 1 + c] = widen(sa2[c * TP + p]);
+    if (g == 0) {
+      ar[d.n] = 1.0;
+      ar[d.n + 1 + d.h1] = 1.0;
+      ar[d.n + 1 + d.h1 + 1 + d.h2] = 1.0;
+    }
+  }
   unsigned long long mx = 0ull;
   if (p < np) {
     const int j = j0 + p;
     const double dt = step_dt(tb, len, step_of(a.reverse, a.i0, a.L, j));
     for (int r = g; r < d.n; r += G) {
-      double h, dh;
+      T h, dh;
       act_out<KIND>(sz3[r * TP + p], h, dh);
-      dv_tile[p * dvs + d.h1 + d.h2 + r] = dh;
-      if (!a.reverse) {
-        const double prev = (j > 0) ? dyb[(j - 1) * d.n + r] : 0.0;
-        const double R = fma(-dt, h, dyb[j * d.n + r] - prev);
-        a.R[(static_cast<size_t>(b) * a.c + j) * d.n + r] = R;
-        mx = umax64(mx, abs_bits(R));
+      dv_tile[p * dvs + d.h1 + d.h2 + r] = widen(dh);
+      if constexpr (sizeof(T) == sizeof(double)) {
+        if (!a.reverse) {
+          const double prev = (j > 0) ? dyb[(j - 1) * d.n + r] : 0.0;
+          const double R = fma(-dt, h, dyb[j * d.n + r] - prev);
+          a.R[(static_cast<size_t>(b) * a.c + j) * d.n + r] = R;
+          mx = umax64(mx, abs_bits(R));
+        }
       }
     }
   }
@@ -887,16 +918,17 @@ __global__ void __launch_bounds__(32 * kChainWarps) mlp_chain_kernel(ChainArgs a
 }
 
 // ---------------------------------------------------------------------------
-// FP64 vector-Jacobian product at the stored trajectory (adjoint).  For each
+// Vector-Jacobian product at the stored trajectory (adjoint), backward pass
+// only: the derivative pass stored act'(z1), act'(z2), h'(z3) in dv.  For each
 // pair (row j = step k = i0 + L - j) with adjoint a_j:
 //   delta3 = a * h'(z3), delta2 = (W3^T delta3) * act'(z2),
 //   delta1 = (W2^T delta2) * act'(z1), J^T a = W1^T delta1.
-// Outputs (each optional):
-//   res  r_j = g_k + a_{j-1} - a_j + dt_k J^T a_j  (a_{-1} = carry): the FP64
+// The products run in T (FP64, or FP32 in the mixed-precision adjoint); the
+// residual is assembled in FP64 around them.  Outputs (each optional):
+//   res  r_j = g_k + a_{j-1} - a_j + dt_k J^T a_j  (a_{-1} = carry): the
 //        residual of the chunk's adjoint system, for refinement
-//   act  [pair][n+1+h1+1+h2+1] = (y, 1, a1, 1, a2, 1) and
-//   del  [pair][h1+h2+n] = dt_k (delta1, delta2, delta3): the factors of the
-//        parameter gradient dt_k (dh/dp)^T a_k
+//   del  [pair][h1+h2+n] = dt_k (delta1, delta2, delta3): with the activations
+//        the derivative pass stored, the factors of dt_k (dh/dp)^T a_k
 // Grid: (ceil(L / TP), B).
 // ---------------------------------------------------------------------------
 struct VjpArgs {
@@ -904,17 +936,17 @@ struct VjpArgs {
   int B, N, i0, L, c;
   const double* times;
   const int* lengths;
-  const double* params;
-  const double* ytraj;     // [B][N+1][n]
+  const double* params;    // FP64 weights (T = double)
+  const float* Wf;         // FP32 weights (T = float)
   const double* g;         // [B][N+1][n]
   const double* carry;     // [B][n]
   const double* av;        // [B][c][n] adjoint by row
+  const double* dv;        // [B][c][h1+h2+n] activation derivatives
   double* res;             // [B][c][n] or null
-  double* act;             // [B*c][n+h1+h2+3] or null
   double* del;             // [B*c][h1+h2+n] or null
 };
 
-template <int KIND, int TP>
+template <int KIND, int TP, typename T>
 __global__ void __launch_bounds__(kTileThreads) mlp_vjp_kernel(VjpArgs a) {
   extern __shared__ double smem[];
   const MlpDims d = a.d;
@@ -922,45 +954,43 @@ __global__ void __launch_bounds__(kTileThreads) mlp_vjp_kernel(VjpArgs a) {
   const int b = blockIdx.y;
   const int j0 = blockIdx.x * TP;
   const int np = min(TP, a.L - j0);
-  double* sy = smem;               // [n][TP]
-  double* sa1 = sy + n * TP;       // [h1][TP]
-  double* sa2 = sa1 + h1 * TP;     // [h2][TP]
-  double* sd1 = sa2 + h2 * TP;     // [h1][TP] act'(z1), then delta1
-  double* sd2 = sd1 + h1 * TP;     // [h2][TP] act'(z2), then delta2
-  double* sz3 = sd2 + h2 * TP;     // [n][TP]  z3, then delta3
-  const MlpW w = mlp_split(a.params, d);
+  T* sd1 = reinterpret_cast<T*>(smem);  // [h1][TP] act'(z1), then delta1
+  T* sd2 = sd1 + h1 * TP;               // [h2][TP] act'(z2), then delta2
+  T* sz3 = sd2 + h2 * TP;               // [n][TP]  h'(z3), then delta3
+  MlpW<T> w;
+  if constexpr (sizeof(T) == sizeof(double)) w = mlp_split(a.params, d);
+  else w = mlp_split(a.Wf, d);
   const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
   const int len = a.lengths ? min(max(a.lengths[b], 0), a.N) : a.N;
-  for (int e = threadIdx.x; e < n * TP; e += kTileThreads) {
-    const int c = e / TP, p = e % TP;
-    sy[e] = (p < np) ? a.ytraj[(static_cast<size_t>(b) * (a.N + 1) +
-                                step_of(1, a.i0, a.L, j0 + p)) * n + c]
-                     : 0.0;
-  }
-  __syncthreads();
-  mlp_tile_forward<KIND, TP>(w, d, sy, sa1, sa2, sz3, sd1, sd2, np, nullptr, 0);
   constexpr int G = kTileThreads / TP;
   const int t = threadIdx.x, p = t % TP, g = t / TP;
   const bool live = p < np;
   const int j = j0 + p;
   const double* avb = a.av + static_cast<size_t>(b) * a.c * n;
-  // delta3 = a * h'(z3)
-  for (int r = g; r < n; r += G) {
-    double h, dh;
-    act_out<KIND>(sz3[r * TP + p], h, dh);
-    sz3[r * TP + p] = live ? avb[j * n + r] * dh : 0.0;
+  const int dvs = h1 + h2 + n;
+  const double* dvt = a.dv + (static_cast<size_t>(b) * a.c + j0) * dvs;
+  for (int e = threadIdx.x; e < dvs * TP; e += kTileThreads) {
+    const int pp = e / dvs, q = e - pp * dvs;  // consecutive threads read one row
+    const T v = pp < np ? narrow<T>(dvt[pp * dvs + q]) : T(0);
+    if (q < h1) sd1[q * TP + pp] = v;
+    else if (q < h1 + h2) sd2[(q - h1) * TP + pp] = v;
+    else sz3[(q - h1 - h2) * TP + pp] = v;
   }
+  __syncthreads();
+  // delta3 = a * h'(z3)
+  for (int r = g; r < n; r += G)
+    sz3[r * TP + p] = live ? narrow<T>(avb[j * n + r]) * sz3[r * TP + p] : T(0);
   __syncthreads();
   // delta2 = (W3^T delta3) * act'(z2)
   for (int c = g; c < h2; c += G) {
-    double acc = 0.0;
+    T acc = T(0);
     for (int r = 0; r < n; ++r) acc = fma(__ldg(w.W3 + r * h2 + c), sz3[r * TP + p], acc);
     sd2[c * TP + p] *= acc;
   }
   __syncthreads();
   // delta1 = (W2^T delta2) * act'(z1)
   for (int c = g; c < h1; c += G) {
-    double acc = 0.0;
+    T acc = T(0);
     for (int r = 0; r < h2; ++r) acc = fma(__ldg(w.W2 + r * h1 + c), sd2[r * TP + p], acc);
     sd1[c * TP + p] *= acc;
   }
@@ -969,30 +999,22 @@ __global__ void __launch_bounds__(kTileThreads) mlp_vjp_kernel(VjpArgs a) {
   const int k = step_of(1, a.i0, a.L, j);
   const double dt = step_dt(tb, len, k);
   if (a.res) {
-    // r_j = g_k + a_{j-1} - a_j + dt (W1^T delta1)
+    // r_j = g_k + a_{j-1} - a_j + dt (W1^T delta1), assembled in FP64
     for (int c = g; c < n; c += G) {
-      double acc = 0.0;
+      T acc = T(0);
       for (int r = 0; r < h1; ++r) acc = fma(__ldg(w.W1 + r * n + c), sd1[r * TP + p], acc);
       const double prev = (j > 0) ? avb[(j - 1) * n + c] : a.carry[b * n + c];
       const double gk = a.g[(static_cast<size_t>(b) * (a.N + 1) + k) * n + c];
-      a.res[(static_cast<size_t>(b) * a.c + j) * n + c] = fma(dt, acc, gk + prev - avb[j * n + c]);
+      a.res[(static_cast<size_t>(b) * a.c + j) * n + c] =
+          fma(dt, widen(acc), gk + prev - avb[j * n + c]);
     }
   }
-  if (a.act) {
-    const int aw = n + h1 + h2 + 3, dw = h1 + h2 + n;
-    double* ar = a.act + (static_cast<size_t>(b) * a.c + j) * aw;
+  if (a.del) {
+    const int dw = h1 + h2 + n;
     double* dr = a.del + (static_cast<size_t>(b) * a.c + j) * dw;
-    for (int c = g; c < n; c += G) ar[c] = sy[c * TP + p];
-    for (int c = g; c < h1; c += G) ar[n + 1 + c] = sa1[c * TP + p];
-    for (int c = g; c < h2; c += G) ar[n + 1 + h1 + 1 + c] = sa2[c * TP + p];
-    if (g == 0) {
-      ar[n] = 1.0;
-      ar[n + 1 + h1] = 1.0;
-      ar[n + 1 + h1 + 1 + h2] = 1.0;
-    }
-    for (int c = g; c < h1; c += G) dr[c] = dt * sd1[c * TP + p];
-    for (int c = g; c < h2; c += G) dr[h1 + c] = dt * sd2[c * TP + p];
-    for (int c = g; c < n; c += G) dr[h1 + h2 + c] = dt * sz3[c * TP + p];
+    for (int c = g; c < h1; c += G) dr[c] = dt * widen(sd1[c * TP + p]);
+    for (int c = g; c < h2; c += G) dr[h1 + c] = dt * widen(sd2[c * TP + p]);
+    for (int c = g; c < n; c += G) dr[h1 + h2 + c] = dt * widen(sz3[c * TP + p]);
   }
 }
 
@@ -1227,7 +1249,7 @@ size_t residual_smem(const MlpDims& d) {
   return sizeof(double) * (2 * d.n + d.h1 + d.h2) * kResTP;
 }
 size_t vjp_smem(const MlpDims& d) {
-  return sizeof(double) * (2 * d.n + 2 * d.h1 + 2 * d.h2) * kVjpTP;
+  return sizeof(double) * (d.n + d.h1 + d.h2) * kVjpTP;
 }
 
 // pairs per Jacobian tile: about 32k bytes of U per block, at least 1
@@ -1251,24 +1273,40 @@ cudaError_t set_smem(K kernel, size_t bytes) {
                               static_cast<int>(bytes));
 }
 
-template <int KIND>
-cudaError_t launch_residual(const ResidualArgs& r, cudaStream_t s) {
+template <int KIND, typename T>
+cudaError_t launch_residual_t(const ResidualArgs& r, cudaStream_t s) {
   const size_t sm = residual_smem(r.d);
-  cudaError_t e = set_smem(mlp_residual_kernel<KIND, kResTP>, sm);
+  cudaError_t e = set_smem(mlp_residual_kernel<KIND, kResTP, T>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((r.L + kResTP - 1) / kResTP, r.B);
-  mlp_residual_kernel<KIND, kResTP><<<grid, kTileThreads, sm, s>>>(r);
+  mlp_residual_kernel<KIND, kResTP, T><<<grid, kTileThreads, sm, s>>>(r);
   return cudaGetLastError();
 }
 
-template <int KIND>
-cudaError_t launch_vjp(const VjpArgs& v, cudaStream_t s) {
+// FP64 always for the Newton residual; the adjoint's derivative pass in FP32
+// when the blocks are FP32 / BF16
+cudaError_t launch_residual(int kind, bool fp32, const ResidualArgs& r, cudaStream_t s) {
+  if (kind == kKindMlpTanh)
+    return fp32 ? launch_residual_t<kKindMlpTanh, float>(r, s)
+                : launch_residual_t<kKindMlpTanh, double>(r, s);
+  return fp32 ? launch_residual_t<kKindMlpSilu, float>(r, s)
+              : launch_residual_t<kKindMlpSilu, double>(r, s);
+}
+
+template <int KIND, typename T>
+cudaError_t launch_vjp_t(const VjpArgs& v, cudaStream_t s) {
   const size_t sm = vjp_smem(v.d);
-  cudaError_t e = set_smem(mlp_vjp_kernel<KIND, kVjpTP>, sm);
+  cudaError_t e = set_smem(mlp_vjp_kernel<KIND, kVjpTP, T>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((v.L + kVjpTP - 1) / kVjpTP, v.B);
-  mlp_vjp_kernel<KIND, kVjpTP><<<grid, kTileThreads, sm, s>>>(v);
+  mlp_vjp_kernel<KIND, kVjpTP, T><<<grid, kTileThreads, sm, s>>>(v);
   return cudaGetLastError();
+}
+
+cudaError_t launch_vjp(int kind, bool fp32, const VjpArgs& v, cudaStream_t s) {
+  if (kind == kKindMlpTanh)
+    return fp32 ? launch_vjp_t<kKindMlpTanh, float>(v, s) : launch_vjp_t<kKindMlpTanh, double>(v, s);
+  return fp32 ? launch_vjp_t<kKindMlpSilu, float>(v, s) : launch_vjp_t<kKindMlpSilu, double>(v, s);
 }
 
 template <typename T>
@@ -1379,8 +1417,7 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
       r.d = d; r.B = B; r.N = N; r.i0 = i0; r.L = L; r.c = c; r.reverse = 0;
       r.times = a.times; r.lengths = a.lengths; r.params = a.params; r.yi = w.yi; r.dy = w.dy;
       r.R = w.R; r.dv = w.dv; r.norm = w.norm; r.active = w.active;
-      TVI_TRY(kind == kKindMlpTanh ? launch_residual<kKindMlpTanh>(r, s)
-                                   : launch_residual<kKindMlpSilu>(r, s));
+      TVI_TRY(launch_residual(kind, false, r, s));
       TVI_TRY(cudaMemsetAsync(w.remaining, 0, sizeof(int), s));
       CheckArgs ck{B, it, a.max_iter, a.tol_abs, a.tol_rel, w.norm, w.norm0, w.active, w.status,
                    w.iters, w.remaining};
@@ -1422,6 +1459,9 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
   TVI_TRY(cudaMemsetAsync(w.carry, 0, sizeof(double) * B * n, s));  // a_{N+1} = 0
   TVI_TRY(cudaMemsetAsync(w.acc, 0, sizeof(double) * d.P, s));
   const int refine = precision == kPrecFp64 ? 0 : a.refine;
+  // mixed precision: every MLP pass of the adjoint in FP32 (the refinement
+  // residual is still assembled in FP64); FP64 blocks: FP64 throughout
+  const bool mixed = precision != kPrecFp64;
   const int nch = (N + c - 1) / c;
   for (int ci = nch - 1; ci >= 0; --ci) {
     const int i0 = ci * c;
@@ -1430,8 +1470,8 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
     ResidualArgs r{};
     r.d = d; r.B = B; r.N = N; r.i0 = i0; r.L = L; r.c = c; r.reverse = 1;
     r.times = a.times; r.lengths = a.lengths; r.params = a.params; r.ytraj = a.y; r.dv = w.dv;
-    TVI_TRY(kind == kKindMlpTanh ? launch_residual<kKindMlpTanh>(r, s)
-                                 : launch_residual<kKindMlpSilu>(r, s));
+    r.act = w.act; r.Wf = w.Wf;
+    TVI_TRY(launch_residual(kind, mixed, r, s));
     BlocksArgs bk{};
     bk.d = d; bk.B = B; bk.N = N; bk.i0 = i0; bk.L = L; bk.c = c; bk.reverse = 1;
     bk.times = a.times; bk.lengths = a.lengths; bk.Wf = w.Wf; bk.Wd = a.params; bk.dv = w.dv;
@@ -1444,13 +1484,13 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
     TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s));
     VjpArgs v{};
     v.d = d; v.B = B; v.N = N; v.i0 = i0; v.L = L; v.c = c; v.times = a.times;
-    v.lengths = a.lengths; v.params = a.params; v.ytraj = a.y; v.g = a.grad_out;
+    v.lengths = a.lengths; v.params = a.params; v.Wf = w.Wf; v.g = a.grad_out;
     v.carry = w.carry; v.av = w.dy;
+    v.dv = w.dv;  // backward passes only: the derivative pass above stored act' and h'
     for (int it = 0; it < refine; ++it) {
       v.res = w.R;
-      v.act = nullptr;
       v.del = nullptr;
-      TVI_TRY(kind == kKindMlpTanh ? launch_vjp<kKindMlpTanh>(v, s) : launch_vjp<kKindMlpSilu>(v, s));
+      TVI_TRY(launch_vjp(kind, mixed, v, s));
       ChainArgs cr = ch;
       cr.rhs_traj = nullptr;
       cr.rhs_buf = w.R;
@@ -1460,9 +1500,8 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
     }
     // parameter gradient factors at the final a, then the tiled sums
     v.res = nullptr;
-    v.act = w.act;
-    v.del = w.del;
-    TVI_TRY(kind == kKindMlpTanh ? launch_vjp<kKindMlpTanh>(v, s) : launch_vjp<kKindMlpSilu>(v, s));
+    v.del = w.del;  // the activations were stored by the derivative pass
+    TVI_TRY(launch_vjp(kind, mixed, v, s));
     // pairs split into up to kMaxParamSplits ranges of >= 1024 so the tiles fill the GPU
     const int npairs = B * L;
     int nsplit = (npairs + 1023) / 1024;
