@@ -40,11 +40,15 @@ METRIC = "series*steps/s fwd+adjoint vs chunk=1 sequential on GB300, same Newton
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 rate (recipe table); no measured FP64 peak given
 
+# refine: FP64-residual refinement sweeps of the mixed-precision adjoint (van der Pol:
+# one sweep leaves 1e-8 relative error against the FP64 oracle, tested at full size)
 WORKLOADS = {
-    "vdp": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 128, "N": 10000},
-    "vdp_pred": {"chunk": 100, "precision": "fp32", "tol": 1e-8, "B": 128, "N": 10000},
-    "node16": {"chunk": 200, "precision": "bf16", "tol": 1e-8, "B": 64, "N": 2000},
-    "node32": {"chunk": 1000, "precision": "bf16", "tol": 1e-8, "B": 512, "N": 20000},
+    "vdp": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 128, "N": 10000, "refine": 1},
+    "vdp_pred": {"chunk": 100, "precision": "fp32", "tol": 1e-8, "B": 128, "N": 10000,
+                 "refine": 1},
+    "node16": {"chunk": 200, "precision": "bf16", "tol": 1e-8, "B": 64, "N": 2000, "refine": 2},
+    "node32": {"chunk": 1000, "precision": "bf16", "tol": 1e-8, "B": 512, "N": 20000,
+               "refine": 2},
 }
 
 
@@ -63,6 +67,8 @@ def parse():
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "bf16"])
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--rpt", type=int, default=0, help="steps per thread (0 = library default)")
+    ap.add_argument("--refine", type=int, default=None,
+                    help="adjoint refinement sweeps (mixed precision)")
     ap.add_argument("--B", type=int, default=None)
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--baseline-steps", type=int, default=5)
@@ -102,6 +108,20 @@ def make_workload(args, rank=0):
     return w, g
 
 
+def job_throughput(units_local, steps, local_ms, world, dist=None, device="cpu"):
+    """Whole-job series*steps/s over N ranks: the real steps every rank integrated
+    (summed: ranks hold different per-series lengths) over the slowest rank's time
+    (max over ranks).  Returns (value, max_ms)."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local) * steps], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    max_ms = float(t.item())
+    return float(u.item()) / (max_ms / 1e3), max_ms
+
+
 def real_steps(w):
     B, Np1 = w["times"].shape
     return int(np.sum(w["lengths"])) if w["lengths"] is not None else B * (Np1 - 1)
@@ -116,7 +136,8 @@ def workload_config(args):
                       "U[2000,N] padded, uniform steps on [0,10]"}[args.workload]
     return {"workload": f"{desc}; {args.B} series x {args.N} steps, Newton tol {args.tol:g}",
             "B": args.B, "N": args.N, "chunk": args.chunk,
-            "blocks": args.precision, "residual": "fp64", "tol_abs": args.tol}
+            "blocks": args.precision, "residual": "fp64", "tol_abs": args.tol,
+            "adjoint_refine": args.refine if args.precision != "fp64" else 0}
 
 
 # ---------------------------------------------------------------------------
@@ -386,11 +407,12 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     opts = tvi.Options(chunk=args.chunk, tol_abs=args.tol, precision=args.precision,
-                       rows_per_thread=args.rpt, sync_status=False, **pred_opts)
+                       rows_per_thread=args.rpt, sync_status=False, adjoint_refine=args.refine,
+                       **pred_opts)
     res = timed_steps(opts, args.steps, args.warmup)
     if pred_info is not None:
         o0 = tvi.Options(chunk=args.chunk, tol_abs=args.tol, precision=args.precision,
-                         rows_per_thread=args.rpt, sync_status=False)
+                         rows_per_thread=args.rpt, sync_status=False, adjoint_refine=args.refine)
         r0 = timed_steps(o0, args.steps, 1)
         s1, s0 = res["stats"], r0["stats"]
         v0 = units_per_step * args.steps / (r0["total_ms"] / 1e3)
@@ -400,11 +422,8 @@ def run_ours(args):
             "guesses_used": int(s1[:, 4].sum()), "fallbacks": int(s1[:, 5].sum()),
             "fwd_ms": float(np.mean(res["fwd_ms"])), "fwd_ms_zero_guess": float(np.mean(r0["fwd_ms"])),
             "value_zero_guess": v0})
-    total_ms = torch.tensor([res["total_ms"]], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(total_ms, op=dist.ReduceOp.MAX)
-    total_ms = float(total_ms.item())
-    value = units_per_step * world * args.steps / (total_ms / 1e3)
+    value, total_ms = job_throughput(units_per_step, args.steps, res["total_ms"], world,
+                                     dist if world > 1 else None, dev)
 
     # end-to-end through the public API: pinned host inputs in, gradients out
     host_in = [("y0", w["y0"], torch.float64), ("times", w["times"], torch.float64),

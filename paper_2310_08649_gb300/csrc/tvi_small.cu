@@ -112,8 +112,10 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
     const bool wact = warp < nwa;
     const bool can_halve = a.retry_halving && c_cur > 1;
     // ---- per-thread rows of this chunk attempt ----
-    double dt[RPT], dy[RPT][NS];
-    T dtT[RPT], yiT[NS], dyT[RPT][NS];  // block-precision shadows (mixed mode)
+    // the iterate is held as y_j = y_i + dy_j itself (FP64), so the residual needs
+    // no y_i + dy_j adds: 9 FP64 operations per step and pass (van der Pol)
+    double dt[RPT], yv[RPT][NS];
+    T dtT[RPT], yiT[NS], yT[RPT][NS];  // block-precision shadows (mixed mode)
     bool act[RPT];
 #pragma unroll
     for (int s = 0; s < NS; ++s) yiT[s] = narrow<T>(yi[s]);
@@ -126,8 +128,8 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
       dtT[r] = narrow<T>(dt[r]);
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        dy[r][s] = 0.0;  // Sec. 2.3 guess: dy = 0
-        dyT[r][s] = T(0);
+        yv[r][s] = yi[s];  // Sec. 2.3 guess: dy = 0
+        yT[r][s] = yiT[s];
       }
     }
 
@@ -199,8 +201,13 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
 #pragma unroll
           for (int s = 0; s < NS; ++s)
             dyp[r][s] = act[r] ? static_cast<double>(outv[(tid * RPT + r) * NS + s]) : 0.0;
+        double dz[RPT][NS];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+          for (int s = 0; s < NS; ++s) dz[r][s] = 0.0;
         const unsigned long long n_zero =
-            residual_norm_block<Model, RPT>(mdl, yi, dy, dt, act, s_wlast, s_red, lane, warp);
+            residual_norm_block<Model, RPT>(mdl, yi, dz, dt, act, s_wlast, s_red, lane, warp);
         const unsigned long long n_pred =
             residual_norm_block<Model, RPT>(mdl, yi, dyp, dt, act, s_wlast, s_red, lane, warp);
         if (n_pred < n_zero) {  // both finite bit patterns compare as values
@@ -208,8 +215,8 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
           for (int r = 0; r < RPT; ++r)
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-              dy[r][s] = dyp[r][s];
-              dyT[r][s] = narrow<T>(dyp[r][s]);
+              yv[r][s] = yi[s] + dyp[r][s];
+              yT[r][s] = narrow<T>(yv[r][s]);
             }
           ++pred_used;
           pred_streak = 0;
@@ -232,15 +239,15 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
       // dy_{j-1} of the first own row: last row of the previous thread
       double prev[NS];
 #pragma unroll
-      for (int s = 0; s < NS; ++s) prev[s] = __shfl_up_sync(kFull, dy[RPT - 1][s], 1);
+      for (int s = 0; s < NS; ++s) prev[s] = __shfl_up_sync(kFull, yv[RPT - 1][s], 1);
       if (lane == 31) {
 #pragma unroll
-        for (int s = 0; s < NS; ++s) s_wlast[warp][s] = dy[RPT - 1][s];
+        for (int s = 0; s < NS; ++s) s_wlast[warp][s] = yv[RPT - 1][s];
       }
       sync_first(32 * nwa);
-      if (lane == 0) {
+      if (lane == 0) {  // the row before row 0 is the chunk start y_i
 #pragma unroll
-        for (int s = 0; s < NS; ++s) prev[s] = (warp > 0) ? s_wlast[warp - 1][s] : 0.0;
+        for (int s = 0; s < NS; ++s) prev[s] = (warp > 0) ? s_wlast[warp - 1][s] : yi[s];
       }
       // ---- residual, FP64 ----
       double R[RPT][NS];
@@ -250,12 +257,12 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
         for (int r = 0; r < RPT; ++r) {
           double y[NS], h[NS];
 #pragma unroll
-          for (int s = 0; s < NS; ++s) y[s] = yi[s] + dy[r][s];
+          for (int s = 0; s < NS; ++s) y[s] = yv[r][s];
           mdl.rhs(y, h);
 #pragma unroll
           for (int s = 0; s < NS; ++s) {
-            const double pv = (r == 0) ? prev[s] : dy[r - 1][s];
-            R[r][s] = act[r] ? fma(-dt[r], h[s], dy[r][s] - pv) : 0.0;
+            const double pv = (r == 0) ? prev[s] : yv[r - 1][s];
+            R[r][s] = act[r] ? fma(-dt[r], h[s], yv[r][s] - pv) : 0.0;
             mx = umax64(mx, abs_bits(R[r][s]));
           }
         }
@@ -281,8 +288,8 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
             T yt[NS], A[NS][NS];
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-              if constexpr (kMixed) yt[s] = yiT[s] + dyT[r][s];
-              else yt[s] = yi[s] + dy[r][s];
+              if constexpr (kMixed) yt[s] = yT[r][s];
+              else yt[s] = yv[r][s];
             }
             mdl.step_matrix(yt, dtT[r], A);
             block_inverse<NS, T>(A, f[r].M);
@@ -309,8 +316,8 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
 #pragma unroll
           for (int s = 0; s < NS; ++s)
             if (act[r]) {
-              dy[r][s] -= widen<T>(d[r][s]);
-              if constexpr (kMixed) dyT[r][s] -= d[r][s];
+              yv[r][s] -= widen<T>(d[r][s]);
+              if constexpr (kMixed) yT[r][s] -= d[r][s];
             }
       }
       ++it;
@@ -344,11 +351,11 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
       if (act[r]) {
         double* out = yb + static_cast<size_t>(i + 1 + j) * NS;
 #pragma unroll
-        for (int s = 0; s < NS; ++s) out[s] = yi[s] + dy[r][s];
+        for (int s = 0; s < NS; ++s) out[s] = yv[r][s];
       }
       if (j == L - 1) {
 #pragma unroll
-        for (int s = 0; s < NS; ++s) s_carry[s] = yi[s] + dy[r][s];
+        for (int s = 0; s < NS; ++s) s_carry[s] = yv[r][s];
       }
     }
     __syncthreads();

@@ -151,17 +151,19 @@ def test_vdp_forward_parity_full_size(tvi, oracle_lib, precision, chunk, tol):
     assert res.max() <= 4 * tol
 
 
+@pytest.mark.parametrize("refine", [2, 1])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("chunk", [1000, 37, 1])
-def test_vdp_adjoint_parity_full_size(tvi, oracle_lib, precision, chunk):
+def test_vdp_adjoint_parity_full_size(tvi, oracle_lib, precision, chunk, refine):
     """Both adjoints run on the oracle's trajectory, so they solve the same
-    linear system; the gradient is compared directly."""
+    linear system; the gradient is compared directly.  One refinement sweep is
+    the benchmark's setting."""
     w, ref, _ = vdp_reference(oracle_lib, 1e-10)
     m = OModel.from_spec(w["spec"])
     g = workloads.random_grad_out(78, 128, 10000, 2)
     dmu, dy0 = oracle_lib.adjoint(m, w["times"], w["params"], ref, g)
     tm = tvi.Model.from_spec(w["spec"])
-    o = tvi.Options(chunk=chunk, precision=precision, adjoint_refine=2)
+    o = tvi.Options(chunk=chunk, precision=precision, adjoint_refine=refine)
     dmug, dy0g = tvi.adjoint(tm, o, dev(w["times"]), dev(w["params"]), dev(ref), dev(g))
     dmug, dy0g = dmug.cpu().numpy(), dy0g.cpu().numpy()
     e_mu = np.abs(dmug - dmu)[:, 0] / np.maximum(np.abs(dmu)[:, 0], 1e-300)
