@@ -284,8 +284,8 @@ def roofline(args, w, stats, fwd_ms, adj_ms, refine):
     nchk = stats[:, 1].astype(np.float64)
     spc = N / np.maximum(nchk, 1)  # steps per solved chunk
     if args.workload.startswith("vdp"):
-        # residual y = y_i + dy (2), h (3), R (4) = 9; update dy -= d: 2
-        fwd_ops = float(np.sum(((upd + nchk) * 9.0 + upd * 2.0) * spc))
+        # residual on the stored iterate y: h (3) + R (4) = 7; update y -= d: 2
+        fwd_ops = float(np.sum(((upd + nchk) * 7.0 + upd * 2.0) * spc))
         # adjoint per step: per refinement sweep 14, parameter VJP 4
         adj_ops = float(B * N * (refine * 14.0 + 4.0))
         names = ("forward_small_kernel<vdp,fp32>", "adjoint_small_kernel<vdp,fp32>")
