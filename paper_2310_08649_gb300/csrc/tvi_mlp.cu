@@ -491,7 +491,7 @@ constexpr int kTcWaitLimit = 1 << 24; // mbarrier polls before giving up
 constexpr size_t kTcMinSmem = 58 * 1024;  // <= 3 blocks per SM: 3 x 128 TMEM columns fit
 
 struct TcLayout {
-  uint32_t w2, w3, ug, w1t, dv, total;  // byte offsets in dynamic shared memory
+  uint32_t w2, w3, ug, w1t, dv, dvraw, total;  // byte offsets in dynamic shared memory
 };
 
 // The A operands of the two GEMMs share one region (U is dead once GEMM 1 has
@@ -505,7 +505,8 @@ __host__ __device__ inline TcLayout tc_layout(const MlpDims& d) {
   L.ug = L.w3 + 2u * d.n * d.h2;              // [128][h1] then [128][h2] BF16, operand layout
   L.w1t = L.ug + 2u * kTcRows * hmax;         // [n][h1] FP32
   L.dv = L.w1t + 4u * d.n * d.h1;             // [TP][h1+h2+n] FP32
-  L.total = L.dv + 4u * tp * (d.h1 + d.h2 + d.n);
+  L.dvraw = L.dv + 4u * tp * (d.h1 + d.h2 + d.n);  // 2 x [TP][h1+h2+n] FP64, bulk-copied
+  L.total = L.dvraw + 2u * 8u * tp * (d.h1 + d.h2 + d.n);
   return L;
 }
 
@@ -544,6 +545,7 @@ template <int NN>
 __global__ void __launch_bounds__(kTcThreads) mlp_blocks_tc_kernel(BlocksArgs a, int* err) {
   extern __shared__ __align__(128) unsigned char tsm[];
   __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_dvbar[2];
   __shared__ uint32_t s_tmem;
   __shared__ float s_dt[kTcRows / NN];
   __shared__ int s_stop;
@@ -579,6 +581,8 @@ __global__ void __launch_bounds__(kTcThreads) mlp_blocks_tc_kernel(BlocksArgs a,
   }
   if (tid == 0) {
     tc::mbar_init(&s_bar, 1);
+    tc::mbar_init(&s_dvbar[0], 1);
+    tc::mbar_init(&s_dvbar[1], 1);
     s_stop = 0;
   }
   if (warp == 0) tc::tmem_alloc(&s_tmem, kTcCols);
@@ -597,17 +601,53 @@ __global__ void __launch_bounds__(kTcThreads) mlp_blocks_tc_kernel(BlocksArgs a,
   const int tiles_per = (a.L + TP - 1) / TP;
   const int total = a.B * tiles_per;
 
-  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+  // The activation derivatives of a tile (np x dvs FP64, contiguous) arrive by a
+  // bulk copy issued while the previous tile is processed (two buffers, one
+  // mbarrier each); inactive series' tiles are skipped.
+  double* dvraw = reinterpret_cast<double*>(tsm + Lo.dvraw);
+  auto next_tile = [&](int t) {
+    while (t < total && a.active && !a.active[t / tiles_per]) t += gridDim.x;
+    return t;
+  };
+  auto issue_dv = [&](int t, int bf) {  // thread 0
+    const int bb = t / tiles_per, jj = (t - bb * tiles_per) * TP;
+    const int npp = min(TP, a.L - jj);
+    const uint32_t bytes = static_cast<uint32_t>(8 * npp * dvs);
+    tc::fence_smem_to_async();  // earlier reads of this buffer precede the refill
+    tc::mbar_expect_tx(&s_dvbar[bf], bytes);
+    tc::bulk_g2s(dvraw + bf * TP * dvs, a.dv + (static_cast<size_t>(bb) * a.c + jj) * dvs, bytes,
+                 &s_dvbar[bf]);
+  };
+  int buf = 0, nxt = 0;
+  uint32_t dvphase = 0;  // bit bf: parity of buffer bf's next completion
+  uint32_t outst = 0;    // bit bf: a copy into buffer bf is in flight
+  const int first = next_tile(blockIdx.x);
+  if (first < total) {
+    if (tid == 0) issue_dv(first, 0);
+    outst |= 1u;
+  }
+  for (int tile = first; tile < total; tile = nxt, buf ^= 1) {
     const int b = tile / tiles_per;
     const int j0 = (tile - b * tiles_per) * TP;
-    if (a.active && !a.active[b]) continue;
     const int np = min(TP, a.L - j0);
-    const double* dvt = a.dv + (static_cast<size_t>(b) * a.c + j0) * dvs;
+    nxt = next_tile(tile + gridDim.x);
+    if (nxt < total) {
+      if (tid == 0) issue_dv(nxt, buf ^ 1);
+      outst |= 1u << (buf ^ 1);
+    }
     const int len = a.lengths ? min(max(a.lengths[b], 0), a.N) : a.N;
     const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
     if (tid < TP)
       s_dt[tid] = tid < np ? narrow<float>(step_dt(tb, len, step_of(a.reverse, a.i0, a.L, j0 + tid)))
                            : 0.0f;
+    if (tc::mbar_wait_bounded(&s_dvbar[buf], (dvphase >> buf) & 1u, kTcWaitLimit))
+      outst &= ~(1u << buf);
+    else
+      s_stop = 1;
+    dvphase ^= 1u << buf;
+    __syncthreads();
+    if (s_stop) break;
+    const double* dvt = dvraw + buf * TP * dvs;
     for (int e = tid; e < TP * dvs; e += kTcThreads)
       sdv[e] = e < np * dvs ? narrow<float>(dvt[e]) : 0.0f;
     __syncthreads();
@@ -800,6 +840,12 @@ __global__ void __launch_bounds__(kTcThreads) mlp_blocks_tc_kernel(BlocksArgs a,
   if (s_stop) {
     if (tid == 0) atomicExch(err, 1);
     tc::mbar_wait_bounded(&s_bar, phase ^ 1u, kTcWaitLimit);  // the MMAs that timed out
+    for (int bf = 0; bf < 2; ++bf)  // derivative copies still in flight
+      if (outst & (1u << bf)) {
+        const uint32_t par = (dvphase >> bf) & 1u;
+        // the buffer being waited on when the timeout hit has already flipped its parity
+        tc::mbar_wait_bounded(&s_dvbar[bf], bf == buf ? par ^ 1u : par, kTcWaitLimit);
+      }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -814,9 +860,8 @@ __global__ void __launch_bounds__(kTcThreads) mlp_blocks_tc_kernel(BlocksArgs a,
 // The chain is latency bound (one dependent mat-vec per step), so everything
 // that does not depend on d_{j-1} -- the block M_j (stored transposed), rhs_j
 // and the accumulator row x_j -- is staged D steps ahead into a per-warp ring
-// of shared-memory slots with cp.async, and d_{j-1} + rhs_j is broadcast
-// through shared memory.  Every staged address is 16-byte aligned (workspace
-// buffers by construction, caller arrays checked by the C ABI).
+// of shared-memory slots by bulk copies, and d_{j-1} + rhs_j is broadcast
+// through shared memory.
 // ---------------------------------------------------------------------------
 struct ChainArgs {
   int B, n, L, c, N, i0, reverse;
@@ -827,67 +872,71 @@ struct ChainArgs {
   const int* active;       // [B] or null
   double* x;               // [B][c][n]
   int mode;                // 0: x -= d   1: x = d   2: x += d
+  int* err;                // set when a bounded wait for staged data gives up
 };
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int PENDING>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
-}
-
 constexpr int kChainWarps = 4;
+constexpr int kChainWaitLimit = 1 << 22;
 
 template <typename T>
 size_t chain_slot_bytes(int n) {
   return sizeof(T) * n * n + 2 * sizeof(double) * n;
 }
 
+// Lane 0 of each warp stages step j's block, rhs row and x row into ring slot
+// j % D with bulk copies (the TMA unit) that complete on the slot's mbarrier;
+// the warp waits on the barrier's phase (j / D) & 1 for step j.  Every source is
+// 16-byte aligned and every size a multiple of 16 (n even; workspace buffers by
+// construction, caller arrays checked by the C ABI).
 template <typename T, int D>
 __global__ void __launch_bounds__(32 * kChainWarps) mlp_chain_kernel(ChainArgs a) {
   extern __shared__ __align__(16) unsigned char chain_smem[];
   __shared__ T s_u[kChainWarps][32];
+  __shared__ __align__(8) uint64_t s_bar[kChainWarps][D];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int b = blockIdx.x * kChainWarps + wib;
   // warp-uniform exit: the kernel synchronises only within a warp
   if (b >= a.B || (a.active && !a.active[b])) return;
   const int n = a.n;
   const bool own = lane < n;
-  const size_t mbytes = sizeof(T) * n * n;
-  const size_t slot_bytes = mbytes + 2 * sizeof(double) * n;
+  const uint32_t mbytes = static_cast<uint32_t>(sizeof(T) * n * n);
+  const uint32_t vbytes = static_cast<uint32_t>(sizeof(double) * n);
+  const size_t slot_bytes = mbytes + 2 * vbytes;
   unsigned char* ring = chain_smem + static_cast<size_t>(wib) * D * slot_bytes;
+  uint64_t* bars = s_bar[wib];
   const unsigned char* Mb = static_cast<const unsigned char*>(a.M) +
                             static_cast<size_t>(b) * a.c * mbytes;
   double* xb = a.x + static_cast<size_t>(b) * a.c * n;
   T* su = s_u[wib];
-  auto issue = [&](int j) {  // stage step j into slot j % D (empty group past the end)
-    if (j < a.L) {
-      unsigned char* slot = ring + static_cast<size_t>(j % D) * slot_bytes;
-      const unsigned char* gM = Mb + static_cast<size_t>(j) * mbytes;
-      for (int k = lane; k < static_cast<int>(mbytes / 16); k += 32) cp_async16(slot + 16 * k, gM + 16 * k);
-      const double* gr =
-          a.rhs_buf ? a.rhs_buf + (static_cast<size_t>(b) * a.c + j) * n
-                    : a.rhs_traj + (static_cast<size_t>(b) * (a.N + 1) +
-                                    step_of(a.reverse, a.i0, a.L, j)) * n;
-      for (int k = lane; k < n / 2; k += 32) cp_async16(slot + mbytes + 16 * k, gr + 2 * k);
-      if (a.mode != 1)
-        for (int k = lane; k < n / 2; k += 32)
-          cp_async16(slot + mbytes + 8 * n + 16 * k, xb + static_cast<size_t>(j) * n + 2 * k);
-    }
-    cp_async_commit();
+  if (lane == 0)
+    for (int k = 0; k < D; ++k) tc::mbar_init(&bars[k], 1);
+  __syncwarp();
+  auto issue = [&](int j) {  // lane 0: stage step j into slot j % D
+    if (lane != 0 || j >= a.L) return;
+    unsigned char* slot = ring + static_cast<size_t>(j % D) * slot_bytes;
+    const double* gr =
+        a.rhs_buf ? a.rhs_buf + (static_cast<size_t>(b) * a.c + j) * n
+                  : a.rhs_traj + (static_cast<size_t>(b) * (a.N + 1) +
+                                  step_of(a.reverse, a.i0, a.L, j)) * n;
+    tc::fence_smem_to_async();  // the warp's reads of this slot precede the refill
+    tc::mbar_expect_tx(&bars[j % D], mbytes + vbytes + (a.mode != 1 ? vbytes : 0u));
+    tc::bulk_g2s(slot, Mb + static_cast<size_t>(j) * mbytes, mbytes, &bars[j % D]);
+    tc::bulk_g2s(slot + mbytes, gr, vbytes, &bars[j % D]);
+    if (a.mode != 1)
+      tc::bulk_g2s(slot + mbytes + vbytes, xb + static_cast<size_t>(j) * n, vbytes, &bars[j % D]);
   };
 #pragma unroll 1
   for (int j = 0; j < D; ++j) issue(j);
   T dprev = (a.x_init && own) ? narrow<T>(a.x_init[b * n + lane]) : T(0);
+  int done = 0;  // steps whose staged data has been consumed
 #pragma unroll 1
   for (int j = 0; j < a.L; ++j) {
-    cp_async_wait<D - 1>();
-    __syncwarp();
+    const bool ok = __all_sync(kFull, tc::mbar_wait_bounded(&bars[j % D], (j / D) & 1,
+                                                           kChainWaitLimit));
+    if (!ok) {
+      if (lane == 0) atomicExch(a.err, 1);
+      break;
+    }
     const unsigned char* slot = ring + static_cast<size_t>(j % D) * slot_bytes;
     const T* Mt = reinterpret_cast<const T*>(slot);  // Mt[q * n + r] = M_j[r][q]
     const double* rr = reinterpret_cast<const double*>(slot + mbytes);
@@ -905,6 +954,7 @@ __global__ void __launch_bounds__(32 * kChainWarps) mlp_chain_kernel(ChainArgs a
       }
     }
     __syncwarp();  // slot j % D and su are free again
+    done = j + 1;
     issue(j + D);
     const T acc = (acc0 + acc1) + (acc2 + acc3);
     dprev = own ? acc : T(0);
@@ -914,7 +964,10 @@ __global__ void __launch_bounds__(32 * kChainWarps) mlp_chain_kernel(ChainArgs a
           (a.mode == 0) ? x_cur - dd : (a.mode == 1 ? dd : x_cur + dd);
     }
   }
-  cp_async_wait<0>();
+  // after a timeout: give the copies still in flight (steps done .. done + D - 1)
+  // a second bounded wait before the block's shared memory goes away
+  for (int j = done; j < a.L && j < done + D; ++j)
+    tc::mbar_wait_bounded(&bars[j % D], (j / D) & 1, kChainWaitLimit);
 }
 
 // ---------------------------------------------------------------------------
@@ -1433,7 +1486,7 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
       bk.active = w.active; bk.M = w.M;
       ChainArgs ch{};
       ch.B = B; ch.n = n; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 0; ch.M = w.M;
-      ch.rhs_buf = w.R; ch.active = w.active; ch.x = w.dy; ch.mode = 0;
+      ch.rhs_buf = w.R; ch.active = w.active; ch.x = w.dy; ch.mode = 0; ch.err = w.tcerr;
       TVI_TRY(launch_blocks_any(bk, precision, w.tcerr, s));
       TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s));
     }
@@ -1479,7 +1532,7 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
     // a_j = A^-T (a_{j-1} + g_k), a_{-1} = carry
     ChainArgs ch{};
     ch.B = B; ch.n = n; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 1; ch.M = w.M;
-    ch.rhs_traj = a.grad_out; ch.x_init = w.carry; ch.x = w.dy; ch.mode = 1;
+    ch.rhs_traj = a.grad_out; ch.x_init = w.carry; ch.x = w.dy; ch.mode = 1; ch.err = w.tcerr;
     TVI_TRY(launch_blocks_any(bk, precision, w.tcerr, s));
     TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s));
     VjpArgs v{};

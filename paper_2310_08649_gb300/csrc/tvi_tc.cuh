@@ -1,7 +1,8 @@
 // tvi_tc.cuh -- fifth-generation tensor-core (tcgen05) building blocks for
 // sm_103a, in inline PTX: tensor-memory (TMEM) allocation, shared-memory operand
 // descriptors in the no-swizzle K-major layout, the BF16 x BF16 -> FP32 MMA
-// with its accumulator in TMEM, completion through an mbarrier, and TMEM loads.
+// with its accumulator in TMEM, completion through an mbarrier, TMEM loads, and
+// 1-D bulk copies (global -> shared through the TMA unit) completing on an mbarrier.
 //
 // Operand layout (K-major, no swizzle).  A tile of R rows by K columns of BF16
 // is stored as 8-row x 16-byte "core matrices" (128 contiguous bytes, row i of
@@ -86,6 +87,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   for (int i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// ---- bulk copies (the TMA unit, 1-D): global -> shared, completion on an mbarrier ----
+// `bytes` expected on `bar` for the current phase, plus this thread's arrival
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
 // ---- MMA: D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread ----
