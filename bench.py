@@ -327,6 +327,8 @@ def run_ours(args):
     from paper_2310_08649_gb300 import build as lib_build
     lib_build.build()
     import paper_2310_08649_gb300 as tvi
+    from paper_2310_08649_gb300 import _lib
+    lib = _lib.load()
 
     dev = torch.device("cuda", local)
     # weak scaling: every rank integrates its own batch of the same shape
@@ -374,9 +376,11 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        launches0 = lib.tvi_kernel_launches()
         for k in range(K):
             flush.fill_(k & 0xff)  # L2 flush between timed steps (outside the events)
             step(ev[k])
+        launches = lib.tvi_kernel_launches() - launches0
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -386,7 +390,7 @@ def run_ours(args):
         adj = [b.elapsed_time(c) for _, b, c in ev]
         assert int(st.max().item()) == 0, "a series failed to converge"
         return {"fwd_ms": fwd, "adj_ms": adj, "total_ms": float(np.sum(fwd) + np.sum(adj)),
-                "stats": stats.cpu().numpy(), "t0": t0, "t1": t1}
+                "stats": stats.cpu().numpy(), "t0": t0, "t1": t1, "launches": int(launches)}
 
     pred_info, pred_opts = None, {}
     if args.workload == "vdp_pred":
@@ -489,7 +493,6 @@ def run_ours(args):
 
     if rank == 0:
         upd, nchk = stats_np[:, 0].astype(np.float64), stats_np[:, 1].astype(np.float64)
-        launches = 2 * args.steps if args.workload.startswith("vdp") else None
         line = {"metric": METRIC, "value": value, "unit": "series*steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -509,19 +512,11 @@ def run_ours(args):
                 "chunk1_fp64": chunk1, "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "series*steps/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "clocks": clk}
+                "gpu_launches": res["launches"],
+                "gpu_launches_source": "tvi_kernel_launches() delta over the timed steps",
+                "clocks": clk}
         if pred_info is not None:
             line["predictor"] = pred_info
-        if launches is None:
-            # MLP path, per step: forward 3 + per chunk (init, store) + per Newton pass
-            # (residual, check) + per update (blocks, chain); adjoint 2 + per chunk
-            # (derivatives, blocks, chain, 2 per refinement sweep, VJP, gradient, carry)
-            nch = float(np.max(nchk))
-            passes = float(np.mean(upd + nchk))  # batch passes >= mean per series
-            fwd = 3 + 2 * nch + 2 * passes + 2 * float(np.mean(upd))
-            adj = 2 + nch * (6 + 2 * refine)
-            line["gpu_launches"] = int(round(args.steps * (fwd + adj)))
-            line["gpu_launches_note"] = "MLP path: lower estimate from the Newton statistics"
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

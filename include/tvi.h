@@ -235,6 +235,11 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
 /* Text of the last error on the calling host thread ("" if none). */
 const char* tvi_last_error(void);
 
+/* Kernels this library has enqueued since it was loaded, over every host thread
+ * (a benchmark reads it before and after a region to count that region's
+ * launches).  The paper has no counterpart. */
+unsigned long long tvi_kernel_launches(void);
+
 /* Library build identification, e.g. "tvi sm_103a". */
 const char* tvi_version(void);
 

@@ -20,8 +20,8 @@ TVI_ENOTCONV, TVI_ENONFINITE = -4, -5
 # every symbol include/tvi.h declares
 EXPORTS = ("tvi_default_options", "tvi_param_count", "tvi_workspace_bytes", "tvi_integrate",
            "tvi_adjoint", "tvi_adjoint_noalloc", "tvi_predictor_size", "tvi_predictor_forward",
-           "tvi_predictor_workspace_bytes", "tvi_predictor_train_step", "tvi_last_error",
-           "tvi_version")
+           "tvi_predictor_workspace_bytes", "tvi_predictor_train_step", "tvi_kernel_launches",
+           "tvi_last_error", "tvi_version")
 STATS = 6  # per-series statistics columns of tvi_integrate
 
 
@@ -85,6 +85,8 @@ def load():
             lib.tvi_predictor_train_step.argtypes = [vp, vp, vp, ci, ci, ci, ci, vp, vp, vp,
                                                      ctypes.c_float, ci, vp, vp, sz, vp]
             lib.tvi_predictor_train_step.restype = ci
+            lib.tvi_kernel_launches.argtypes = []
+            lib.tvi_kernel_launches.restype = ctypes.c_ulonglong
             lib.tvi_last_error.argtypes = []
             lib.tvi_last_error.restype = ctypes.c_char_p
             lib.tvi_version.argtypes = []

@@ -2,6 +2,7 @@
 // layout, kernel dispatch and status read-back.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -14,6 +15,7 @@
 namespace {
 
 thread_local std::string g_last_error;
+std::atomic<unsigned long long> g_launches{0};
 
 tvi_status fail(tvi_status code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 tvi_status fail(tvi_status code, const char* fmt, ...) {
@@ -111,6 +113,8 @@ tvi_status check_opt(const tvi_options* o) {
 }
 
 }  // namespace
+
+void tvi::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 extern "C" {
 
@@ -292,6 +296,10 @@ tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, in
 }
 
 const char* tvi_last_error(void) { return g_last_error.c_str(); }
+
+unsigned long long tvi_kernel_launches(void) {
+  return g_launches.load(std::memory_order_relaxed);
+}
 
 const char* tvi_version(void) { return "tvi sm_103a"; }
 

@@ -7,6 +7,10 @@
 
 namespace tvi {
 
+// Host-side count of the kernels this library has enqueued (every host thread),
+// read through tvi_kernel_launches(); called right before each launch.
+void note_launch();
+
 enum { kKindLinear = 0, kKindVdp = 1, kKindMlpTanh = 2, kKindMlpSilu = 3 };
 enum { kPrecFp64 = 0, kPrecFp32 = 1, kPrecBf16 = 2 };
 

@@ -1332,6 +1332,7 @@ cudaError_t launch_residual_t(const ResidualArgs& r, cudaStream_t s) {
   cudaError_t e = set_smem(mlp_residual_kernel<KIND, kResTP, T>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((r.L + kResTP - 1) / kResTP, r.B);
+  note_launch();
   mlp_residual_kernel<KIND, kResTP, T><<<grid, kTileThreads, sm, s>>>(r);
   return cudaGetLastError();
 }
@@ -1352,6 +1353,7 @@ cudaError_t launch_vjp_t(const VjpArgs& v, cudaStream_t s) {
   cudaError_t e = set_smem(mlp_vjp_kernel<KIND, kVjpTP, T>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((v.L + kVjpTP - 1) / kVjpTP, v.B);
+  note_launch();
   mlp_vjp_kernel<KIND, kVjpTP, T><<<grid, kTileThreads, sm, s>>>(v);
   return cudaGetLastError();
 }
@@ -1374,6 +1376,7 @@ cudaError_t launch_blocks(const BlocksArgs& bk, int precision, cudaStream_t s) {
   cudaError_t e = set_smem(mlp_blocks_kernel<T>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((bk.L + tp - 1) / tp, bk.B);
+  note_launch();
   mlp_blocks_kernel<T><<<grid, kTileThreads, sm, s>>>(bk, tp, stage);
   return cudaGetLastError();
 }
@@ -1394,10 +1397,13 @@ cudaError_t launch_blocks_tc(const BlocksArgs& bk, int* err, cudaStream_t s) {
   const int per_sm = static_cast<int>(kMaxDynSmem / sm) >= 2 ? 2 : 1;
   const int grid = tiles < per_sm * sms ? tiles : per_sm * sms;
   if (grid < 1) return cudaSuccess;
-  if (bk.d.n == 16)
+  if (bk.d.n == 16) {
+    note_launch();
     mlp_blocks_tc_kernel<16><<<grid, kTcThreads, sm, s>>>(bk, err);
-  else
+  } else {
+    note_launch();
     mlp_blocks_tc_kernel<32><<<grid, kTcThreads, sm, s>>>(bk, err);
+  }
   return cudaGetLastError();
 }
 
@@ -1418,11 +1424,13 @@ cudaError_t launch_chain(const ChainArgs& ch, cudaStream_t s) {
     const size_t sm = kChainWarps * 8 * slot;
     cudaError_t e = set_smem(mlp_chain_kernel<T, 8>, sm);
     if (e != cudaSuccess) return e;
+    note_launch();
     mlp_chain_kernel<T, 8><<<grid, 32 * kChainWarps, sm, s>>>(ch);
   } else {
     const size_t sm = kChainWarps * 4 * slot;
     cudaError_t e = set_smem(mlp_chain_kernel<T, 4>, sm);
     if (e != cudaSuccess) return e;
+    note_launch();
     mlp_chain_kernel<T, 4><<<grid, 32 * kChainWarps, sm, s>>>(ch);
   }
   return cudaGetLastError();
@@ -1456,12 +1464,15 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
   Ws w = carve(static_cast<char*>(workspace), B, c, d, precision, false);
   TVI_TRY(cudaMemsetAsync(w.worst, 0, sizeof(int), s));
   TVI_TRY(cudaMemsetAsync(w.tcerr, 0, sizeof(int), s));
+  note_launch();
   convert_weights_kernel<<<(d.P + 255) / 256, 256, 0, s>>>(a.params, w.Wf, d.P);
+  note_launch();
   mlp_start_kernel<<<(B * n + 255) / 256, 256, 0, s>>>(B, n, N + 1, a.y0, a.y_out, w.yi, w.status);
   TVI_TRY(cudaGetLastError());
   if (a.stats) TVI_TRY(cudaMemsetAsync(a.stats, 0, sizeof(int) * kStats * B, s));
   for (int i0 = 0; i0 < N; i0 += c) {
     const int L = (N - i0 < c) ? N - i0 : c;
+    note_launch();
     mlp_chunk_init_kernel<<<(B * c * n + 255) / 256, 256, 0, s>>>(B, n, c, w.dy, w.active, w.norm,
                                                                    w.iters);
     TVI_TRY(cudaGetLastError());
@@ -1474,6 +1485,7 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
       TVI_TRY(cudaMemsetAsync(w.remaining, 0, sizeof(int), s));
       CheckArgs ck{B, it, a.max_iter, a.tol_abs, a.tol_rel, w.norm, w.norm0, w.active, w.status,
                    w.iters, w.remaining};
+      note_launch();
       mlp_check_kernel<<<(B + 127) / 128, 128, 0, s>>>(ck);
       TVI_TRY(cudaGetLastError());
       int remaining = 0;
@@ -1490,9 +1502,11 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
       TVI_TRY(launch_blocks_any(bk, precision, w.tcerr, s));
       TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s));
     }
+    note_launch();
     mlp_store_kernel<<<B, 128, 0, s>>>(n, L, c, N + 1, i0, w.dy, w.yi, a.y_out, w.iters, a.stats);
     TVI_TRY(cudaGetLastError());
   }
+  note_launch();
   mlp_worst_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, w.status, w.tcerr, a.series_status, w.worst);
   TVI_TRY(cudaGetLastError());
   if (host_worst) {
@@ -1508,6 +1522,7 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
   const int B = a.B, N = a.N, c = a.chunk;
   Ws w = carve(static_cast<char*>(workspace), B, c, d, precision, true);
   TVI_TRY(cudaMemsetAsync(w.tcerr, 0, sizeof(int), s));
+  note_launch();
   convert_weights_kernel<<<(d.P + 255) / 256, 256, 0, s>>>(a.params, w.Wf, d.P);
   TVI_TRY(cudaMemsetAsync(w.carry, 0, sizeof(double) * B * n, s));  // a_{N+1} = 0
   TVI_TRY(cudaMemsetAsync(w.acc, 0, sizeof(double) * d.P, s));
@@ -1563,16 +1578,22 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
     nsplit = (npairs + per - 1) / per;
     ParamArgs pa{d, B, L, c, w.act, w.del, w.part, per};
     const dim3 pgrid(param_grad_tiles(d), nsplit);
-    if (precision == kPrecFp64)
+    if (precision == kPrecFp64) {
+      note_launch();
       mlp_param_grad_kernel<double><<<pgrid, 256, 0, s>>>(pa);
-    else
+    } else {
+      note_launch();
       mlp_param_grad_kernel<float><<<pgrid, 256, 0, s>>>(pa);
+    }
+    note_launch();
     mlp_param_reduce_kernel<<<(d.P + 255) / 256, 256, 0, s>>>(d.P, nsplit, w.part, w.acc);
     TVI_TRY(cudaGetLastError());
+    note_launch();
     mlp_carry_kernel<<<(B * n + 255) / 256, 256, 0, s>>>(B, n, L, c, w.dy, w.carry);
     TVI_TRY(cudaGetLastError());
   }
   const int cnt = (B * n > d.P) ? B * n : d.P;
+  note_launch();
   mlp_adjoint_end_kernel<<<(cnt + 255) / 256, 256, 0, s>>>(B, n, N + 1, w.carry, a.grad_out, a.dy0,
                                                           w.acc, a.dparams, d.P, w.tcerr);
   return cudaGetLastError();

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "tvi.h"
+#include "tvi_internal.h"
 #include "tvi_predictor.cuh"
 
 namespace tvi {
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int K, const f
 void sgemm(int M, int N, int K, const float* A, int sai, int sak, const float* B, int sbk, int sbj,
            const float* bias, float* C, float* H, int act, cudaStream_t s) {
   dim3 grid((N + 63) / 64, (M + 63) / 64);
+  note_launch();
   sgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, sai, sak, B, sbk, sbj, bias, C, H, act);
 }
 
@@ -227,6 +229,7 @@ tvi_status tvi_predictor_forward(const float* packed, int in, int hidden, int ou
   const tvi::PredDims d{in, hidden, out};
   const size_t sm = sizeof(float) * (in + 2 * hidden + out);
   if (sm > 48 * 1024) return TVI_EUNSUPPORTED;
+  tvi::note_launch();
   tvi::infer_kernel<<<M, 256, sm, static_cast<cudaStream_t>(stream)>>>(packed, d, x, y);
   return cudaGetLastError() == cudaSuccess ? TVI_OK : TVI_ECUDA;
 }
@@ -245,6 +248,7 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const PredOffsets o = pred_offsets(d);
   const int H = hidden;
+  note_launch();
   normalize_kernel<<<(M * (in > out ? in : out) + 255) / 256, 256, 0, s>>>(M, in, out, packed, o, x,
                                                                           target, rows, w.xn, w.tn);
   // forward
@@ -252,26 +256,34 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
   sgemm(M, H, H, w.H1, H, 1, packed + o.W2, 1, H, packed + o.b2, w.Z2, w.H2, 1, s);
   sgemm(M, out, H, w.H2, H, 1, packed + o.W3, 1, H, packed + o.b3, w.O, nullptr, 0, s);
   const int cnt = M * out, nb = (cnt + 255) / 256;
+  note_launch();
   mse_grad_kernel<<<nb, 256, 0, s>>>(cnt, w.O, w.tn, w.dO, w.partial);
+  note_launch();
   loss_reduce_kernel<<<1, 32, 0, s>>>(nb, cnt, w.partial, loss);
   // backward (gradients in the packed order W1 b1 W2 b2 W3 b3, offset by train_begin)
   float* g = w.g;
   auto G = [&](int off) { return g + (off - o.train_begin); };
   sgemm(out, H, M, w.dO, 1, out, w.H2, H, 1, nullptr, G(o.W3), nullptr, 0, s);
+  note_launch();
   colsum_kernel<<<(out + 127) / 128, 128, 0, s>>>(M, out, w.dO, G(o.b3));
   sgemm(M, H, out, w.dO, out, 1, packed + o.W3, H, 1, nullptr, w.dH, nullptr, 0, s);
+  note_launch();
   silu_backward_kernel<<<(M * H + 255) / 256, 256, 0, s>>>(M * H, w.Z2, w.dH, w.dZ);
   sgemm(H, H, M, w.dZ, 1, H, w.H1, H, 1, nullptr, G(o.W2), nullptr, 0, s);
+  note_launch();
   colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(M, H, w.dZ, G(o.b2));
   sgemm(M, H, H, w.dZ, H, 1, packed + o.W2, H, 1, nullptr, w.dH, nullptr, 0, s);
+  note_launch();
   silu_backward_kernel<<<(M * H + 255) / 256, 256, 0, s>>>(M * H, w.Z1, w.dH, w.dZ);
   sgemm(H, in, M, w.dZ, 1, H, w.xn, in, 1, nullptr, G(o.W1), nullptr, 0, s);
+  note_launch();
   colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(M, H, w.dZ, G(o.b1));
   // Adam
   const int np = o.total - o.train_begin;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const float c1 = 1.0f - powf(b1, static_cast<float>(step));
   const float c2 = 1.0f - powf(b2, static_cast<float>(step));
+  note_launch();
   adam_kernel<<<(np + 255) / 256, 256, 0, s>>>(np, packed + o.train_begin, g, adam_m, adam_v, lr, b1,
                                               b2, eps, c1, c2);
   return cudaGetLastError() == cudaSuccess ? TVI_OK : TVI_ECUDA;

@@ -564,12 +564,14 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
 
 template <class Model, typename T, int RPT>
 cudaError_t launch_fwd(const FwdArgs& a, int threads, cudaStream_t s) {
+  note_launch();
   forward_small_kernel<Model, T, RPT><<<a.B, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 template <class Model, typename T, int RPT>
 cudaError_t launch_adj(const AdjArgs& a, int threads, cudaStream_t s) {
+  note_launch();
   adjoint_small_kernel<Model, T, RPT><<<a.B, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -654,6 +656,7 @@ cudaError_t small_adjoint(int kind, int n, int precision, int rpt, int threads, 
             : dispatch_adj_rpt<ModelLinear<4>, float>(a, rpt, threads, s);
   if (e != cudaSuccess) return e;
   if (!a.per_series) {
+    note_launch();
     sum_partials_kernel<<<(P + 127) / 128, 128, 0, s>>>(a.partials, a.B, P, a.dparams);
     e = cudaGetLastError();
   }

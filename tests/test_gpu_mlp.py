@@ -215,3 +215,38 @@ def test_bf16_node32_silu_padded_lengths(tvi, oracle_lib):
     dp, dy0 = gpu_adjoint(tvi, w, 500, "bf16", ref, g, lengths=lens)
     assert relerr(dp, dp_ref) <= GATE["bf16"]
     assert relerr(dy0, dy0_ref) <= GATE["bf16"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+def test_mlp_degenerate_sizes(tvi, oracle_lib, precision):
+    """Series of length 0 and 1 among a full one, N = 1 and N = 0 (the trajectory
+    is y0 alone, the gradient is the loss gradient at y0), on every block path."""
+    w = workloads.mlp_ode(B=3, N=50, n=16, hidden=(64, 64), act="silu", t_end=1.0, seed=69)
+    m = OModel.from_spec(w["spec"])
+    lens = np.array([50, 0, 1], dtype=np.int32)
+    ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], lengths=lens,
+                                    tol_abs=1e-12)
+    assert not st.any()
+    y, _, status, rc = gpu_forward(tvi, w, 16, precision, 1e-12, lengths=lens)
+    assert rc == 0 and not status.any()
+    for b, L in enumerate(lens):
+        assert np.all(y[b, L + 1:] == y[b, L])
+    assert relerr_series(y, ref).max() <= GATE[precision]
+    g = workloads.random_grad_out(70, 3, 50, 16)
+    for b, L in enumerate(lens):
+        g[b, L + 1:] = 0.0
+    dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g, lengths=lens)
+    dp, dy0 = gpu_adjoint(tvi, w, 16, precision, ref, g, lengths=lens)
+    assert relerr(dp, dp_ref) <= GATE[precision]
+    assert relerr(dy0, dy0_ref) <= GATE[precision]
+    # N = 1 and N = 0
+    w1 = dict(w, times=w["times"][:, :2], lengths=None)
+    ref1, _, _ = oracle_lib.forward(m, w1["y0"], w1["times"], w1["params"], tol_abs=1e-12)
+    y1, _, _, rc = gpu_forward(tvi, w1, 16, precision, 1e-12)
+    assert rc == 0 and relerr_series(y1, ref1).max() <= GATE[precision]
+    w0 = dict(w, times=w["times"][:, :1], lengths=None)
+    y0o, _, _, rc = gpu_forward(tvi, w0, 16, precision, 1e-12)
+    assert rc == 0 and y0o.shape == (3, 1, 16) and np.array_equal(y0o[:, 0], w["y0"])
+    g0 = workloads.random_grad_out(71, 3, 0, 16)
+    dp0, dy00 = gpu_adjoint(tvi, w0, 16, precision, y0o, g0)
+    assert not dp0.any() and np.array_equal(dy00, g0[:, 0])

@@ -235,3 +235,20 @@ def test_autograd_function_matches_oracle_gradient(tvi, oracle_lib):
     dmu, dy0 = oracle_lib.adjoint(m, w["times"], w["params"], ref, 2.0 * ref)
     assert np.abs(mu.grad.cpu().numpy() - dmu).max() / np.abs(dmu).max() <= 1e-8
     assert np.abs(y0.grad.cpu().numpy() - dy0).max() / np.abs(dy0).max() <= 1e-8
+
+
+def test_kernel_launch_counter(tvi):
+    """One fused launch per forward pass and one per adjoint (per-series parameters:
+    no shared-parameter sum)."""
+    from paper_2310_08649_gb300 import _lib
+    lib = _lib.load()
+    w = workloads.vdp(B=4, N=300, seed=46)
+    c0 = lib.tvi_kernel_launches()
+    y, _, _, rc = run_gpu(tvi, w, 100, "fp32", 1e-10)
+    assert rc == 0 and lib.tvi_kernel_launches() - c0 == 1
+    tm = tvi.Model.from_spec(w["spec"])
+    c1 = lib.tvi_kernel_launches()
+    tvi.adjoint(tm, tvi.Options(chunk=100, precision="fp32"), dev(w["times"]), dev(w["params"]),
+                dev(y), dev(np.ones_like(y)))
+    torch.cuda.synchronize()
+    assert lib.tvi_kernel_launches() - c1 == 1
