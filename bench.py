@@ -266,9 +266,10 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # Roofline of the dominant kernel (FP64 pipe)
 # ---------------------------------------------------------------------------
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu --set full capture
-# of the default van der Pol workload (forward, adjoint); other workloads: not captured
-NCU_TRAFFIC = {("vdp", 1000, "fp32", 128, 10000): (10312448 + 1024, 51243520 + 26368)}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
+# default van der Pol workload (forward, adjoint kernels as built now); other workloads:
+# not captured
+NCU_TRAFFIC = {("vdp", 1000, "fp32", 128, 10000): (10317056 + 256, 51255808 + 0)}
 
 
 def roofline(args, w, stats, fwd_ms, adj_ms, refine):
