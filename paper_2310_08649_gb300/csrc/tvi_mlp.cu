@@ -97,6 +97,47 @@ __device__ __forceinline__ double step_dt(const double* tb, int len, int k) {
 }
 
 // ---------------------------------------------------------------------------
+// FP32 products of a tile of TP pairs: out(r, p) = sum_k A(r, k) X[k][p] for
+// r < R (a multiple of 4), with A(r, k) = Wg[r sr + k sk] read through the
+// read-only cache and X [K][TP] in shared memory.  Each thread owns 4 x 4
+// output tiles (16 FMAs per 4 weight loads and one 16-byte activation load);
+// the lanes of a warp share a row group, so the weight loads are broadcasts.
+// epi(r, p, value) receives every result.
+// ---------------------------------------------------------------------------
+template <int TP, typename Epi>
+__device__ __forceinline__ void tile_mm_f32(const float* __restrict__ Wg, int sr, int sk, int R,
+                                            int K, const float* X, Epi epi) {
+  constexpr int PG = TP / 4;
+  const int tiles = (R / 4) * PG;
+  for (int tt = threadIdx.x; tt < tiles; tt += kTileThreads) {
+    const int r0 = (tt / PG) * 4, p0 = (tt % PG) * 4;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    const float* w0 = Wg + static_cast<size_t>(r0) * sr;
+    for (int k = 0; k < K; ++k) {
+      const float4 x = *reinterpret_cast<const float4*>(X + k * TP + p0);
+      float w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) w[i] = __ldg(w0 + i * sr + k * sk);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        acc[i][0] = fmaf(w[i], x.x, acc[i][0]);
+        acc[i][1] = fmaf(w[i], x.y, acc[i][1]);
+        acc[i][2] = fmaf(w[i], x.z, acc[i][2]);
+        acc[i][3] = fmaf(w[i], x.w, acc[i][3]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) epi(r0 + i, p0 + j, acc[i][j]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Forward pass (in T: FP64, or FP32 for the mixed-precision adjoint) for a tile
 // of TP pairs held in shared memory.  Thread t takes pair p = t % TP and every
 // G-th output row (G = threads / TP), so the lanes of a warp read the same
@@ -109,6 +150,26 @@ template <int KIND, int TP, typename T>
 __device__ __forceinline__ void mlp_tile_forward(const MlpW<T>& w, const MlpDims& d, const T* sy,
                                                  T* sa1, T* sa2, T* sz3, int np, double* dv_tile,
                                                  int dvs) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    tile_mm_f32<TP>(w.W1, d.n, 1, d.h1, d.n, sy, [&](int r, int p, float z) {
+      float a, da;
+      act_hidden<KIND>(z + __ldg(w.b1 + r), a, da);
+      sa1[r * TP + p] = a;
+      if (dv_tile && p < np) dv_tile[p * dvs + r] = widen(da);
+    });
+    __syncthreads();
+    tile_mm_f32<TP>(w.W2, d.h1, 1, d.h2, d.h1, sa1, [&](int r, int p, float z) {
+      float a, da;
+      act_hidden<KIND>(z + __ldg(w.b2 + r), a, da);
+      sa2[r * TP + p] = a;
+      if (dv_tile && p < np) dv_tile[p * dvs + d.h1 + r] = widen(da);
+    });
+    __syncthreads();
+    tile_mm_f32<TP>(w.W3, d.h2, 1, d.n, d.h2, sa2,
+                    [&](int r, int p, float z) { sz3[r * TP + p] = z + __ldg(w.b3 + r); });
+    __syncthreads();
+    return;
+  }
   constexpr int G = kTileThreads / TP;
   const int t = threadIdx.x, p = t % TP, g = t / TP;
   const bool live = p < np;
@@ -1034,6 +1095,40 @@ __global__ void __launch_bounds__(kTileThreads) mlp_vjp_kernel(VjpArgs a) {
   for (int r = g; r < n; r += G)
     sz3[r * TP + p] = live ? narrow<T>(avb[j * n + r]) * sz3[r * TP + p] : T(0);
   __syncthreads();
+  if constexpr (sizeof(T) == sizeof(float)) {
+    // register-tiled products; then outputs with one thread per element
+    tile_mm_f32<TP>(w.W3, 1, h2, h2, n, sz3, [&](int c, int pp, float v) { sd2[c * TP + pp] *= v; });
+    __syncthreads();
+    tile_mm_f32<TP>(w.W2, 1, h1, h1, h2, sd2, [&](int c, int pp, float v) { sd1[c * TP + pp] *= v; });
+    __syncthreads();
+    if (a.res) {
+      float* sjt = sz3 + n * TP;  // J^T a, [n][TP]
+      tile_mm_f32<TP>(w.W1, 1, n, n, h1, sd1, [&](int c, int pp, float v) { sjt[c * TP + pp] = v; });
+      __syncthreads();
+      for (int e = threadIdx.x; e < n * TP; e += kTileThreads) {
+        const int c = e / TP, pp = e - c * TP;
+        if (pp >= np) continue;
+        const int jj = j0 + pp, kk = step_of(1, a.i0, a.L, jj);
+        const double prev = (jj > 0) ? avb[(jj - 1) * n + c] : a.carry[b * n + c];
+        const double gk = a.g[(static_cast<size_t>(b) * (a.N + 1) + kk) * n + c];
+        a.res[(static_cast<size_t>(b) * a.c + jj) * n + c] =
+            fma(step_dt(tb, len, kk), widen(sjt[c * TP + pp]), gk + prev - avb[jj * n + c]);
+      }
+    }
+    if (a.del) {
+      const int dw = h1 + h2 + n;
+      for (int e = threadIdx.x; e < dw * TP; e += kTileThreads) {
+        const int pp = e / dw, q = e - pp * dw;  // consecutive threads fill one row
+        if (pp >= np) continue;
+        const int jj = j0 + pp;
+        const float v = q < h1 ? sd1[q * TP + pp]
+                               : (q < h1 + h2 ? sd2[(q - h1) * TP + pp] : sz3[(q - h1 - h2) * TP + pp]);
+        a.del[(static_cast<size_t>(b) * a.c + jj) * dw + q] =
+            step_dt(tb, len, step_of(1, a.i0, a.L, jj)) * widen(v);
+      }
+    }
+    return;
+  }
   // delta2 = (W3^T delta3) * act'(z2)
   for (int c = g; c < h2; c += G) {
     T acc = T(0);
