@@ -69,6 +69,9 @@ __device__ __forceinline__ unsigned long long residual_norm_block(
 // Newton outcome of one chunk attempt.
 enum { kConv = 0, kMaxIter = 1, kNonFinite = 2, kDiverged = 3 };
 
+// shortest converged prefix of a failed chunk attempt that is kept
+constexpr int kMinPrefix = 8;
+
 template <class Model, typename T, int RPT>
 __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(FwdArgs a) {
   constexpr int NS = Model::NS;
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
   __shared__ double s_wlast[32][NS];
   __shared__ unsigned long long s_red[32];
   __shared__ double s_carry[NS];
-  __shared__ int s_ctl[2];  // outcome and Newton updates of the last attempt
+  __shared__ int s_ctl[3];  // outcome, Newton updates and converged prefix of the last attempt
   // predictor features, hidden activations and outputs (van der Pol only)
   __shared__ float s_pred[Model::kPredictable
                               ? (NS + 1 + kPredMaxChunk) + 2 * kPredMaxHidden + NS * kPredMaxChunk
@@ -270,13 +273,38 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
       const unsigned long long nb = block_max_u64(mx, s_red, lane, warp, nwa);
       const double nr = __longlong_as_double(static_cast<long long>(nb));
       if (it == 0) norm0 = nr;
-      if (nb >= kNonFiniteBits) { outcome = kNonFinite; break; }
-      if (nr <= a.tol_abs || nr <= a.tol_rel * norm0) { outcome = kConv; break; }
-      if (it >= a.max_iter) { outcome = kMaxIter; break; }
+      if (nb < kNonFiniteBits && (nr <= a.tol_abs || nr <= a.tol_rel * norm0)) {
+        outcome = kConv;
+        break;
+      }
       // When a smaller chunk can still be tried, an attempt whose residual is
       // still above 10x its starting value after 4 updates is abandoned early
       // (a heuristic for speed only: the retry solves the same equations).
-      if (can_halve && it >= 4 && nr > 10.0 * norm0) { outcome = kDiverged; break; }
+      const int fail = nb >= kNonFiniteBits                          ? kNonFinite
+                       : it >= a.max_iter                            ? kMaxIter
+                       : (can_halve && it >= 4 && nr > 10.0 * norm0) ? kDiverged
+                                                                     : kConv;
+      if (fail != kConv) {
+        outcome = fail;
+        if (can_halve) {
+          // Rows whose backward-Euler residual is already within the tolerance form
+          // a solution of their steps (row j involves only y_{j-1} and y_j), so the
+          // attempt's longest such prefix is kept: first row index over tolerance.
+          const unsigned long long thr = abs_bits(fmax(a.tol_abs, a.tol_rel * norm0));
+          unsigned long long v = 0ull;  // ~j of the first row over tolerance, max-reduced
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) {
+            bool over = false;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) over = over || abs_bits(R[r][s]) > thr;
+            if (act[r] && over) v = umax64(v, ~static_cast<unsigned long long>(tid * RPT + r));
+          }
+          sync_first(32 * nwa);  // s_red reuse
+          const unsigned long long m = block_max_u64(v, s_red, lane, warp, nwa);
+          if (tid == 0) s_ctl[2] = m ? static_cast<int>(~m) : L;
+        }
+        break;
+      }
 
       // ---- blocks, their inverses, and the cyclic-reduction solve ----
       Aff<NS, T> f[RPT];
@@ -332,10 +360,35 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
     it = s_ctl[1];
 
     if (outcome != kConv && can_halve) {
-      c_cur = (c_cur + 1) / 2;  // re-solve from the same chunk start with half the steps
+      // keep a converged prefix of at least kMinPrefix steps, then re-solve the rest
+      // of the chunk from its end with half the steps
+      const int K = s_ctl[2];
+      if (K >= kMinPrefix) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          const int j = tid * RPT + r;
+          if (act[r] && j < K) {
+            double* out = yb + static_cast<size_t>(i + 1 + j) * NS;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) out[s] = yv[r][s];
+          }
+          if (j == K - 1) {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) s_carry[s] = yv[r][s];
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < NS; ++s) yi[s] = s_carry[s];
+        i += K;
+        tot_iters += it;
+        ++n_chunks;
+        max_it = max(max_it, it);
+      }
+      c_cur = (c_cur + 1) / 2;
       ++retries;
       streak = 0;
-      __syncthreads();  // s_wlast / s_red reuse
+      __syncthreads();  // s_wlast / s_red / s_carry reuse
       continue;
     }
     if (outcome == kNonFinite) st = 2;
