@@ -269,7 +269,7 @@ class ClockSampler:
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the
 # default van der Pol workload (forward, adjoint kernels as built now); other workloads:
 # not captured
-NCU_TRAFFIC = {("vdp", 1000, "fp32", 128, 10000): (10317056 + 256, 51255808 + 0)}
+NCU_TRAFFIC = {("vdp", 1000, "fp32", 128, 10000): (10312192 + 256, 51243520 + 2816)}
 
 
 def roofline(args, w, stats, fwd_ms, adj_ms, refine):
