@@ -150,6 +150,7 @@ def time_oracle(w, g, tol, seconds, min_reps=1):
     import oracle
     m = oracle.Model.from_spec(w["spec"])
     B = w["times"].shape[0]
+    last = {}
 
     def run(S):
         lens = None if w["lengths"] is None else w["lengths"][:S]
@@ -157,8 +158,10 @@ def time_oracle(w, g, tol, seconds, min_reps=1):
         t0 = time.perf_counter()
         y, _, _ = oracle.forward(m, w["y0"][:S], w["times"][:S], p, lengths=lens, tol_abs=tol,
                                  max_iter=100)
-        oracle.adjoint(m, w["times"][:S], p, y, g[:S], lengths=lens)
-        return time.perf_counter() - t0
+        dp, dy0 = oracle.adjoint(m, w["times"][:S], p, y, g[:S], lengths=lens)
+        el = time.perf_counter() - t0
+        last.update(S=S, y=y, dp=dp, dy0=dy0)
+        return el
 
     cores = oracle.max_threads()
     S = min(B, max(cores, 1))
@@ -175,7 +178,7 @@ def time_oracle(w, g, tol, seconds, min_reps=1):
         reps += 1
     sample = (f"{'whole workload' if S == B else f'first {S} of {B} series'}, "
               f"{reps} forward+adjoint passes, {total:.1f} s")
-    return steps * reps / total, sample, cores, reps, total
+    return steps * reps / total, sample, cores, reps, total, last
 
 
 def run_reference(args):
@@ -189,7 +192,7 @@ def run_reference(args):
     t_total, units = 0.0, 0.0
     sample, cores = "", 0
     for _ in range(args.steps):
-        v, sample, cores, reps, el = time_oracle(w, g, args.tol, per_step)
+        v, sample, cores, reps, el, _ = time_oracle(w, g, args.tol, per_step)
         t_total += el
         units += v * el
     value = units / t_total
@@ -498,11 +501,29 @@ def run_ours(args):
     stats_np = res["stats"]
     roof = roofline(args, w, stats_np, fwd_ms, adj_ms, refine)
 
-    cpu = None
+    cpu, accuracy = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sample, cores, _, _ = time_oracle(w, g, args.tol, args.cpu_seconds)
+        v, sample, cores, _, _, ref = time_oracle(w, g, args.tol, args.cpu_seconds)
         cpu = {"value": v, "unit": "series*steps/s", "cores": cores, "kind": "oracle",
                "sample": sample}
+        # error of this run's outputs (the end-to-end leg's last step) against the FP64
+        # oracle on the oracle's sample of series, both stopped at the same Newton tol
+        S = ref["S"]
+        yg = y[:S].cpu().numpy()
+        lens_s = None if w["lengths"] is None else w["lengths"][:S]
+
+        def rel_rows(a, b):
+            a, b = a.reshape(a.shape[0], -1), b.reshape(b.shape[0], -1)
+            return float(np.max(np.abs(a - b).max(axis=1) / np.maximum(np.abs(b).max(axis=1),
+                                                                        1e-300)))
+        accuracy = {"series": int(S), "y_max_rel": rel_rows(yg, ref["y"]),
+                    "dy0_max_rel": rel_rows(h_dy0.numpy()[:S], ref["dy0"])}
+        if model.per_series:
+            accuracy["dparams_max_rel"] = rel_rows(h_dp.numpy()[:S], ref["dp"])
+        accuracy["note"] = ("per series max_k |y - y_ref| / max_k |y_ref|; both solvers stop "
+                            "Newton at tol, so the forward difference includes the problem's "
+                            "conditioning, and the gradients differ through the trajectories"
+                            + ("" if lens_s is None else "; padded series"))
 
     if rank == 0:
         upd, nchk = stats_np[:, 0].astype(np.float64), stats_np[:, 1].astype(np.float64)
@@ -523,6 +544,7 @@ def run_ours(args):
                                  "retries_max": int(stats_np[:, 2].max()),
                                  "max_updates_one_chunk": int(stats_np[:, 3].max())},
                 "chunk1_fp64": chunk1, "roofline": roof, "cpu_baseline": cpu,
+                "accuracy_vs_oracle": accuracy,
                 "e2e": {"value": e2e_value, "unit": "series*steps/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h,
                         "note": "pinned host buffers; dL/dy upload overlapped with the forward "
