@@ -199,8 +199,8 @@ class Integrate(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, y0, params, times, model, opts, lengths=None):
-        y, _, _, _ = integrate(model, opts, y0.contiguous(), times.contiguous(),
-                               params.contiguous(), lengths)
+        times, params = times.contiguous(), params.contiguous()
+        y, _, _, _ = integrate(model, opts, y0.contiguous(), times, params, lengths)
         ctx.model, ctx.opts = model, opts
         ctx.save_for_backward(times, params, y, lengths if lengths is not None else torch.empty(0))
         ctx.has_lengths = lengths is not None
@@ -209,8 +209,8 @@ class Integrate(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_y):
         times, params, y, lengths = ctx.saved_tensors
-        dparams, dy0 = adjoint(ctx.model, ctx.opts, times, params.contiguous(), y,
-                               grad_y.contiguous(), lengths if ctx.has_lengths else None)
+        dparams, dy0 = adjoint(ctx.model, ctx.opts, times, params, y, grad_y.contiguous(),
+                               lengths if ctx.has_lengths else None)
         return dy0, dparams, None, None, None, None
 
 
