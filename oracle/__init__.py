@@ -14,8 +14,9 @@ shares no code with the CUDA path.
   chunk-size invariance checks.
 * ``predictor`` holds the FP64 reference of the Newton-predictor MLP.
 """
-from .core import (KIND_IDS, Model, adjoint, forward, forward_error_estimate, jac, max_threads,
-                   param_count, rhs, step_matrices, vjp_p)
+from .core import (KIND_IDS, Model, adjoint, adjoint_euler, forward, forward_error_estimate,
+                   forward_euler, jac, max_threads, param_count, rhs, step_matrices, vjp_p)
 
-__all__ = ["KIND_IDS", "Model", "adjoint", "forward", "forward_error_estimate", "jac",
+__all__ = ["KIND_IDS", "Model", "adjoint", "adjoint_euler", "forward", "forward_euler",
+           "forward_error_estimate", "jac",
            "max_threads", "param_count", "rhs", "step_matrices", "vjp_p"]

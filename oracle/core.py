@@ -61,6 +61,12 @@ def _load():
             lib.tvo_adjoint.argtypes = [mp, ctypes.c_int, ctypes.c_int, dp, ip, dp, dp, dp,
                                         ctypes.c_int, dp, dp]
             lib.tvo_adjoint.restype = ctypes.c_int
+            lib.tvo_forward_euler.argtypes = [mp, ctypes.c_int, ctypes.c_int, dp, dp, ip, dp,
+                                              ctypes.c_int, dp, ip]
+            lib.tvo_forward_euler.restype = ctypes.c_int
+            lib.tvo_adjoint_euler.argtypes = [mp, ctypes.c_int, ctypes.c_int, dp, ip, dp, dp, dp,
+                                              ctypes.c_int, dp, dp]
+            lib.tvo_adjoint_euler.restype = ctypes.c_int
             lib.tvo_step_matrices.argtypes = [mp, ctypes.c_int, ctypes.c_int, dp, ip, dp, dp, dp]
             lib.tvo_step_matrices.restype = ctypes.c_int
             lib.tvo_max_threads.argtypes = []
@@ -142,6 +148,38 @@ def adjoint(model, times, params, y, grad_out, lengths=None, nthreads=0):
                              _dptr(dparams), _dptr(dy0))
     if rc < 0:
         raise ValueError("tvo_adjoint rejected its arguments")
+    return dparams, dy0
+
+
+def forward_euler(model, y0, times, params, lengths=None, nthreads=0):
+    """Forward Euler, step by step (Sec. 2.2, explicit methods).  Returns
+    (y [B][N+1][n], status [B])."""
+    y0, times, params = _f64(y0), _f64(times), _f64(params)
+    B, n = y0.shape
+    N = times.shape[1] - 1
+    lens = None if lengths is None else np.ascontiguousarray(lengths, dtype=np.int32)
+    y = np.empty((B, N + 1, n))
+    status = np.zeros(B, dtype=np.int32)
+    rc = _load().tvo_forward_euler(ctypes.byref(model.c()), B, N, _dptr(y0), _dptr(times),
+                                   _iptr(lens), _dptr(params), int(nthreads), _dptr(y),
+                                   _iptr(status))
+    if rc < 0:
+        raise ValueError("tvo_forward_euler rejected its arguments")
+    return y, status
+
+
+def adjoint_euler(model, times, params, y, grad_out, lengths=None, nthreads=0):
+    """Discrete adjoint of the forward-Euler recursion.  Returns (dparams, dy0)."""
+    times, params, y, grad_out = _f64(times), _f64(params), _f64(y), _f64(grad_out)
+    B, Np1, n = y.shape
+    lens = None if lengths is None else np.ascontiguousarray(lengths, dtype=np.int32)
+    dparams = np.zeros_like(params)
+    dy0 = np.zeros((B, n))
+    rc = _load().tvo_adjoint_euler(ctypes.byref(model.c()), B, Np1 - 1, _dptr(times),
+                                   _iptr(lens), _dptr(params), _dptr(y), _dptr(grad_out),
+                                   int(nthreads), _dptr(dparams), _dptr(dy0))
+    if rc < 0:
+        raise ValueError("tvo_adjoint_euler rejected its arguments")
     return dparams, dy0
 
 

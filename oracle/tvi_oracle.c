@@ -412,6 +412,97 @@ int tvo_adjoint(const tvo_model* m, int B, int N, const double* times, const int
   return worst;
 }
 
+int tvo_forward_euler(const tvo_model* m, int B, int N, const double* y0, const double* times,
+                      const int* lengths, const double* params, int nthreads, double* y,
+                      int* status) {
+  int P = tvo_param_count(m);
+  if (P < 0 || B < 0 || N < 0) return TVO_BADARG;
+  int n = m->n;
+  int worst = TVO_OK;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(max : worst)
+#endif
+  for (int b = 0; b < B; ++b) {
+    const double* p = m->per_series ? params + (size_t)b * P : params;
+    const double* tb = times + (size_t)b * (N + 1);
+    double* yb = y + (size_t)b * (N + 1) * n;
+    double h[64];
+    double* hp = (n <= 64) ? h : (double*)malloc(sizeof(double) * n);
+    int st = TVO_OK;
+    for (int i = 0; i < n; ++i) yb[i] = y0[(size_t)b * n + i];
+    for (int k = 1; k <= N; ++k) {
+      const double dt = step_dt(tb, lengths, b, k);
+      const double* yp = yb + (size_t)(k - 1) * n;
+      double* yk = yb + (size_t)k * n;
+      tvo_rhs(m, p, yp, tb[k - 1], hp);
+      for (int i = 0; i < n; ++i) {
+        yk[i] = yp[i] + dt * hp[i];
+        if (!isfinite(yk[i])) st = TVO_NONFINITE;
+      }
+    }
+    if (hp != h) free(hp);
+    if (status) status[b] = st;
+    if (st > worst) worst = st;
+  }
+  return worst;
+}
+
+int tvo_adjoint_euler(const tvo_model* m, int B, int N, const double* times, const int* lengths,
+                      const double* params, const double* y, const double* grad_out,
+                      int nthreads, double* dparams, double* dy0) {
+  int P = tvo_param_count(m);
+  if (P < 0 || B < 0 || N < 0) return TVO_BADARG;
+  int n = m->n;
+  size_t dp_len = m->per_series ? (size_t)B * P : (size_t)P;
+  memset(dparams, 0, sizeof(double) * dp_len);
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#else
+  nthreads = 1;
+#endif
+  /* shared parameters: per-series accumulators summed in series order */
+  double* acc = NULL;
+  if (!m->per_series) acc = (double*)calloc((size_t)B * P, sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+  for (int b = 0; b < B; ++b) {
+    const double* p = m->per_series ? params + (size_t)b * P : params;
+    double* gp = m->per_series ? dparams + (size_t)b * P : acc + (size_t)b * P;
+    const double* tb = times + (size_t)b * (N + 1);
+    const double* yb = y + (size_t)b * (N + 1) * n;
+    const double* gb = grad_out + (size_t)b * (N + 1) * n;
+    double* lam = (double*)malloc(sizeof(double) * (2 * n + n * n));
+    double* nxt = lam + n;
+    double* J = nxt + n;
+    for (int i = 0; i < n; ++i) lam[i] = gb[(size_t)N * n + i]; /* lambda_N */
+    for (int k = N; k >= 1; --k) {
+      const double dt = step_dt(tb, lengths, b, k);
+      const double* yp = yb + (size_t)(k - 1) * n;
+      /* dL/dp += dt_k (dh/dp at y_{k-1})^T lambda_k */
+      if (dt != 0.0) tvo_vjp_p(m, p, yp, tb[k - 1], lam, dt, gp);
+      /* lambda_{k-1} = dL/dy_{k-1} + (I + dt_k j(y_{k-1}))^T lambda_k */
+      tvo_jac(m, p, yp, tb[k - 1], J);
+      for (int c = 0; c < n; ++c) {
+        double s = lam[c];
+        for (int r = 0; r < n; ++r) s += dt * J[r * n + c] * lam[r];
+        nxt[c] = gb[(size_t)(k - 1) * n + c] + s;
+      }
+      for (int i = 0; i < n; ++i) lam[i] = nxt[i];
+    }
+    if (dy0)
+      for (int i = 0; i < n; ++i) dy0[(size_t)b * n + i] = lam[i];
+    free(lam);
+  }
+  if (acc) {
+    for (int b = 0; b < B; ++b)
+      for (int q = 0; q < P; ++q) dparams[q] += acc[(size_t)b * P + q];
+    free(acc);
+  }
+  return TVO_OK;
+}
+
 int tvo_step_matrices(const tvo_model* m, int B, int N, const double* times, const int* lengths,
                       const double* params, const double* y, double* A) {
   int P = tvo_param_count(m);

@@ -80,6 +80,22 @@ int tvo_adjoint(const tvo_model* m, int B, int N, const double* times, const int
                 const double* params, const double* y, const double* grad_out, int nthreads,
                 double* dparams, double* dy0);
 
+/* Forward Euler (Sec. 2.2, explicit methods): y_k = y_{k-1} + dt_k h(y_{k-1},
+ * t_{k-1}), step by step; padded steps (dt_k = 0) keep the state.  Returns
+ * TVO_OK, TVO_BADARG or TVO_NONFINITE (status [B] may be NULL). */
+int tvo_forward_euler(const tvo_model* m, int B, int N, const double* y0, const double* times,
+                      const int* lengths, const double* params, int nthreads, double* y,
+                      int* status);
+
+/* Discrete adjoint of tvo_forward_euler's recursion at the trajectory y, written
+ * out from the chain rule: lambda_N = dL/dy_N,
+ *   lambda_k = dL/dy_k + (I + dt_{k+1} j(y_k))^T lambda_{k+1}   (k = N-1 .. 0),
+ *   dL/dp = sum_{k=1..N} dt_k (dh/dp at y_{k-1})^T lambda_k,  dL/dy0 = lambda_0.
+ * Writes dparams (zeroed first) and dy0 (may be NULL). */
+int tvo_adjoint_euler(const tvo_model* m, int B, int N, const double* times, const int* lengths,
+                      const double* params, const double* y, const double* grad_out,
+                      int nthreads, double* dparams, double* dy0);
+
 /* Step matrices A_k = I - dt_k j(y_k) of every series and step k = 1..N at a
  * given trajectory y, into A [B][N][n][n] (dt_k = 0 on padded steps).  Used to
  * propagate perturbations through the linearised backward-Euler recursion
