@@ -73,6 +73,15 @@ typedef enum {
                              ||dt D3 J||_1 > 1/8), chain in FP32 */
 } tvi_precision;
 
+/* Time-integration scheme (Sec. 2.2).  Backward Euler: y_k - y_{k-1} -
+ * dt_k h(y_k) = 0, Newton on the chunk's implicit equations.  Forward Euler:
+ * y_k - y_{k-1} - dt_k h(y_{k-1}) = 0; chunked the same way, its chunk system has
+ * identity diagonal blocks and sub-diagonal -(I + dt_k j(y_{k-1})), so each
+ * Newton update is the same scan with no block inverse, and its adjoint is
+ * a_k = dL/dy_k + (I + dt_{k+1} j(y_k))^T a_{k+1}, dL/dp = sum_k dt_k
+ * (dh/dp at y_{k-1})^T a_k, dL/dy0 = dL/dy_0 + (I + dt_1 j(y_0))^T a_1. */
+typedef enum { TVI_BACKWARD_EULER = 0, TVI_FORWARD_EULER = 1 } tvi_scheme;
+
 typedef struct {
   int kind;        /* tvi_model_kind */
   int n;           /* state size */
@@ -103,11 +112,13 @@ typedef struct {
   int predictor_chunk;     /* steps the predictor proposes (its output is 2 x this);
                               used for chunk attempts of exactly this length */
   int predictor_hidden;    /* hidden width of the predictor MLP (even, <= 256) */
+  int scheme;              /* tvi_scheme: TVI_BACKWARD_EULER (default) or
+                              TVI_FORWARD_EULER (linear and van der Pol models) */
 } tvi_options;
 
 /* Fill *opt with defaults: chunk 1, tol_abs 1e-8, tol_rel 0, max_iter 50, FP64,
  * retry_halving 1, adjoint_refine 2, rows_per_thread 0, sync_status 1, no
- * predictor. */
+ * predictor, backward Euler. */
 void tvi_default_options(tvi_options* opt);
 
 /* Number of parameters P of one parameter vector, or -1 for a bad model. */

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libtvi.so")
 
 MODEL_KINDS = {"linear": 0, "vdp": 1, "mlp_tanh": 2, "mlp_silu": 3}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
+SCHEMES = {"backward": 0, "forward": 1}
 STATUS = {0: "TVI_OK", -1: "TVI_EINVAL", -2: "TVI_EWORKSPACE", -3: "TVI_ECUDA",
           -4: "TVI_ENOTCONV", -5: "TVI_ENONFINITE", -7: "TVI_EUNSUPPORTED"}
 TVI_ENOTCONV, TVI_ENONFINITE = -4, -5
@@ -36,7 +37,8 @@ class TviOptions(ctypes.Structure):
                 ("precision", ctypes.c_int), ("retry_halving", ctypes.c_int),
                 ("adjoint_refine", ctypes.c_int), ("rows_per_thread", ctypes.c_int),
                 ("sync_status", ctypes.c_int), ("predictor", ctypes.c_void_p),
-                ("predictor_chunk", ctypes.c_int), ("predictor_hidden", ctypes.c_int)]
+                ("predictor_chunk", ctypes.c_int), ("predictor_hidden", ctypes.c_int),
+                ("scheme", ctypes.c_int)]
 
 
 class TviError(RuntimeError):

@@ -40,7 +40,8 @@ class Model:
 
 @dataclass
 class Options:
-    """Solver options (tvi_options).  precision: 'fp64' | 'fp32' | 'bf16'."""
+    """Solver options (tvi_options).  precision: 'fp64' | 'fp32' | 'bf16';
+    scheme: 'backward' | 'forward' Euler."""
     chunk: int = 1
     tol_abs: float = 1e-8
     tol_rel: float = 0.0
@@ -53,10 +54,13 @@ class Options:
     predictor: object = None      # packed predictor: CUDA float32 tensor, or None
     predictor_chunk: int = 0
     predictor_hidden: int = 0
+    scheme: str = "backward"      # 'backward' | 'forward' (Euler)
 
     def c(self):
         if self.precision not in _lib.PRECISIONS:
             raise ValueError(f"unknown precision {self.precision!r}")
+        if self.scheme not in _lib.SCHEMES:
+            raise ValueError(f"unknown scheme {self.scheme!r}")
         pred = None
         if self.predictor is not None:
             _check(self.predictor, "predictor", torch.float32, tuple(self.predictor.shape))
@@ -65,7 +69,8 @@ class Options:
                                int(self.max_iter), _lib.PRECISIONS[self.precision],
                                int(bool(self.retry_halving)), int(self.adjoint_refine),
                                int(self.rows_per_thread), int(bool(self.sync_status)), pred,
-                               int(self.predictor_chunk), int(self.predictor_hidden))
+                               int(self.predictor_chunk), int(self.predictor_hidden),
+                               _lib.SCHEMES[self.scheme])
 
 
 def _check(t, name, dtype, shape, allow_none=False):

@@ -75,6 +75,10 @@ tvi_status check_model(const tvi_model* m) {
 
 // BF16 block products run on the tensor cores of the MLP path only
 tvi_status check_precision(const tvi_model* m, const tvi_options* o) {
+  if (o->scheme == TVI_FORWARD_EULER && (is_mlp(m) || o->predictor))
+    return fail(TVI_EUNSUPPORTED,
+                "forward Euler is built for the linear and van der Pol models, without a "
+                "predictor");
   if (o->precision != tvi::kPrecBf16) return TVI_OK;
   if (!is_mlp(m) || !tvi::mlp_tc_supported(m->n, m->hidden1, m->hidden2))
     return fail(TVI_EUNSUPPORTED,
@@ -109,6 +113,8 @@ tvi_status check_opt(const tvi_options* o) {
                 "predictor_hidden <= %d", tvi::kPredMaxChunk, tvi::kPredMaxHidden);
   if (o->adjoint_refine < 0 || o->adjoint_refine > 16)
     return fail(TVI_EINVAL, "adjoint_refine must be in [0, 16]");
+  if (o->scheme != TVI_BACKWARD_EULER && o->scheme != TVI_FORWARD_EULER)
+    return fail(TVI_EINVAL, "unknown scheme %d", o->scheme);
   return TVI_OK;
 }
 
@@ -132,6 +138,7 @@ void tvi_default_options(tvi_options* opt) {
   opt->predictor = nullptr;
   opt->predictor_chunk = 0;
   opt->predictor_hidden = 0;
+  opt->scheme = TVI_BACKWARD_EULER;
 }
 
 int tvi_param_count(const tvi_model* m) {
@@ -202,6 +209,7 @@ tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, 
   a.pred = opt->predictor;
   a.pred_chunk = opt->predictor_chunk;
   a.pred_hid = opt->predictor_hidden;
+  a.scheme = opt->scheme;
   if (a.pred && model->kind != TVI_MODEL_VDP)
     return fail(TVI_EUNSUPPORTED, "the Newton predictor is built for the van der Pol model");
 
@@ -263,6 +271,7 @@ tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, in
   a.N = N;
   a.chunk = opt->chunk < tvi::kSmallMaxChunk ? opt->chunk : tvi::kSmallMaxChunk;
   a.refine = opt->precision == tvi::kPrecFp64 ? 0 : opt->adjoint_refine;
+  a.scheme = opt->scheme;
   a.per_series = model->per_series ? 1 : 0;
   a.times = times;
   a.lengths = lengths;
@@ -393,6 +402,7 @@ extern "C" tvi_status tvi_adjoint_noalloc(const tvi_model* model, const tvi_opti
   a.N = N;
   a.chunk = opt->chunk < tvi::kSmallMaxChunk ? opt->chunk : tvi::kSmallMaxChunk;
   a.refine = opt->precision == tvi::kPrecFp64 ? 0 : opt->adjoint_refine;
+  a.scheme = opt->scheme;
   a.per_series = model->per_series ? 1 : 0;
   a.times = times;
   a.lengths = lengths;

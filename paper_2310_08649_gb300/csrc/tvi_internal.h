@@ -13,6 +13,8 @@ void note_launch();
 
 enum { kKindLinear = 0, kKindVdp = 1, kKindMlpTanh = 2, kKindMlpSilu = 3 };
 enum { kPrecFp64 = 0, kPrecFp32 = 1, kPrecBf16 = 2 };
+// integration schemes (Sec. 2.2): backward Euler, forward Euler
+enum { kSchemeBackward = 0, kSchemeForward = 1 };
 
 // Largest chunk the fused small-state kernels hold on chip; a larger requested
 // chunk is solved as chunks of this size (same equations, same result).
@@ -37,6 +39,7 @@ struct FwdArgs {
   int* worst;          // device word: max status over series
   const float* pred;   // packed Newton predictor or null
   int pred_chunk, pred_hid;
+  int scheme;          // kSchemeBackward / kSchemeForward
 };
 
 // per-series statistics: updates, chunks, retries, max updates of a chunk,
@@ -55,6 +58,7 @@ struct AdjArgs {
   double* dparams;
   double* dy0;       // [B][n] or null
   double* partials;  // [B][P] per-series gradient partials (shared parameters)
+  int scheme;        // kSchemeBackward / kSchemeForward
 };
 
 bool small_supported(int kind, int n);

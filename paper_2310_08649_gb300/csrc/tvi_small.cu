@@ -16,7 +16,10 @@
 //   reduction  d_j = M_j d_{j-1} + v_j  by serial runs + cyclic reduction  in T
 //   update     dy_j -= d_j                                   FP64
 // T = double (FP64 mode) or float (mixed mode: the FP64 residual makes Newton
-// an iterative refinement that converges to the FP64 solution).
+// an iterative refinement that converges to the FP64 solution).  The iterate is
+// held as y_j = y_i + dy_j itself.  Forward Euler (Sec. 2.2, explicit methods)
+// uses the same loop with h and j taken at y_{j-1}: R_j = y_j - y_{j-1} -
+// dt_j h(y_{j-1}) and d_j = (I + dt_j j(y_{j-1})) d_{j-1} + R_j (no inverse).
 #include "tvi_device.cuh"
 #include "tvi_internal.h"
 #include "tvi_models.cuh"
@@ -90,6 +93,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int pred_used = 0, pred_rejected = 0;
   int pred_wait = 0, pred_streak = 0;  // back-off after rejected guesses
+  const bool fwd_euler = a.scheme == kSchemeForward;
   const int N = a.N;
   const double* tb = a.times + static_cast<size_t>(b) * (N + 1);
   double* yb = a.y_out + static_cast<size_t>(b) * (N + 1) * NS;
@@ -258,14 +262,17 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
       if (wact) {
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
-          double y[NS], h[NS];
-#pragma unroll
-          for (int s = 0; s < NS; ++s) y[s] = yv[r][s];
-          mdl.rhs(y, h);
+          // backward Euler evaluates h at y_j, forward Euler at y_{j-1} (Sec. 2.2)
+          double yp[NS], yh[NS], h[NS];
 #pragma unroll
           for (int s = 0; s < NS; ++s) {
-            const double pv = (r == 0) ? prev[s] : yv[r - 1][s];
-            R[r][s] = act[r] ? fma(-dt[r], h[s], yv[r][s] - pv) : 0.0;
+            yp[s] = (r == 0) ? prev[s] : yv[r - 1][s];
+            yh[s] = fwd_euler ? yp[s] : yv[r][s];
+          }
+          mdl.rhs(yh, h);
+#pragma unroll
+          for (int s = 0; s < NS; ++s) {
+            R[r][s] = act[r] ? fma(-dt[r], h[s], yv[r][s] - yp[s]) : 0.0;
             mx = umax64(mx, abs_bits(R[r][s]));
           }
         }
@@ -316,20 +323,35 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
             T yt[NS], A[NS][NS];
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-              if constexpr (kMixed) yt[s] = yT[r][s];
-              else yt[s] = yv[r][s];
+              if (fwd_euler) {  // the Jacobian block of forward Euler is taken at y_{j-1}
+                if constexpr (kMixed) yt[s] = (r == 0) ? narrow<T>(prev[s]) : yT[r - 1][s];
+                else yt[s] = (r == 0) ? prev[s] : yv[r - 1][s];
+              } else {
+                if constexpr (kMixed) yt[s] = yT[r][s];
+                else yt[s] = yv[r][s];
+              }
             }
-            mdl.step_matrix(yt, dtT[r], A);
-            block_inverse<NS, T>(A, f[r].M);
+            mdl.step_matrix(yt, dtT[r], A);  // A = I - dt j
             T Rt[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) Rt[q] = narrow<T>(R[r][q]);
+            if (fwd_euler) {
+              // diagonal block I, sub-diagonal -(I + dt j): d_j = (2I - A) d_{j-1} + R_j
 #pragma unroll
-            for (int p = 0; p < NS; ++p) {
-              T sacc = T(0);
+              for (int p = 0; p < NS; ++p) {
 #pragma unroll
-              for (int q = 0; q < NS; ++q) sacc = fma(f[r].M[p][q], Rt[q], sacc);
-              f[r].v[p] = sacc;
+                for (int q = 0; q < NS; ++q) f[r].M[p][q] = (p == q ? T(2) : T(0)) - A[p][q];
+                f[r].v[p] = Rt[p];
+              }
+            } else {
+              block_inverse<NS, T>(A, f[r].M);
+#pragma unroll
+              for (int p = 0; p < NS; ++p) {
+                T sacc = T(0);
+#pragma unroll
+                for (int q = 0; q < NS; ++q) sacc = fma(f[r].M[p][q], Rt[q], sacc);
+                f[r].v[p] = sacc;
+              }
             }
           } else {
             aff_identity(f[r]);
@@ -458,6 +480,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
   const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int N = a.N, c = a.chunk;
+  const bool fwd_euler = a.scheme == kSchemeForward;
   const double* tb = a.times + static_cast<size_t>(b) * (N + 1);
   const double* yb = a.y + static_cast<size_t>(b) * (N + 1) * NS;
   const double* gb = a.grad_out + static_cast<size_t>(b) * (N + 1) * NS;
@@ -478,7 +501,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
     const int i = ci * c;
     const int L = min(c, N - i);
     const int nwa = ((L + RPT - 1) / RPT + 31) / 32;
-    double yk[RPT][NS], gk[RPT][NS], dt[RPT], av[RPT][NS];
+    double yk[RPT][NS], gk[RPT][NS], dt[RPT], dtb[RPT], av[RPT][NS];
     bool act[RPT];
     Aff<NS, T> f[RPT];
     // warps holding no step of a short (last) chunk skip to the carry barrier
@@ -490,6 +513,9 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
       act[r] = q < L;
       const int k = i + L - q;
       dt[r] = (act[r] && k <= len) ? (tb[k] - tb[k - 1]) : 0.0;
+      // the step whose block couples a_k to a_{k+1}: backward Euler dt_k at y_k;
+      // forward Euler dt_{k+1} at y_k (a_k = g_k + (I + dt_{k+1} j_k)^T a_{k+1})
+      dtb[r] = !fwd_euler ? dt[r] : ((act[r] && k + 1 <= len) ? (tb[k + 1] - tb[k]) : 0.0);
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         yk[r][s] = act[r] ? yb[static_cast<size_t>(k) * NS + s] : 0.0;
@@ -499,21 +525,37 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
         T yt[NS], A[NS][NS], Ai[NS][NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) yt[s] = narrow<T>(yk[r][s]);
-        mdl.step_matrix(yt, narrow<T>(dt[r]), A);
-        block_inverse<NS, T>(A, Ai);
+        mdl.step_matrix(yt, narrow<T>(dtb[r]), A);  // A = I - dt j(y_k)
+        if (fwd_euler) {
+          // x_q = (2I - A)^T x_{q-1} + g_k, the carry a_{i+L+1} entering row 0
 #pragma unroll
-        for (int p = 0; p < NS; ++p)
+          for (int p = 0; p < NS; ++p)
 #pragma unroll
-          for (int q2 = 0; q2 < NS; ++q2) f[r].M[p][q2] = Ai[q2][p];  // A^-T
-        double rhs[NS];
+            for (int q2 = 0; q2 < NS; ++q2) f[r].M[p][q2] = (p == q2 ? T(2) : T(0)) - A[q2][p];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) rhs[s] = gk[r][s] + ((q == 0) ? carry[s] : 0.0);
+          for (int p = 0; p < NS; ++p) {
+            T sacc = narrow<T>(gk[r][p]);
+            if (q == 0)
 #pragma unroll
-        for (int p = 0; p < NS; ++p) {
-          T sacc = T(0);
+              for (int q2 = 0; q2 < NS; ++q2) sacc = fma(f[r].M[p][q2], narrow<T>(carry[q2]), sacc);
+            f[r].v[p] = sacc;
+          }
+        } else {
+          block_inverse<NS, T>(A, Ai);
 #pragma unroll
-          for (int q2 = 0; q2 < NS; ++q2) sacc = fma(f[r].M[p][q2], narrow<T>(rhs[q2]), sacc);
-          f[r].v[p] = sacc;
+          for (int p = 0; p < NS; ++p)
+#pragma unroll
+            for (int q2 = 0; q2 < NS; ++q2) f[r].M[p][q2] = Ai[q2][p];  // A^-T
+          double rhs[NS];
+#pragma unroll
+          for (int s = 0; s < NS; ++s) rhs[s] = gk[r][s] + ((q == 0) ? carry[s] : 0.0);
+#pragma unroll
+          for (int p = 0; p < NS; ++p) {
+            T sacc = T(0);
+#pragma unroll
+            for (int q2 = 0; q2 < NS; ++q2) sacc = fma(f[r].M[p][q2], narrow<T>(rhs[q2]), sacc);
+            f[r].v[p] = sacc;
+          }
         }
       } else {
         aff_identity(f[r]);
@@ -548,13 +590,23 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
         double A[NS][NS];
-        mdl.step_matrix(yk[r], dt[r], A);
+        mdl.step_matrix(yk[r], dtb[r], A);
         double res[NS];
 #pragma unroll
         for (int p = 0; p < NS; ++p) {
-          double sacc = gk[r][p] + ((r == 0) ? nxt[p] : av[r - 1][p]);
+          double sacc;
+          if (fwd_euler) {  // g_k + (2I - A)^T a_{k+1} - a_k
+            sacc = gk[r][p] - av[r][p];
 #pragma unroll
-          for (int q2 = 0; q2 < NS; ++q2) sacc = fma(-A[q2][p], av[r][q2], sacc);
+            for (int q2 = 0; q2 < NS; ++q2) {
+              const double an = (r == 0) ? nxt[q2] : av[r - 1][q2];
+              sacc = fma((p == q2 ? 2.0 : 0.0) - A[q2][p], an, sacc);
+            }
+          } else {  // g_k + a_{k+1} - A^T a_k
+            sacc = gk[r][p] + ((r == 0) ? nxt[p] : av[r - 1][p]);
+#pragma unroll
+            for (int q2 = 0; q2 < NS; ++q2) sacc = fma(-A[q2][p], av[r][q2], sacc);
+          }
           res[p] = act[r] ? sacc : 0.0;
         }
 #pragma unroll
@@ -576,7 +628,17 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
     // ---- parameter VJP: acc += dt_k (dh/dp)^T a_k ----
 #pragma unroll
     for (int r = 0; r < RPT; ++r)
-      if (act[r] && dt[r] != 0.0) mdl.vjp_p(yk[r], av[r], dt[r], acc);
+      if (act[r] && dt[r] != 0.0) {
+        if (fwd_euler) {  // forward Euler's step k evaluates h at y_{k-1}
+          const int k = i + L - (tid * RPT + r);
+          double ykm[NS];
+#pragma unroll
+          for (int s = 0; s < NS; ++s) ykm[s] = yb[static_cast<size_t>(k - 1) * NS + s];
+          mdl.vjp_p(ykm, av[r], dt[r], acc);
+        } else {
+          mdl.vjp_p(yk[r], av[r], dt[r], acc);
+        }
+      }
     }  // wact
     // ---- carry a_{i+1} (row L-1) to the earlier chunk ----
 #pragma unroll
@@ -594,8 +656,22 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
 
   // dL/dy0 = a_1 + dL/dy_0
   if (tid == 0 && a.dy0) {
+    if (fwd_euler) {  // lambda_0 = g_0 + (I + dt_1 j(y_0))^T a_1
+      double y0v[NS], A[NS][NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) a.dy0[static_cast<size_t>(b) * NS + s] = carry[s] + gb[s];
+      for (int s = 0; s < NS; ++s) y0v[s] = yb[s];
+      mdl.step_matrix(y0v, (N >= 1 && 1 <= len) ? tb[1] - tb[0] : 0.0, A);
+#pragma unroll
+      for (int p = 0; p < NS; ++p) {
+        double v = gb[p];
+#pragma unroll
+        for (int q2 = 0; q2 < NS; ++q2) v = fma((p == q2 ? 2.0 : 0.0) - A[q2][p], carry[q2], v);
+        a.dy0[static_cast<size_t>(b) * NS + p] = v;
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) a.dy0[static_cast<size_t>(b) * NS + s] = carry[s] + gb[s];
+    }
   }
   // deterministic block sum of the parameter gradient: warp tree, then warps in order
 #pragma unroll
