@@ -96,11 +96,14 @@ typedef struct {
   double tol_rel;     /* ... or ||R||_inf <= tol_rel ||R_0||_inf (norm over the whole chunk) */
   int max_iter;       /* Newton update limit per chunk attempt */
   int precision;      /* tvi_precision */
-  int retry_halving;  /* 1: a chunk whose Newton fails (limit, non-finite, or residual
-                         still > 10x its start after 4 updates) is re-solved from the same
-                         start with half the steps, recursively down to one step; after
-                         each success the chunk doubles back up to `chunk`.  The equations
-                         solved are the same, so the result is the same. */
+  int retry_halving;  /* 1 (linear and van der Pol models): a chunk whose Newton fails
+                         (limit, non-finite, or residual still > 10x its start after 4
+                         updates) keeps its longest leading run of >= 8 steps whose
+                         residuals are within the tolerance (those steps are solved), and
+                         the rest is re-solved with half the steps, recursively down to
+                         one step; after two successes in a row the chunk doubles back up
+                         to `chunk`.  Every kept step satisfies the same equation to the
+                         same tolerance.  The MLP models do not halve. */
   int adjoint_refine; /* FP64-residual refinement sweeps of each adjoint chunk solve
                          (used when precision != FP64) */
   int rows_per_thread;/* solver tiling: steps held by one thread (0 = automatic) */
@@ -130,7 +133,8 @@ int tvi_param_count(const tvi_model* model);
 size_t tvi_workspace_bytes(const tvi_model* model, const tvi_options* opt, int B, int N);
 
 /*
- * Forward integration, chunked backward Euler with Newton (Alg. 1).
+ * Forward integration, chunked backward (or forward, opt->scheme) Euler with
+ * Newton (Alg. 1).
  *   B, N        series and steps; times has N+1 entries per series.
  *   y0          [B][n]       initial states.
  *   times       [B][N+1]     per-series time points; dt_k = t_k - t_{k-1} (Sec. 2.2).
@@ -150,11 +154,13 @@ size_t tvi_workspace_bytes(const tvi_model* model, const tvi_options* opt, int B
  * predictor_chunk steps starts from the predictor's guess instead when the
  * guess's FP64 residual infinity-norm is below that of dy = 0; after k
  * rejected guesses in a row (k <= 5) the series skips the predictor on its next
- * 2^k - 1 eligible chunks, and an accepted guess resets k.  A failed chunk is retried by halving when
- * opt->retry_halving; otherwise, or on a one-step chunk, the series' status is
- * set and its integration continues from the unconverged iterate.
+ * 2^k - 1 eligible chunks, and an accepted guess resets k.  A failed chunk is
+ * retried as opt->retry_halving describes; otherwise, or on a one-step chunk,
+ * the series' status is set and its integration continues from the
+ * unconverged iterate.
  * Returns TVI_OK, an argument error, or (sync_status = 1) TVI_ENOTCONV /
- * TVI_ENONFINITE if any series failed.
+ * TVI_ENONFINITE if any series failed, TVI_ETIMEOUT if a bounded device wait of
+ * the tensor-core path gave up.
  */
 tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, int N,
                          const double* y0, const double* times, const int* lengths,
@@ -167,9 +173,14 @@ tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, 
  *               Jacobians are recomputed from it, nothing else is kept).
  *   grad_out    [B][N+1][n]  dL/dy_k for every output, including k = 0.
  *   dparams     [B][P] or [P] output: dL/dp = sum_k dt_k (dh/dp(y_k))^T a_k, where
- *               a solves (I - dt_k j(y_k))^T a_k = a_{k+1} + dL/dy_k, a_{N+1} = 0.
+ *               a solves (I - dt_k j(y_k))^T a_k = a_{k+1} + dL/dy_k, a_{N+1} = 0
+ *               (backward Euler; forward Euler: see tvi_scheme).
  *   dy0         [B][n] output or NULL: dL/dy0 = a_1 + dL/dy_0.
- * The adjoint chunk size is opt->chunk.  Returns TVI_OK or an argument error.
+ * The adjoint chunk size is opt->chunk; opt->scheme must match the forward pass.
+ * With FP32 / BF16 blocks the chunk solves are refined opt->adjoint_refine
+ * times with FP64-assembled residuals.  Returns TVI_OK or an argument error;
+ * on the tensor-core path a bounded device wait that gave up leaves NaN in
+ * dparams and dy0.
  */
 tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, int N,
                        const double* times, const int* lengths, const double* params,
