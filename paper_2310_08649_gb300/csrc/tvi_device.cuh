@@ -14,8 +14,10 @@
 // serial substitution inside a thread, cyclic reduction across threads).
 #pragma once
 
+#ifndef __CUDACC_RTC__  // host compile (NVRTC provides the device built-ins)
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 namespace tvi {
 

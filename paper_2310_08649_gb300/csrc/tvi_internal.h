@@ -2,14 +2,12 @@
 // the kernel translation units.  Not part of the public interface.
 #pragma once
 
+#ifndef __CUDACC_RTC__  // host compile (NVRTC provides the device built-ins)
 #include <cuda_runtime.h>
 #include <stddef.h>
+#endif
 
 namespace tvi {
-
-// Host-side count of the kernels this library has enqueued (every host thread),
-// read through tvi_kernel_launches(); called right before each launch.
-void note_launch();
 
 enum { kKindLinear = 0, kKindVdp = 1, kKindMlpTanh = 2, kKindMlpSilu = 3 };
 enum { kPrecFp64 = 0, kPrecFp32 = 1, kPrecBf16 = 2 };
@@ -61,6 +59,11 @@ struct AdjArgs {
   int scheme;        // kSchemeBackward / kSchemeForward
 };
 
+#ifndef __CUDACC_RTC__
+// Host-side count of the kernels this library has enqueued (every host thread),
+// read through tvi_kernel_launches(); called right before each launch.
+void note_launch();
+
 bool small_supported(int kind, int n);
 void small_launch_shape(int chunk, int preferred, int* rpt, int* threads);
 cudaError_t small_forward(int kind, int n, int precision, int rpt, int threads, const FwdArgs& a,
@@ -80,5 +83,7 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
                         void* workspace, cudaStream_t s, int* host_worst);
 cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const AdjArgs& a,
                         void* workspace, cudaStream_t s);
+
+#endif  // __CUDACC_RTC__
 
 }  // namespace tvi

@@ -10,7 +10,9 @@
 // formed by the caller); hidden layers use SiLU, the output layer is linear.
 #pragma once
 
+#ifndef __CUDACC_RTC__  // host compile (NVRTC provides the device built-ins)
 #include <cuda_runtime.h>
+#endif
 
 namespace tvi {
 
