@@ -22,7 +22,8 @@
  *     result back to form its return code (see tvi_options.sync_status).
  *   - Errors are returned, never raised: no call aborts, traps or prints.  The
  *     text of the last error of the calling host thread is tvi_last_error().
- *   - rhs/jac are chosen by tvi_model.kind; callers do not pass functions.
+ *   - rhs/jac are chosen by tvi_model.kind: a built-in model, or a user model
+ *     whose rhs/jac are device source compiled at run time (tvi_user_model_create).
  */
 #ifndef TVI_H
 #define TVI_H
@@ -52,12 +53,16 @@ typedef enum {
  *   TVI_MODEL_MLP_SILU  h = W3 silu(W2 silu(W1 y + b1) + b2) + b3.
  * MLP parameters are one flat FP64 vector W1[h1][n] b1[h1] W2[h2][h1] b2[h2]
  * W3[n][h2] b3[n] (W row-major, out x in), shared by all series (per_series =
- * 0); n in {4, 8, 16, 32}, hidden widths <= 128 and multiples of 4. */
+ * 0); n in {4, 8, 16, 32}, hidden widths <= 128 and multiples of 4.
+ *   TVI_MODEL_USER      h, dh/dy and (dh/dp)^T a given as device source
+ *                       (tvi_user_model_create); n and P are the user model's,
+ *                       and tvi_model.user points at it. */
 typedef enum {
   TVI_MODEL_LINEAR = 0,
   TVI_MODEL_VDP = 1,
   TVI_MODEL_MLP_TANH = 2,
-  TVI_MODEL_MLP_SILU = 3
+  TVI_MODEL_MLP_SILU = 3,
+  TVI_MODEL_USER = 4
 } tvi_model_kind;
 
 /* Arithmetic of the block Jacobian, its inverse and the cyclic reduction.
@@ -82,12 +87,17 @@ typedef enum {
  * (dh/dp at y_{k-1})^T a_k, dL/dy0 = dL/dy_0 + (I + dt_1 j(y_0))^T a_1. */
 typedef enum { TVI_BACKWARD_EULER = 0, TVI_FORWARD_EULER = 1 } tvi_scheme;
 
+/* A user model compiled at run time (opaque; tvi_user_model_create). */
+typedef struct tvi_user_model tvi_user_model;
+
 typedef struct {
   int kind;        /* tvi_model_kind */
   int n;           /* state size */
   int hidden1;     /* MLP hidden widths (0 otherwise) */
   int hidden2;
   int per_series;  /* 1: params [B][P] (one vector per series); 0: one shared [P] */
+  const tvi_user_model* user;  /* TVI_MODEL_USER: the compiled model (n must be its n);
+                                  ignored for the other kinds */
 } tvi_model;
 
 typedef struct {
@@ -253,6 +263,52 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
                                     int out, int M, const float* x, const float* target,
                                     const int* rows, float lr, int step, float* loss,
                                     void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * User-defined models.  The integrator of Sec. 2.2 takes the right-hand side h
+ * and its Jacobian j = dh/dy as functions; here they are CUDA C++ device source,
+ * compiled at run time (NVRTC, sm_103a) together with the fused small-state
+ * solver kernels, so they run inlined in the same one-block-per-series kernels
+ * as the built-in linear and van der Pol models.  `source` defines, at global
+ * scope, with TVI_N (= n) and TVI_P (= P) #defined before it:
+ *
+ *   __device__ void tvi_rhs(const double* y, const double* p, double* h);
+ *       h[i] = h_i(y; p), i < n: the autonomous ODE dy/dt = h(y; p)
+ *   __device__ void tvi_jac(const double* y, const double* p, double* J);
+ *       J[i * n + j] = dh_i/dy_j: the step Jacobian of step k is I - dt_k J
+ *   __device__ void tvi_vjp_p(const double* y, const double* p, const double* a,
+ *                             double* g);
+ *       g[q] = sum_i a_i dh_i/dp_q, q < P: the adjoint's gradient integrand
+ *       (App. A.1)
+ *
+ * y and p hold n and P values, a holds n; h, J and g must be written in full.
+ * All three are evaluated in FP64 (with FP32 blocks, J is rounded to FP32 after
+ * evaluation).  The library trusts them: J must be the Jacobian of h for Newton
+ * to converge quadratically, and g its parameter product for the gradients to
+ * be those of the discrete loss.  Sizes 1 <= n <= 4 and 1 <= P <= 32; FP64 or
+ * FP32 blocks (BF16: TVI_EUNSUPPORTED); both schemes, retry_halving, per-series
+ * or shared parameters, tvi_adjoint_noalloc; no Newton predictor.  Calls on one
+ * model from several host threads are safe.  The paper has no counterpart to
+ * run-time compilation: it is how an ABI of plain pointers accepts functions.
+ */
+
+/* Check that `source` (host string, copied) compiles against the interface
+ * above and create a model.  Needs NVRTC (libnvrtc.so.13) but no GPU.
+ * TVI_EINVAL: bad sizes, or source that does not compile (compiler log in
+ * tvi_last_error); TVI_EUNSUPPORTED: NVRTC cannot be loaded.  *out is set only
+ * on TVI_OK. */
+tvi_status tvi_user_model_create(int n, int P, const char* source, tvi_user_model** out);
+
+/* Compile the solver kernels of one block precision (TVI_PREC_FP64 or
+ * TVI_PREC_FP32) for every steps-per-thread tiling now.  Otherwise a tiling is
+ * compiled (about a second) and loaded by the first tvi_integrate or
+ * tvi_adjoint that needs it; do that first call, or this one, before any stream
+ * capture.  No GPU needed. */
+tvi_status tvi_user_model_prepare(tvi_user_model* model, int precision);
+
+/* Free the model and unload its kernels, after all work using it has completed.
+ * NULL is ignored. */
+void tvi_user_model_destroy(tvi_user_model* model);
 
 /* Text of the last error on the calling host thread ("" if none). */
 const char* tvi_last_error(void);

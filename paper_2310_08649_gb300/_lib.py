@@ -11,24 +11,26 @@ import threading
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libtvi.so")
 
-MODEL_KINDS = {"linear": 0, "vdp": 1, "mlp_tanh": 2, "mlp_silu": 3}
+MODEL_KINDS = {"linear": 0, "vdp": 1, "mlp_tanh": 2, "mlp_silu": 3, "user": 4}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 SCHEMES = {"backward": 0, "forward": 1}
 STATUS = {0: "TVI_OK", -1: "TVI_EINVAL", -2: "TVI_EWORKSPACE", -3: "TVI_ECUDA",
-          -4: "TVI_ENOTCONV", -5: "TVI_ENONFINITE", -7: "TVI_EUNSUPPORTED"}
+          -4: "TVI_ENOTCONV", -5: "TVI_ENONFINITE", -6: "TVI_ETIMEOUT", -7: "TVI_EUNSUPPORTED"}
 TVI_ENOTCONV, TVI_ENONFINITE = -4, -5
 
 # every symbol include/tvi.h declares
 EXPORTS = ("tvi_default_options", "tvi_param_count", "tvi_workspace_bytes", "tvi_integrate",
            "tvi_adjoint", "tvi_adjoint_noalloc", "tvi_predictor_size", "tvi_predictor_forward",
-           "tvi_predictor_workspace_bytes", "tvi_predictor_train_step", "tvi_kernel_launches",
+           "tvi_predictor_workspace_bytes", "tvi_predictor_train_step", "tvi_user_model_create",
+           "tvi_user_model_prepare", "tvi_user_model_destroy", "tvi_kernel_launches",
            "tvi_last_error", "tvi_version")
 STATS = 6  # per-series statistics columns of tvi_integrate
 
 
 class TviModel(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("hidden1", ctypes.c_int),
-                ("hidden2", ctypes.c_int), ("per_series", ctypes.c_int)]
+                ("hidden2", ctypes.c_int), ("per_series", ctypes.c_int),
+                ("user", ctypes.c_void_p)]
 
 
 class TviOptions(ctypes.Structure):
@@ -87,6 +89,13 @@ def load():
             lib.tvi_predictor_train_step.argtypes = [vp, vp, vp, ci, ci, ci, ci, vp, vp, vp,
                                                      ctypes.c_float, ci, vp, vp, sz, vp]
             lib.tvi_predictor_train_step.restype = ci
+            lib.tvi_user_model_create.argtypes = [ci, ci, ctypes.c_char_p,
+                                                  ctypes.POINTER(ctypes.c_void_p)]
+            lib.tvi_user_model_create.restype = ci
+            lib.tvi_user_model_prepare.argtypes = [vp, ci]
+            lib.tvi_user_model_prepare.restype = ci
+            lib.tvi_user_model_destroy.argtypes = [vp]
+            lib.tvi_user_model_destroy.restype = None
             lib.tvi_kernel_launches.argtypes = []
             lib.tvi_kernel_launches.restype = ctypes.c_ulonglong
             lib.tvi_last_error.argtypes = []

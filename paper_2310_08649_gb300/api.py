@@ -15,12 +15,14 @@ from . import _lib
 
 @dataclass(frozen=True)
 class Model:
-    """kind: 'linear' | 'vdp' | 'mlp_tanh' | 'mlp_silu'; n: state size;
-    hidden: MLP hidden widths; per_series: one parameter vector per series."""
+    """kind: 'linear' | 'vdp' | 'mlp_tanh' | 'mlp_silu' | 'user'; n: state size;
+    hidden: MLP hidden widths; per_series: one parameter vector per series;
+    user: the UserModel of kind 'user' (UserModel.model() builds this)."""
     kind: str
     n: int
     hidden: tuple = (0, 0)
     per_series: bool = False
+    user: object = None
 
     @classmethod
     def from_spec(cls, spec):
@@ -31,11 +33,52 @@ class Model:
         if self.kind not in _lib.MODEL_KINDS:
             raise ValueError(f"unknown model kind {self.kind!r}")
         h = tuple(self.hidden) if self.hidden else (0, 0)
+        handle = self.user.handle if self.user is not None else None
         return _lib.TviModel(_lib.MODEL_KINDS[self.kind], self.n, h[0], h[1],
-                             int(self.per_series))
+                             int(self.per_series), handle)
 
     def param_count(self):
         return _lib.load().tvi_param_count(ctypes.byref(self.c()))
+
+
+class UserModel:
+    """A small-state model given as CUDA C++ device source (tvi_user_model_create):
+    `source` defines tvi_rhs(y, p, h), tvi_jac(y, p, J) and tvi_vjp_p(y, p, a, g)
+    over FP64 pointers, with TVI_N = n and TVI_P = P defined.  The source is
+    compile-checked here (no GPU needed); the solver kernels compile on first
+    use, or all at once with prepare(precision)."""
+
+    def __init__(self, n, P, source):
+        lib = _lib.load()
+        h = ctypes.c_void_p()
+        rc = lib.tvi_user_model_create(int(n), int(P), source.encode(), ctypes.byref(h))
+        if rc != 0:
+            raise _lib.TviError(rc, _lib.last_error())
+        self.n, self.P, self.handle = int(n), int(P), h.value
+        self._lib = lib
+
+    def prepare(self, precision="fp64"):
+        if precision not in _lib.PRECISIONS:
+            raise ValueError(f"unknown precision {precision!r}")
+        rc = self._lib.tvi_user_model_prepare(self.handle, _lib.PRECISIONS[precision])
+        if rc != 0:
+            raise _lib.TviError(rc, _lib.last_error())
+        return self
+
+    def model(self, per_series=True):
+        return Model("user", self.n, per_series=per_series, user=self)
+
+    def close(self):
+        """Unload the kernels; call after the work that uses them has completed."""
+        if self.handle:
+            self._lib.tvi_user_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 @dataclass

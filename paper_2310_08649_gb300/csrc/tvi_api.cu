@@ -53,8 +53,41 @@ bool is_mlp(const tvi_model* m) {
   return m->kind == TVI_MODEL_MLP_TANH || m->kind == TVI_MODEL_MLP_SILU;
 }
 
+// a user-model error from tvi_jit.cu: the full text (a compiler log can be long)
+tvi_status jit_fail(int kind, const std::string& text) {
+  g_last_error = text;
+  return kind == tvi::kJitNoNvrtc ? TVI_EUNSUPPORTED
+         : kind == tvi::kJitCuda  ? TVI_ECUDA
+                                  : TVI_EINVAL;
+}
+
+// fused small-state forward kernel of a built-in or user model
+tvi_status small_forward(const tvi_model* m, int precision, int rpt, int threads,
+                         const tvi::FwdArgs& a, cudaStream_t s) {
+  if (m->kind == TVI_MODEL_USER) {
+    std::string err;
+    int rc = tvi::user_forward(m->user, precision, rpt, threads, a, s, &err);
+    return rc == tvi::kJitOk ? TVI_OK : jit_fail(rc, "tvi_integrate: " + err);
+  }
+  cudaError_t e = tvi::small_forward(m->kind, m->n, precision, rpt, threads, a, s);
+  return e == cudaSuccess ? TVI_OK : cuda_fail(e, "tvi_integrate: kernel launch");
+}
+
+tvi_status small_adjoint(const tvi_model* m, int precision, int rpt, int threads,
+                         const tvi::AdjArgs& a, int P, cudaStream_t s, const char* who) {
+  if (m->kind == TVI_MODEL_USER) {
+    std::string err;
+    int rc = tvi::user_adjoint(m->user, precision, rpt, threads, a, s, &err);
+    return rc == tvi::kJitOk ? TVI_OK : jit_fail(rc, std::string(who) + ": " + err);
+  }
+  cudaError_t e = tvi::small_adjoint(m->kind, m->n, precision, rpt, threads, a, P, s);
+  return e == cudaSuccess ? TVI_OK : cuda_fail(e, who);
+}
+
 tvi_status check_model(const tvi_model* m) {
   if (!m) return fail(TVI_EINVAL, "model is NULL");
+  if (m->kind == TVI_MODEL_USER && (!tvi::user_valid(m->user) || m->n != tvi::user_n(m->user)))
+    return fail(TVI_EINVAL, "user model: tvi_model.user must be a live model of n = %d", m->n);
   if (tvi_param_count(m) < 0)
     return fail(TVI_EINVAL, "bad model (kind %d, n %d, hidden %d/%d)", m->kind, m->n, m->hidden1,
                 m->hidden2);
@@ -68,6 +101,7 @@ tvi_status check_model(const tvi_model* m) {
                   m->n, m->hidden1, m->hidden2);
     return TVI_OK;
   }
+  if (m->kind == TVI_MODEL_USER) return TVI_OK;  // sizes fixed at creation
   if (!tvi::small_supported(m->kind, m->n))
     return fail(TVI_EUNSUPPORTED, "model kind %d with n = %d is not built", m->kind, m->n);
   return TVI_OK;
@@ -79,6 +113,8 @@ tvi_status check_precision(const tvi_model* m, const tvi_options* o) {
     return fail(TVI_EUNSUPPORTED,
                 "forward Euler is built for the linear and van der Pol models, without a "
                 "predictor");
+  if (m->kind == TVI_MODEL_USER && o->precision == tvi::kPrecBf16)
+    return fail(TVI_EUNSUPPORTED, "user models run with FP64 or FP32 blocks");
   if (o->precision != tvi::kPrecBf16) return TVI_OK;
   if (!is_mlp(m) || !tvi::mlp_tc_supported(m->n, m->hidden1, m->hidden2))
     return fail(TVI_EUNSUPPORTED,
@@ -151,6 +187,9 @@ int tvi_param_count(const tvi_model* m) {
       if (m->hidden1 <= 0 || m->hidden2 <= 0) return -1;
       return m->hidden1 * m->n + m->hidden1 + m->hidden2 * m->hidden1 + m->hidden2 +
              m->n * m->hidden2 + m->n;
+    case TVI_MODEL_USER:
+      if (!tvi::user_valid(m->user) || m->n != tvi::user_n(m->user)) return -1;
+      return tvi::user_P(m->user);
     default: return -1;
   }
 }
@@ -231,8 +270,7 @@ tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, 
   tvi::small_launch_shape(a.chunk, opt->rows_per_thread, &rpt, &threads);
   // the predictor's layers are latency-bound GEMVs: give them every warp the block can hold
   if (a.pred) threads = tvi::small_max_threads(rpt);
-  e = tvi::small_forward(model->kind, model->n, opt->precision, rpt, threads, a, s);
-  if (e != cudaSuccess) return cuda_fail(e, "tvi_integrate: kernel launch");
+  if ((r = small_forward(model, opt->precision, rpt, threads, a, s)) != TVI_OK) return r;
   if (!opt->sync_status) return TVI_OK;
   int worst = 0;
   e = cudaMemcpyAsync(&worst, a.worst, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -299,10 +337,34 @@ tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, in
   }
   int rpt, threads;
   tvi::small_launch_shape(a.chunk, opt->rows_per_thread, &rpt, &threads);
-  cudaError_t e = tvi::small_adjoint(model->kind, model->n, opt->precision, rpt, threads, a, P, s);
-  if (e != cudaSuccess) return cuda_fail(e, "tvi_adjoint: kernel launch");
+  return small_adjoint(model, opt->precision, rpt, threads, a, P, s, "tvi_adjoint: kernel launch");
+}
+
+tvi_status tvi_user_model_create(int n, int P, const char* source, tvi_user_model** out) {
+  g_last_error.clear();
+  if (!out || !source) return fail(TVI_EINVAL, "tvi_user_model_create: NULL source or out");
+  if (n < 1 || n > tvi::kUserMaxN || P < 1 || P > tvi::kUserMaxP)
+    return fail(TVI_EINVAL, "user models take 1 <= n <= %d and 1 <= P <= %d (got n %d, P %d)",
+                tvi::kUserMaxN, tvi::kUserMaxP, n, P);
+  std::string err;
+  tvi_user_model* m = nullptr;
+  int rc = tvi::user_create(n, P, source, &m, &err);
+  if (rc != tvi::kJitOk) return jit_fail(rc, "tvi_user_model_create: " + err);
+  *out = m;
   return TVI_OK;
 }
+
+tvi_status tvi_user_model_prepare(tvi_user_model* model, int precision) {
+  g_last_error.clear();
+  if (!tvi::user_valid(model)) return fail(TVI_EINVAL, "tvi_user_model_prepare: not a live model");
+  if (precision != TVI_PREC_FP64 && precision != TVI_PREC_FP32)
+    return fail(TVI_EUNSUPPORTED, "user models run with FP64 or FP32 blocks (got %d)", precision);
+  std::string err;
+  int rc = tvi::user_prepare(model, precision, &err);
+  return rc == tvi::kJitOk ? TVI_OK : jit_fail(rc, "tvi_user_model_prepare: " + err);
+}
+
+void tvi_user_model_destroy(tvi_user_model* model) { tvi::user_destroy(model); }
 
 const char* tvi_last_error(void) { return g_last_error.c_str(); }
 
@@ -424,7 +486,6 @@ extern "C" tvi_status tvi_adjoint_noalloc(const tvi_model* model, const tvi_opti
   }
   int rpt, threads;
   tvi::small_launch_shape(a.chunk, opt->rows_per_thread, &rpt, &threads);
-  cudaError_t e = tvi::small_adjoint(model->kind, model->n, opt->precision, rpt, threads, a, P, s);
-  if (e != cudaSuccess) return cuda_fail(e, "tvi_adjoint_noalloc: kernel launch");
-  return TVI_OK;
+  return small_adjoint(model, opt->precision, rpt, threads, a, P, s,
+                       "tvi_adjoint_noalloc: kernel launch");
 }

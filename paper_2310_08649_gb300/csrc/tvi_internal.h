@@ -5,11 +5,15 @@
 #ifndef __CUDACC_RTC__  // host compile (NVRTC provides the device built-ins)
 #include <cuda_runtime.h>
 #include <stddef.h>
+
+#include <string>
+
+struct tvi_user_model;  // a run-time compiled user model (tvi_jit.cu)
 #endif
 
 namespace tvi {
 
-enum { kKindLinear = 0, kKindVdp = 1, kKindMlpTanh = 2, kKindMlpSilu = 3 };
+enum { kKindLinear = 0, kKindVdp = 1, kKindMlpTanh = 2, kKindMlpSilu = 3, kKindUser = 4 };
 enum { kPrecFp64 = 0, kPrecFp32 = 1, kPrecBf16 = 2 };
 // integration schemes (Sec. 2.2): backward Euler, forward Euler
 enum { kSchemeBackward = 0, kSchemeForward = 1 };
@@ -70,6 +74,25 @@ cudaError_t small_forward(int kind, int n, int precision, int rpt, int threads, 
                           cudaStream_t s);
 cudaError_t small_adjoint(int kind, int n, int precision, int rpt, int threads, const AdjArgs& a,
                           int P, cudaStream_t s);
+// dparams = sum over series of the per-series partials (shared parameters)
+cudaError_t small_sum_partials(const AdjArgs& a, int P, cudaStream_t s);
+
+// User models (tvi_jit.cu): the small-state kernels compiled at run time with
+// the caller's right-hand side.  Return kJitOk or an error kind, with the text
+// (the compiler log for kJitCompile) in *err.
+enum { kJitOk = 0, kJitNoNvrtc = 1, kJitCompile = 2, kJitCuda = 3 };
+constexpr int kUserMaxN = 4;
+constexpr int kUserMaxP = 32;
+bool user_valid(const tvi_user_model* m);
+int user_n(const tvi_user_model* m);
+int user_P(const tvi_user_model* m);
+int user_create(int n, int P, const char* source, tvi_user_model** out, std::string* err);
+void user_destroy(tvi_user_model* m);
+int user_prepare(tvi_user_model* m, int precision, std::string* err);
+int user_forward(const tvi_user_model* m, int precision, int rpt, int threads, const FwdArgs& a,
+                 cudaStream_t s, std::string* err);
+int user_adjoint(const tvi_user_model* m, int precision, int rpt, int threads, const AdjArgs& a,
+                 cudaStream_t s, std::string* err);
 
 // Neural-ODE (MLP right-hand side) path: shared parameters, n <= 32 and hidden
 // widths <= 128, all multiples of 4.  The chunk in the argument blocks is the

@@ -125,12 +125,13 @@ cudaError_t small_adjoint(int kind, int n, int precision, int rpt, int threads, 
     e = f64 ? dispatch_adj_rpt<ModelLinear<4>, double>(a, rpt, threads, s)
             : dispatch_adj_rpt<ModelLinear<4>, float>(a, rpt, threads, s);
   if (e != cudaSuccess) return e;
-  if (!a.per_series) {
-    note_launch();
-    sum_partials_kernel<<<(P + 127) / 128, 128, 0, s>>>(a.partials, a.B, P, a.dparams);
-    e = cudaGetLastError();
-  }
-  return e;
+  return a.per_series ? cudaSuccess : small_sum_partials(a, P, s);
+}
+
+cudaError_t small_sum_partials(const AdjArgs& a, int P, cudaStream_t s) {
+  note_launch();
+  sum_partials_kernel<<<(P + 127) / 128, 128, 0, s>>>(a.partials, a.B, P, a.dparams);
+  return cudaGetLastError();
 }
 
 }  // namespace tvi

@@ -1,0 +1,96 @@
+"""User models compiled at run time (tvi_user_model_create / _prepare /
+_destroy), on the host: NVRTC compiles the user's functions together with the
+fused solver kernels for sm_103a without a GPU, so the interface checks, the
+compiler-log reporting and the full kernel compile are tested here."""
+import ctypes
+
+import pytest
+
+from user_sources import LINEAR, VDP, mlp_param_count, mlp_tanh
+
+tvi = pytest.importorskip("paper_2310_08649_gb300")
+from paper_2310_08649_gb300 import _lib  # noqa: E402
+
+EINVAL, EUNSUPPORTED = -1, -7
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2310_08649_gb300 import build
+    build.build()
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    rc = lib.tvi_user_model_create(2, 1, VDP.encode(), ctypes.byref(h))
+    if rc == EUNSUPPORTED and "could not be loaded" in _lib.last_error():
+        pytest.skip("NVRTC is not available: " + _lib.last_error())
+    assert rc == 0, _lib.last_error()
+    lib.tvi_user_model_destroy(h)
+    return lib
+
+
+def create(lib, n, P, src):
+    h = ctypes.c_void_p()
+    rc = lib.tvi_user_model_create(n, P, src.encode() if src is not None else None,
+                                   ctypes.byref(h))
+    return rc, h
+
+
+def test_create_and_param_count(lib):
+    u = tvi.UserModel(2, 1, VDP)
+    assert u.model().param_count() == 1
+    m = _lib.TviModel(4, 3, 0, 0, 1, u.handle)  # n differs from the user model's
+    assert lib.tvi_param_count(ctypes.byref(m)) == -1
+    m = _lib.TviModel(4, 2, 0, 0, 1, None)      # no user model
+    assert lib.tvi_param_count(ctypes.byref(m)) == -1
+    u.close()
+    assert u.handle is None
+
+
+def test_compile_error_reports_the_users_line(lib):
+    bad = VDP.replace("h[0] = y[1];", "h[0] = undefined_name;")  # line 4 of the source
+    rc, _ = create(lib, 2, 1, bad)
+    assert rc == EINVAL
+    msg = _lib.last_error()
+    assert "does not compile" in msg and "user_model.cu(4)" in msg, msg
+    assert "undefined_name" in msg
+
+
+def test_missing_function_is_rejected(lib):
+    no_vjp = VDP[:VDP.index("__device__ void tvi_vjp_p")]
+    rc, _ = create(lib, 2, 1, no_vjp)
+    assert rc == EINVAL and "tvi_vjp_p" in _lib.last_error()
+
+
+@pytest.mark.parametrize("n,P", [(0, 1), (5, 1), (2, 0), (2, 33), (-1, -1)])
+def test_bad_sizes(lib, n, P):
+    rc, h = create(lib, n, P, VDP)
+    assert rc == EINVAL and h.value is None
+
+
+def test_null_arguments(lib):
+    rc, _ = create(lib, 2, 1, None)
+    assert rc == EINVAL
+    assert lib.tvi_user_model_create(2, 1, VDP.encode(), None) == EINVAL
+    assert lib.tvi_user_model_prepare(None, 0) == EINVAL
+    lib.tvi_user_model_destroy(None)  # ignored
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_prepare_compiles_every_tiling(lib, precision):
+    """Every steps-per-thread tiling of the forward and adjoint kernels compiles
+    for a nonlinear model with shared MLP parameters (n = 3, P = 23) and for a
+    linear model of the largest state size (n = 4, P = 16)."""
+    u = tvi.UserModel(3, mlp_param_count(3, 2, 2), mlp_tanh(2, 2))
+    u.prepare(precision)
+    u.close()
+    v = tvi.UserModel(4, 16, LINEAR)
+    v.prepare(precision)
+    v.close()
+
+
+def test_prepare_rejects_bf16(lib):
+    u = tvi.UserModel(1, 1, LINEAR)
+    with pytest.raises(_lib.TviError) as e:
+        u.prepare("bf16")
+    assert e.value.code == EUNSUPPORTED
+    u.close()
