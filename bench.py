@@ -46,6 +46,9 @@ WORKLOADS = {
     "vdp": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 128, "N": 10000, "refine": 1},
     "vdp_pred": {"chunk": 100, "precision": "fp32", "tol": 1e-8, "B": 128, "N": 10000,
                  "refine": 1},
+    # the same van der Pol workload through a user model (device source compiled at run time)
+    "vdp_user": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 128, "N": 10000,
+                 "refine": 1},
     "node16": {"chunk": 200, "precision": "bf16", "tol": 1e-8, "B": 64, "N": 2000, "refine": 2},
     "node32": {"chunk": 1000, "precision": "bf16", "tol": 1e-8, "B": 512, "N": 20000,
                "refine": 2},
@@ -91,7 +94,7 @@ def dist_env():
 
 def make_workload(args, rank=0):
     """(inputs, dL/dy) for the chosen workload; ranks draw their own batches."""
-    if args.workload == "vdp":
+    if args.workload in ("vdp", "vdp_user"):
         w = workloads.vdp(B=args.B, N=args.N, seed=workloads.SEED_VDP + 1000 * rank)
     elif args.workload == "vdp_pred":
         w = workloads.vdp(B=args.B, N=args.N, seed=PRED_EVAL_SEED + rank)
@@ -131,6 +134,8 @@ def workload_config(args):
     desc = {"vdp": "van der Pol n=2, mu log-uniform [10,1000], log-spaced steps",
             "vdp_pred": "van der Pol n=2 (held-out seed) with the learned Newton predictor "
                         "(MLP 103-256-256-200)",
+            "vdp_user": "van der Pol n=2 as a user model (device source compiled at run time), "
+                        "mu log-uniform [10,1000], log-spaced steps",
             "node16": "neural ODE n=16, MLP 16-64-64-16 tanh, uniform steps on [0,10]",
             "node32": "neural ODE n=32, MLP 32-128-128-32 SiLU, per-series lengths "
                       "U[2000,N] padded, uniform steps on [0,10]"}[args.workload]
@@ -292,7 +297,9 @@ def roofline(args, w, stats, fwd_ms, adj_ms, refine):
         fwd_ops = float(np.sum(((upd + nchk) * 7.0 + upd * 2.0) * spc))
         # adjoint per step: per refinement sweep 14, parameter VJP 4
         adj_ops = float(B * N * (refine * 14.0 + 4.0))
-        names = ("forward_small_kernel<vdp,fp32>", "adjoint_small_kernel<vdp,fp32>")
+        mdl = "TviUserModel" if args.workload == "vdp_user" else "vdp"
+        names = (f"forward_small_kernel<{mdl},{args.precision}>",
+                 f"adjoint_small_kernel<{mdl},{args.precision}>")
     else:
         n, (h1, h2) = w["spec"]["n"], w["spec"]["hidden"]
         fma = n * h1 + h1 * h2 + h2 * n  # FMAs of one MLP evaluation (activations not counted)
@@ -350,6 +357,10 @@ def run_ours(args):
     y0, times, params, grad = d(w["y0"]), d(w["times"]), d(w["params"]), d(g)
     lengths = None if w["lengths"] is None else d(w["lengths"], torch.int32)
     model = tvi.Model.from_spec(w["spec"])
+    if args.workload == "vdp_user":
+        from paper_2310_08649_gb300.user_sources import VDP
+        user = tvi.UserModel(2, 1, VDP).prepare(args.precision)  # compiled before timing
+        model = user.model(per_series=True)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 

@@ -282,8 +282,11 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
  *       (App. A.1)
  *
  * y and p hold n and P values, a holds n; h, J and g must be written in full.
- * All three are evaluated in FP64 (with FP32 blocks, J is rounded to FP32 after
- * evaluation).  The library trusts them: J must be the Jacobian of h for Newton
+ * tvi_rhs and tvi_vjp_p are evaluated in FP64.  tvi_jac may instead be a
+ * template over the element type of y and J,
+ *   template <typename T> __device__ void tvi_jac(const T* y, const double* p, T* J);
+ * and is then evaluated in the block type (FP32 with FP32 blocks, as for the
+ * built-in models); a plain FP64 tvi_jac is evaluated in FP64 and rounded.  The library trusts them: J must be the Jacobian of h for Newton
  * to converge quadratically, and g its parameter product for the gradients to
  * be those of the discrete loss.  Sizes 1 <= n <= 4 and 1 <= P <= 32; FP64 or
  * FP32 blocks (BF16: TVI_EUNSUPPORTED); both schemes, retry_halving, per-series

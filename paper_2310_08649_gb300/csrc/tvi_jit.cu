@@ -120,6 +120,17 @@ const Nvrtc& nvrtc() {
 // that adapts them to the kernels' model interface.
 // ---------------------------------------------------------------------------
 const char* const kAdapter = R"tvi_src(
+// true when tvi_jac accepts element type T for y and J (a template over T)
+template <class...> struct TviVoid { typedef void type; };
+template <class T> T&& tvi_declval();
+template <class T, class = void> struct TviTypedJac { static constexpr bool value = false; };
+template <class T>
+struct TviTypedJac<T, typename TviVoid<decltype(tvi_jac(tvi_declval<const T*>(),
+                                                        tvi_declval<const double*>(),
+                                                        tvi_declval<T*>()))>::type> {
+  static constexpr bool value = true;
+};
+
 struct TviUserModel {
   static constexpr int NS = TVI_N;
   static constexpr int NP = TVI_P;
@@ -135,18 +146,28 @@ struct TviUserModel {
   __device__ __forceinline__ void rhs(const double (&y)[NS], double (&h)[NS]) const {
     tvi_rhs(y, p, h);
   }
-  // A = I - dt J with J = dh/dy evaluated in FP64, then rounded to the block type
+  // A = I - dt J, J = dh/dy evaluated in the block type T when tvi_jac is a
+  // template over it, else in FP64 and rounded to T (integer-pipe conversions)
   template <typename T>
   __device__ __forceinline__ void step_matrix(const T (&y)[NS], T dt, T (&A)[NS][NS]) const {
-    double yd[NS], J[NS * NS];
+    if constexpr (TviTypedJac<T>::value) {
+      T J[NS * NS];
+      tvi_jac(y, p, J);
 #pragma unroll
-    for (int s = 0; s < NS; ++s) yd[s] = static_cast<double>(y[s]);
-    tvi_jac(yd, p, J);
+      for (int r = 0; r < NS; ++r)
 #pragma unroll
-    for (int r = 0; r < NS; ++r)
+        for (int c = 0; c < NS; ++c) A[r][c] = fma(-dt, J[r * NS + c], r == c ? T(1) : T(0));
+    } else {
+      double yd[NS], J[NS * NS];
 #pragma unroll
-      for (int c = 0; c < NS; ++c)
-        A[r][c] = fma(-dt, static_cast<T>(J[r * NS + c]), r == c ? T(1) : T(0));
+      for (int s = 0; s < NS; ++s) yd[s] = tvi::widen(y[s]);
+      tvi_jac(yd, p, J);
+#pragma unroll
+      for (int r = 0; r < NS; ++r)
+#pragma unroll
+        for (int c = 0; c < NS; ++c)
+          A[r][c] = fma(-dt, tvi::narrow<T>(J[r * NS + c]), r == c ? T(1) : T(0));
+    }
   }
   // acc += scale (dh/dp)^T a
   __device__ __forceinline__ void vjp_p(const double (&y)[NS], const double (&a)[NS],

@@ -1,7 +1,16 @@
-"""Device source of user models (tvi_user_model_create) written the way a user
-would: van der Pol, a linear system of any size, and a small tanh MLP.  Each
-matches one of the oracle's built-in models, so the run-time compiled kernels
-can be checked against the oracle."""
+"""Example user models: CUDA C++ device source for tvi_user_model_create
+(UserModel), each defining tvi_rhs, tvi_jac and tvi_vjp_p over FP64 pointers.
+
+    VDP          van der Pol, h = [y2, mu (1 - y1^2) y2 - y1], p = [mu]   (n 2, P 1)
+                 (tvi_jac a template: FP32 Jacobians with FP32 blocks)
+    VDP_FP64_JAC the same with an FP64 tvi_jac
+    LINEAR       h = A y, p = A row-major                                (any n, P n^2)
+    mlp_tanh()   h = tanh(W3 tanh(W2 tanh(W1 y + b1) + b2) + b3)         (any n)
+
+    import paper_2310_08649_gb300 as tvi
+    from paper_2310_08649_gb300.user_sources import VDP
+    model = tvi.UserModel(2, 1, VDP).model(per_series=True)
+"""
 
 VDP = r"""
 // van der Pol: h = [y2, mu (1 - y1^2) y2 - y1], p = [mu]
@@ -9,16 +18,28 @@ __device__ void tvi_rhs(const double* y, const double* p, double* h) {
   h[0] = y[1];
   h[1] = p[0] * (1.0 - y[0] * y[0]) * y[1] - y[0];
 }
-__device__ void tvi_jac(const double* y, const double* p, double* J) {
-  J[0] = 0.0;
-  J[1] = 1.0;
-  J[2] = -2.0 * p[0] * y[0] * y[1] - 1.0;
-  J[3] = p[0] * (1.0 - y[0] * y[0]);
+// the Jacobian as a template: evaluated in FP32 with FP32 blocks
+template <typename T>
+__device__ void tvi_jac(const T* y, const double* p, T* J) {
+  const T mu = static_cast<T>(p[0]);
+  J[0] = T(0);
+  J[1] = T(1);
+  J[2] = -T(2) * mu * y[0] * y[1] - T(1);
+  J[3] = mu * (T(1) - y[0] * y[0]);
 }
 __device__ void tvi_vjp_p(const double* y, const double* p, const double* a, double* g) {
   g[0] = a[1] * (1.0 - y[0] * y[0]) * y[1];
 }
 """
+
+# van der Pol with a plain FP64 Jacobian (rounded to the block type after evaluation)
+VDP_FP64_JAC = VDP[:VDP.index("// the Jacobian as a template")] + r"""__device__ void tvi_jac(const double* y, const double* p, double* J) {
+  J[0] = 0.0;
+  J[1] = 1.0;
+  J[2] = -2.0 * p[0] * y[0] * y[1] - 1.0;
+  J[3] = p[0] * (1.0 - y[0] * y[0]);
+}
+""" + VDP[VDP.index("__device__ void tvi_vjp_p"):]
 
 LINEAR = r"""
 // h = A y with A = p as a row-major TVI_N x TVI_N matrix

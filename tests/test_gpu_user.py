@@ -16,7 +16,8 @@ import pytest
 import workloads
 from oracle import Model as OModel
 from test_gpu_euler import fe_error_estimate
-from user_sources import LINEAR, VDP, mlp_param_count, mlp_tanh
+from paper_2310_08649_gb300.user_sources import LINEAR, VDP, VDP_FP64_JAC, mlp_param_count, \
+    mlp_tanh
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -36,7 +37,8 @@ def tvi():
 
 @pytest.fixture(scope="module")
 def users(tvi):
-    made = {"vdp": tvi.UserModel(2, 1, VDP), "lin1": tvi.UserModel(1, 1, LINEAR),
+    made = {"vdp": tvi.UserModel(2, 1, VDP), "vdp64": tvi.UserModel(2, 1, VDP_FP64_JAC),
+            "lin1": tvi.UserModel(1, 1, LINEAR),
             "lin3": tvi.UserModel(3, 9, LINEAR),
             "mlp3": tvi.UserModel(3, mlp_param_count(3, 2, 2), mlp_tanh(2, 2))}
     yield made
@@ -72,9 +74,10 @@ def adjoint(tvi, model, w, o, y, g, lengths=None):
     return dp.cpu().numpy(), dy0.cpu().numpy()
 
 
+@pytest.mark.parametrize("jac", ["vdp", "vdp64"])  # Jacobian in the block type / in FP64
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("chunk", [1000, 64, 1])
-def test_user_vdp_matches_oracle(tvi, users, oracle_lib, precision, chunk):
+def test_user_vdp_matches_oracle(tvi, users, oracle_lib, precision, chunk, jac):
     w = workloads.vdp(B=32, N=3000, seed=61)
     m = OModel.from_spec(w["spec"])
     tol = 1e-10
@@ -82,7 +85,7 @@ def test_user_vdp_matches_oracle(tvi, users, oracle_lib, precision, chunk):
                                     max_iter=100)
     assert not st.any()
     est = oracle_lib.forward_error_estimate(m, w["times"], w["params"], ref, tol)
-    model = users["vdp"].model(per_series=True)
+    model = users[jac].model(per_series=True)
     o = tvi.Options(chunk=chunk, tol_abs=tol, precision=precision, adjoint_refine=2)
     y, stats, status, rc = forward(tvi, model, w, o)
     assert rc == 0 and not status.any()

@@ -6,7 +6,8 @@ import ctypes
 
 import pytest
 
-from user_sources import LINEAR, VDP, mlp_param_count, mlp_tanh
+from paper_2310_08649_gb300.user_sources import LINEAR, VDP, VDP_FP64_JAC, mlp_param_count, \
+    mlp_tanh
 
 tvi = pytest.importorskip("paper_2310_08649_gb300")
 from paper_2310_08649_gb300 import _lib  # noqa: E402
@@ -86,6 +87,14 @@ def test_prepare_compiles_every_tiling(lib, precision):
     v = tvi.UserModel(4, 16, LINEAR)
     v.prepare(precision)
     v.close()
+
+
+@pytest.mark.parametrize("src", [VDP, VDP_FP64_JAC], ids=["template_jac", "fp64_jac"])
+def test_prepare_both_jacobian_forms(lib, src):
+    """tvi_jac as a template over the block type, or as a plain FP64 function."""
+    u = tvi.UserModel(2, 1, src)
+    u.prepare("fp32")
+    u.close()
 
 
 def test_prepare_rejects_bf16(lib):
