@@ -26,6 +26,7 @@ int tvo_param_count(const tvo_model* m) {
   switch (m->kind) {
     case TVO_LINEAR: return m->n * m->n;
     case TVO_VDP: return m->n == 2 ? 1 : -1;
+    case TVO_MDS: return m->n % 2 == 0 ? 3 * (m->n / 2) + 2 : -1;
     case TVO_MLP_TANH:
     case TVO_MLP_SILU:
       if (m->h1 <= 0 || m->h2 <= 0) return -1;
@@ -99,10 +100,31 @@ static double out_d(const tvo_model* m, double z3) {
   return 1.0; /* SiLU network: linear output layer */
 }
 
+/* Mass-damper-spring chain: force F_i of spring and damper i (mass i to mass
+ * i+1, the fixed wall for i = u), with F_0 = 0 at the free end. */
+static double mds_force(int u, const double* p, const double* y, int i) {
+  if (i < 0) return 0.0;
+  const double* K = p;
+  const double* C = p + u;
+  double dn = (i + 1 < u) ? y[i + 1] : 0.0;
+  double vn = (i + 1 < u) ? y[u + i + 1] : 0.0;
+  return K[i] * (dn - y[i]) + C[i] * (vn - y[u + i]);
+}
+
+static const double kTwoPi = 6.283185307179586476925286766559;
+
 void tvo_rhs(const tvo_model* m, const double* p, const double* y, double t, double* h) {
-  (void)t; /* all models here are autonomous */
   int n = m->n;
-  if (m->kind == TVO_LINEAR) {
+  if (m->kind == TVO_MDS) {
+    int u = n / 2;
+    const double* M = p + 2 * u;
+    double fa = p[3 * u], T = p[3 * u + 1];
+    for (int i = 0; i < u; ++i) {
+      h[i] = y[u + i];
+      h[u + i] = (mds_force(u, p, y, i) - mds_force(u, p, y, i - 1)) / M[i];
+    }
+    h[u] += fa * sin(kTwoPi * t / T);
+  } else if (m->kind == TVO_LINEAR) {
     for (int r = 0; r < n; ++r) {
       double s = 0.0;
       for (int c = 0; c < n; ++c) s += p[r * n + c] * y[c];
@@ -123,7 +145,30 @@ void tvo_rhs(const tvo_model* m, const double* p, const double* y, double t, dou
 void tvo_jac(const tvo_model* m, const double* p, const double* y, double t, double* j) {
   (void)t;
   int n = m->n;
-  if (m->kind == TVO_LINEAR) {
+  if (m->kind == TVO_MDS) {
+    /* h is linear in y: column c of j is h(e_c) without the forcing */
+    int u = n / 2;
+    const double *K = p, *C = p + u, *M = p + 2 * u;
+    memset(j, 0, sizeof(double) * n * n);
+    for (int i = 0; i < u; ++i) {
+      j[i * n + u + i] = 1.0;           /* d_i' = v_i */
+      double* row = j + (u + i) * n;    /* v_i' */
+      /* + F_i / M_i */
+      row[i] -= K[i] / M[i];
+      row[u + i] -= C[i] / M[i];
+      if (i + 1 < u) {
+        row[i + 1] += K[i] / M[i];
+        row[u + i + 1] += C[i] / M[i];
+      }
+      /* - F_{i-1} / M_i, F_{i-1} = K_{i-1} (d_i - d_{i-1}) + C_{i-1} (v_i - v_{i-1}) */
+      if (i > 0) {
+        row[i] -= K[i - 1] / M[i];
+        row[i - 1] += K[i - 1] / M[i];
+        row[u + i] -= C[i - 1] / M[i];
+        row[u + i - 1] += C[i - 1] / M[i];
+      }
+    }
+  } else if (m->kind == TVO_LINEAR) {
     memcpy(j, p, sizeof(double) * n * n);
   } else if (m->kind == TVO_VDP) {
     double mu = p[0];
@@ -159,9 +204,27 @@ void tvo_jac(const tvo_model* m, const double* p, const double* y, double t, dou
 
 void tvo_vjp_p(const tvo_model* m, const double* p, const double* y, double t, const double* a,
                double scale, double* gp) {
-  (void)t;
   int n = m->n;
-  if (m->kind == TVO_LINEAR) {
+  if (m->kind == TVO_MDS) {
+    /* v_i' = (F_i - F_{i-1}) / M_i: F_i enters v_i' with +1/M_i and v_{i+1}' with
+     * -1/M_{i+1}; F_i is linear in K_i and C_i. */
+    int u = n / 2;
+    const double* M = p + 2 * u;
+    double fa = p[3 * u], T = p[3 * u + 1];
+    const double* av = a + u;
+    for (int i = 0; i < u; ++i) {
+      double dn = (i + 1 < u) ? y[i + 1] : 0.0;
+      double vn = (i + 1 < u) ? y[u + i + 1] : 0.0;
+      double w = av[i] / M[i] - ((i + 1 < u) ? av[i + 1] / M[i + 1] : 0.0);
+      gp[i] += scale * w * (dn - y[i]);          /* dK_i */
+      gp[u + i] += scale * w * (vn - y[u + i]);  /* dC_i */
+      double Fnet = mds_force(u, p, y, i) - mds_force(u, p, y, i - 1);
+      gp[2 * u + i] += scale * av[i] * (-Fnet / (M[i] * M[i]));  /* dM_i */
+    }
+    double ph = kTwoPi * t / T;
+    gp[3 * u] += scale * av[0] * sin(ph);                              /* df_a */
+    gp[3 * u + 1] += scale * av[0] * fa * cos(ph) * (-ph / T);         /* dT */
+  } else if (m->kind == TVO_LINEAR) {
     /* h_r = sum_c A_rc y_c  =>  dh_r/dA_rc = y_c, so (dh/dA)^T a = a y^T. */
     for (int r = 0; r < n; ++r)
       for (int c = 0; c < n; ++c) gp[r * n + c] += scale * a[r] * y[c];

@@ -27,6 +27,14 @@
  *   TVO_MLP_TANH  h = tanh(W3 tanh(W2 tanh(W1 y + b1) + b2) + b3)
  *                 (the neural ODE of Sec. 5.1.1 without the forcing input)
  *   TVO_MLP_SILU  h = W3 silu(W2 silu(W1 y + b1) + b2) + b3
+ *   TVO_MDS       mass-damper-spring chain of u = n/2 units (Sec. 5.1.1, Table
+ *                 mass-params), y = [d_1..d_u, v_1..v_u],
+ *                 p = [K_1..K_u, C_1..C_u, M_1..M_u, f_a, T]  (P = 3u + 2):
+ *                   d_i' = v_i
+ *                   v_i' = (F_i - F_{i-1}) / M_i + [i = 1] f_a sin(2 pi t / T)
+ *                   F_i  = K_i (d_{i+1} - d_i) + C_i (v_{i+1} - v_i),
+ *                 F_0 = 0 (free end, where the force acts) and d_{u+1} = v_{u+1} = 0
+ *                 (the fixed end): spring and damper i join mass i to mass i+1.
  * MLP parameter layout (flat, FP64): W1[h1][n] b1[h1] W2[h2][h1] b2[h2]
  * W3[n][h2] b3[n]; W are row-major (out x in).
  *
@@ -43,11 +51,11 @@
 extern "C" {
 #endif
 
-enum { TVO_LINEAR = 0, TVO_VDP = 1, TVO_MLP_TANH = 2, TVO_MLP_SILU = 3 };
+enum { TVO_LINEAR = 0, TVO_VDP = 1, TVO_MLP_TANH = 2, TVO_MLP_SILU = 3, TVO_MDS = 4 };
 enum { TVO_OK = 0, TVO_NOT_CONVERGED = 1, TVO_NONFINITE = 2, TVO_SINGULAR = 3, TVO_BADARG = -1 };
 
 typedef struct {
-  int kind;        /* TVO_LINEAR / TVO_VDP / TVO_MLP_TANH / TVO_MLP_SILU */
+  int kind;        /* TVO_LINEAR / TVO_VDP / TVO_MLP_TANH / TVO_MLP_SILU / TVO_MDS */
   int n;           /* state size */
   int h1, h2;      /* MLP hidden widths (ignored otherwise) */
   int per_series;  /* 1: params [B][P]; 0: one shared parameter vector [P] */

@@ -19,10 +19,13 @@ Default sizes are the paper-shaped workloads:
   mlp_ode       neural ODE n=16, MLP 16-64-64-16 tanh, 64 series, 2000 steps on [0, 10]
   mlp_large     neural ODE n=32, MLP 32-128-128-32 SiLU, 512 series, 20,000 padded
                 steps with per-series lengths uniform in [2000, 20000]
+  mds           mass-damper-spring chain (n = 2 n_unit), the parameter table of the
+                paper's timing study, 100 series, 2000 uniform steps on [0, 1]
 """
 import numpy as np
 
 SEED_LINEAR, SEED_VDP, SEED_MLP, SEED_PREDICTOR, SEED_MLP_LARGE = 1001, 1002, 1003, 1004, 1005
+SEED_MDS = 1006
 
 
 def _rng(seed):
@@ -112,6 +115,26 @@ def mlp_large(seed=SEED_MLP_LARGE, B=512, N=20000, n=32, hidden=(128, 128), t_en
     """n = 32 SiLU neural ODE, per-series random lengths padded into one launch."""
     return mlp_ode(seed=seed, B=B, N=N, n=n, hidden=hidden, act="silu", t_end=t_end,
                    lengths_range=lengths_range)
+
+
+def mds(seed=SEED_MDS, B=100, N=2000, n_unit=2, t_max=1.0, jitter=0.0):
+    """Mass-damper-spring chain (Sec. 5.1.1, Table mass-params): K_i, C_i, M_i
+    linspace over the units in [1e-2, 1], [1e-6, 1e-4], [1e-7, 1e-5]; f_a = 1;
+    forcing period T linspace over the series in [1e-2, 1]; zero initial
+    state; N uniform steps on [0, t_max].  Per-series parameter vectors
+    [K_1..K_u, C_1..C_u, M_1..M_u, f_a, T].  jitter > 0 multiplies every
+    parameter by a seeded factor exp(jitter * N(0, 1)) (distinct series for
+    tests); 0 keeps the table's values."""
+    u = int(n_unit)
+    base = np.concatenate([np.linspace(1e-2, 1.0, u), np.linspace(1e-6, 1e-4, u),
+                           np.linspace(1e-7, 1e-5, u), [1.0]])
+    T = np.linspace(1e-2, 1.0, B)
+    params = np.concatenate([np.tile(base, (B, 1)), T[:, None]], axis=1)
+    if jitter > 0.0:
+        params = params * np.exp(jitter * _rng(seed).standard_normal(params.shape))
+    return {"spec": {"kind": "mds", "n": 2 * u, "hidden": (0, 0), "per_series": True},
+            "y0": np.zeros((B, 2 * u)), "times": uniform_times(B, N, t_max),
+            "params": params, "lengths": None}
 
 
 def random_grad_out(seed, B, N, n, scale=1.0):
