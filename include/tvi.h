@@ -272,19 +272,21 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
  * as the built-in linear and van der Pol models.  `source` defines, at global
  * scope, with TVI_N (= n) and TVI_P (= P) #defined before it:
  *
- *   __device__ void tvi_rhs(const double* y, const double* p, double* h);
- *       h[i] = h_i(y; p), i < n: the autonomous ODE dy/dt = h(y; p)
- *   __device__ void tvi_jac(const double* y, const double* p, double* J);
+ *   __device__ void tvi_rhs(const double* y, double t, const double* p, double* h);
+ *       h[i] = h_i(y, t; p), i < n: the ODE dy/dt = h(y, t; p) (Sec. 2.1)
+ *   __device__ void tvi_jac(const double* y, double t, const double* p, double* J);
  *       J[i * n + j] = dh_i/dy_j: the step Jacobian of step k is I - dt_k J
- *   __device__ void tvi_vjp_p(const double* y, const double* p, const double* a,
- *                             double* g);
+ *   __device__ void tvi_vjp_p(const double* y, double t, const double* p,
+ *                             const double* a, double* g);
  *       g[q] = sum_i a_i dh_i/dp_q, q < P: the adjoint's gradient integrand
  *       (App. A.1)
  *
- * y and p hold n and P values, a holds n; h, J and g must be written in full.
- * tvi_rhs and tvi_vjp_p are evaluated in FP64.  tvi_jac may instead be a
- * template over the element type of y and J,
- *   template <typename T> __device__ void tvi_jac(const T* y, const double* p, T* J);
+ * y and p hold n and P values, a holds n, t is the time of the evaluation (t_k
+ * for backward Euler's step k, t_{k-1} for forward Euler's); h, J and g must be
+ * written in full.  tvi_rhs and tvi_vjp_p are evaluated in FP64.  tvi_jac may
+ * instead be a template over the element type of y and J,
+ *   template <typename T>
+ *   __device__ void tvi_jac(const T* y, double t, const double* p, T* J);
  * and is then evaluated in the block type (FP32 with FP32 blocks, as for the
  * built-in models); a plain FP64 tvi_jac is evaluated in FP64 and rounded.  The library trusts them: J must be the Jacobian of h for Newton
  * to converge quadratically, and g its parameter product for the gradients to

@@ -125,7 +125,7 @@ template <class...> struct TviVoid { typedef void type; };
 template <class T> T&& tvi_declval();
 template <class T, class = void> struct TviTypedJac { static constexpr bool value = false; };
 template <class T>
-struct TviTypedJac<T, typename TviVoid<decltype(tvi_jac(tvi_declval<const T*>(),
+struct TviTypedJac<T, typename TviVoid<decltype(tvi_jac(tvi_declval<const T*>(), 0.0,
                                                         tvi_declval<const double*>(),
                                                         tvi_declval<T*>()))>::type> {
   static constexpr bool value = true;
@@ -143,16 +143,17 @@ struct TviUserModel {
 #pragma unroll
     for (int q = 0; q < NP; ++q) p[q] = src[q];
   }
-  __device__ __forceinline__ void rhs(const double (&y)[NS], double (&h)[NS]) const {
-    tvi_rhs(y, p, h);
+  __device__ __forceinline__ void rhs(const double (&y)[NS], double t, double (&h)[NS]) const {
+    tvi_rhs(y, t, p, h);
   }
   // A = I - dt J, J = dh/dy evaluated in the block type T when tvi_jac is a
   // template over it, else in FP64 and rounded to T (integer-pipe conversions)
   template <typename T>
-  __device__ __forceinline__ void step_matrix(const T (&y)[NS], T dt, T (&A)[NS][NS]) const {
+  __device__ __forceinline__ void step_matrix(const T (&y)[NS], double t, T dt,
+                                              T (&A)[NS][NS]) const {
     if constexpr (TviTypedJac<T>::value) {
       T J[NS * NS];
-      tvi_jac(y, p, J);
+      tvi_jac(y, t, p, J);
 #pragma unroll
       for (int r = 0; r < NS; ++r)
 #pragma unroll
@@ -161,7 +162,7 @@ struct TviUserModel {
       double yd[NS], J[NS * NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) yd[s] = tvi::widen(y[s]);
-      tvi_jac(yd, p, J);
+      tvi_jac(yd, t, p, J);
 #pragma unroll
       for (int r = 0; r < NS; ++r)
 #pragma unroll
@@ -170,10 +171,10 @@ struct TviUserModel {
     }
   }
   // acc += scale (dh/dp)^T a
-  __device__ __forceinline__ void vjp_p(const double (&y)[NS], const double (&a)[NS],
+  __device__ __forceinline__ void vjp_p(const double (&y)[NS], double t, const double (&a)[NS],
                                         double scale, double (&acc)[NP]) const {
     double g[NP];
-    tvi_vjp_p(y, p, a, g);
+    tvi_vjp_p(y, t, p, a, g);
 #pragma unroll
     for (int q = 0; q < NP; ++q) acc[q] = fma(scale, g[q], acc[q]);
   }
@@ -183,11 +184,12 @@ struct TviUserModel {
 // Kernel that calls each user function once: compiling it checks the source
 // without instantiating the solver templates.
 const char* const kCheck = R"tvi_src(
-__global__ void tvi_user_check(const double* y, const double* p, const double* a, double* out) {
+__global__ void tvi_user_check(const double* y, double t, const double* p, const double* a,
+                               double* out) {
   double h[TVI_N], J[TVI_N * TVI_N], g[TVI_P];
-  tvi_rhs(y, p, h);
-  tvi_jac(y, p, J);
-  tvi_vjp_p(y, p, a, g);
+  tvi_rhs(y, t, p, h);
+  tvi_jac(y, t, p, J);
+  tvi_vjp_p(y, t, p, a, g);
   for (int i = 0; i < TVI_N; ++i) out[i] = h[i];
   for (int i = 0; i < TVI_N * TVI_N; ++i) out[TVI_N + i] = J[i];
   for (int i = 0; i < TVI_P; ++i) out[TVI_N + TVI_N * TVI_N + i] = g[i];

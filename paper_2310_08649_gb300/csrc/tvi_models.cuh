@@ -5,10 +5,11 @@
 // Every model provides
 //   NS, NP                         state size, parameters per vector
 //   load(params, b, per_series)    fetch the series' parameters into registers
-//   rhs(y, h)                      FP64 h(y)              (residual: always FP64)
-//   step_matrix<T>(y, dt, A)       A = I - dt j(y) in T   (block: FP32 or FP64)
-//   vjp_p(y, a, scale, acc)        acc[NP] += scale (dh/dp)^T a   (FP64)
-// The models here are autonomous, so t is not an argument.
+//   rhs(y, t, h)                   FP64 h(y, t)                (residual: always FP64)
+//   step_matrix<T>(y, t, dt, A)    A = I - dt j(y, t) in T     (block: FP32 or FP64)
+//   vjp_p(y, t, a, scale, acc)     acc[NP] += scale (dh/dp)^T a at (y, t)   (FP64)
+// The models here are autonomous and ignore t (the kernels' loads of t then
+// compile away); run-time compiled user models may use it.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -27,13 +28,13 @@ struct ModelVdp {
   __device__ __forceinline__ void load(const double* params, int b, int per_series) {
     mu = params[per_series ? b : 0];
   }
-  __device__ __forceinline__ void rhs(const double (&y)[2], double (&h)[2]) const {
+  __device__ __forceinline__ void rhs(const double (&y)[2], double, double (&h)[2]) const {
     h[0] = y[1];
     h[1] = fma(mu * fma(-y[0], y[0], 1.0), y[1], -y[0]);
   }
   // j = [[0, 1], [-2 mu y1 y2 - 1, mu (1 - y1^2)]]
   template <typename T>
-  __device__ __forceinline__ void step_matrix(const T (&y)[2], T dt, T (&A)[2][2]) const {
+  __device__ __forceinline__ void step_matrix(const T (&y)[2], double, T dt, T (&A)[2][2]) const {
     T m = static_cast<T>(mu);
     A[0][0] = T(1);
     A[0][1] = -dt;
@@ -41,8 +42,8 @@ struct ModelVdp {
     A[1][1] = fma(-dt * m, fma(-y[0], y[0], T(1)), T(1));
   }
   // dh/dmu = [0, (1 - y1^2) y2]
-  __device__ __forceinline__ void vjp_p(const double (&y)[2], const double (&a)[2], double scale,
-                                        double (&acc)[NP]) const {
+  __device__ __forceinline__ void vjp_p(const double (&y)[2], double, const double (&a)[2],
+                                        double scale, double (&acc)[NP]) const {
     acc[0] = fma(scale * a[1], fma(-y[0], y[0], 1.0) * y[1], acc[0]);
   }
 };
@@ -63,7 +64,7 @@ struct ModelLinear {
 #pragma unroll
       for (int j = 0; j < NS; ++j) A[i][j] = p[i * NS + j];
   }
-  __device__ __forceinline__ void rhs(const double (&y)[N_], double (&h)[N_]) const {
+  __device__ __forceinline__ void rhs(const double (&y)[N_], double, double (&h)[N_]) const {
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
       double s = 0.0;
@@ -73,7 +74,8 @@ struct ModelLinear {
     }
   }
   template <typename T>
-  __device__ __forceinline__ void step_matrix(const T (&y)[N_], T dt, T (&M)[N_][N_]) const {
+  __device__ __forceinline__ void step_matrix(const T (&y)[N_], double, T dt,
+                                              T (&M)[N_][N_]) const {
     (void)y;
 #pragma unroll
     for (int i = 0; i < NS; ++i)
@@ -82,7 +84,7 @@ struct ModelLinear {
         M[i][j] = fma(-dt, static_cast<T>(A[i][j]), (i == j) ? T(1) : T(0));
   }
   // dh_i/dA_ij = y_j  =>  (dh/dA)^T a = a y^T
-  __device__ __forceinline__ void vjp_p(const double (&y)[N_], const double (&a)[N_],
+  __device__ __forceinline__ void vjp_p(const double (&y)[N_], double, const double (&a)[N_],
                                         double scale, double (&acc)[NP]) const {
 #pragma unroll
     for (int i = 0; i < NS; ++i)

@@ -17,8 +17,8 @@ namespace kern {
 template <class Model, int RPT>
 __device__ __forceinline__ unsigned long long residual_norm_block(
     const Model& mdl, const double (&yi)[Model::NS], const double (&dyv)[RPT][Model::NS],
-    const double (&dt)[RPT], const bool (&act)[RPT], double (*s_wlast)[Model::NS],
-    unsigned long long* s_red, int lane, int warp) {
+    const double (&dt)[RPT], const bool (&act)[RPT], const double* tb, int k0,
+    double (*s_wlast)[Model::NS], unsigned long long* s_red, int lane, int warp) {
   constexpr int NS = Model::NS;
   const int nwarps = static_cast<int>(blockDim.x >> 5);
   double prev[NS];
@@ -39,7 +39,7 @@ __device__ __forceinline__ unsigned long long residual_norm_block(
     double y[NS], h[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) y[s] = yi[s] + dyv[r][s];
-    mdl.rhs(y, h);
+    mdl.rhs(y, act[r] ? tb[k0 + r] : 0.0, h);  // row r is step k0 + r
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const double pv = (r == 0) ? prev[s] : dyv[r - 1][s];
@@ -196,9 +196,11 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
 #pragma unroll
           for (int s = 0; s < NS; ++s) dz[r][s] = 0.0;
         const unsigned long long n_zero =
-            residual_norm_block<Model, RPT>(mdl, yi, dz, dt, act, s_wlast, s_red, lane, warp);
+            residual_norm_block<Model, RPT>(mdl, yi, dz, dt, act, tb, i + 1 + tid * RPT, s_wlast,
+                                            s_red, lane, warp);
         const unsigned long long n_pred =
-            residual_norm_block<Model, RPT>(mdl, yi, dyp, dt, act, s_wlast, s_red, lane, warp);
+            residual_norm_block<Model, RPT>(mdl, yi, dyp, dt, act, tb, i + 1 + tid * RPT, s_wlast,
+                                            s_red, lane, warp);
         if (n_pred < n_zero) {  // both finite bit patterns compare as values
 #pragma unroll
           for (int r = 0; r < RPT; ++r)
@@ -251,7 +253,8 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
             yp[s] = (r == 0) ? prev[s] : yv[r - 1][s];
             yh[s] = fwd_euler ? yp[s] : yv[r][s];
           }
-          mdl.rhs(yh, h);
+          const int k = i + 1 + tid * RPT + r;
+          mdl.rhs(yh, act[r] ? tb[fwd_euler ? k - 1 : k] : 0.0, h);
 #pragma unroll
           for (int s = 0; s < NS; ++s) {
             R[r][s] = act[r] ? fma(-dt[r], h[s], yv[r][s] - yp[s]) : 0.0;
@@ -313,7 +316,8 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
                 else yt[s] = yv[r][s];
               }
             }
-            mdl.step_matrix(yt, dtT[r], A);  // A = I - dt j
+            const int k = i + 1 + tid * RPT + r;
+            mdl.step_matrix(yt, tb[fwd_euler ? k - 1 : k], dtT[r], A);  // A = I - dt j
             T Rt[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) Rt[q] = narrow<T>(R[r][q]);
@@ -507,7 +511,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
         T yt[NS], A[NS][NS], Ai[NS][NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) yt[s] = narrow<T>(yk[r][s]);
-        mdl.step_matrix(yt, narrow<T>(dtb[r]), A);  // A = I - dt j(y_k)
+        mdl.step_matrix(yt, tb[k], narrow<T>(dtb[r]), A);  // A = I - dt j(y_k, t_k)
         if (fwd_euler) {
           // x_q = (2I - A)^T x_{q-1} + g_k, the carry a_{i+L+1} entering row 0
 #pragma unroll
@@ -572,7 +576,8 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
         double A[NS][NS];
-        mdl.step_matrix(yk[r], dtb[r], A);
+        const int k = i + L - (tid * RPT + r);
+        mdl.step_matrix(yk[r], act[r] ? tb[k] : 0.0, dtb[r], A);
         double res[NS];
 #pragma unroll
         for (int p = 0; p < NS; ++p) {
@@ -616,9 +621,9 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
           double ykm[NS];
 #pragma unroll
           for (int s = 0; s < NS; ++s) ykm[s] = yb[static_cast<size_t>(k - 1) * NS + s];
-          mdl.vjp_p(ykm, av[r], dt[r], acc);
+          mdl.vjp_p(ykm, tb[k - 1], av[r], dt[r], acc);
         } else {
-          mdl.vjp_p(yk[r], av[r], dt[r], acc);
+          mdl.vjp_p(yk[r], tb[i + L - (tid * RPT + r)], av[r], dt[r], acc);
         }
       }
     }  // wact
@@ -642,7 +647,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
       double y0v[NS], A[NS][NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) y0v[s] = yb[s];
-      mdl.step_matrix(y0v, (N >= 1 && 1 <= len) ? tb[1] - tb[0] : 0.0, A);
+      mdl.step_matrix(y0v, tb[0], (N >= 1 && 1 <= len) ? tb[1] - tb[0] : 0.0, A);
 #pragma unroll
       for (int p = 0; p < NS; ++p) {
         double v = gb[p];

@@ -1,11 +1,14 @@
 """Example user models: CUDA C++ device source for tvi_user_model_create
-(UserModel), each defining tvi_rhs, tvi_jac and tvi_vjp_p over FP64 pointers.
+(UserModel), each defining tvi_rhs, tvi_jac and tvi_vjp_p over FP64 pointers and
+the time t.
 
     VDP          van der Pol, h = [y2, mu (1 - y1^2) y2 - y1], p = [mu]   (n 2, P 1)
                  (tvi_jac a template: FP32 Jacobians with FP32 blocks)
     VDP_FP64_JAC the same with an FP64 tvi_jac
     LINEAR       h = A y, p = A row-major                                (any n, P n^2)
     mlp_tanh()   h = tanh(W3 tanh(W2 tanh(W1 y + b1) + b2) + b3)         (any n)
+    MDS          mass-damper-spring chain of n/2 units with periodic forcing
+                 (time-dependent; p = [K_1.., C_1.., M_1.., f_a, T], P = 3n/2 + 2)
 
     import paper_2310_08649_gb300 as tvi
     from paper_2310_08649_gb300.user_sources import VDP
@@ -14,26 +17,28 @@
 
 VDP = r"""
 // van der Pol: h = [y2, mu (1 - y1^2) y2 - y1], p = [mu]
-__device__ void tvi_rhs(const double* y, const double* p, double* h) {
+__device__ void tvi_rhs(const double* y, double t, const double* p, double* h) {
   h[0] = y[1];
   h[1] = p[0] * (1.0 - y[0] * y[0]) * y[1] - y[0];
 }
 // the Jacobian as a template: evaluated in FP32 with FP32 blocks
 template <typename T>
-__device__ void tvi_jac(const T* y, const double* p, T* J) {
+__device__ void tvi_jac(const T* y, double t, const double* p, T* J) {
   const T mu = static_cast<T>(p[0]);
   J[0] = T(0);
   J[1] = T(1);
   J[2] = -T(2) * mu * y[0] * y[1] - T(1);
   J[3] = mu * (T(1) - y[0] * y[0]);
 }
-__device__ void tvi_vjp_p(const double* y, const double* p, const double* a, double* g) {
+__device__ void tvi_vjp_p(const double* y, double t, const double* p, const double* a,
+                          double* g) {
   g[0] = a[1] * (1.0 - y[0] * y[0]) * y[1];
 }
 """
 
 # van der Pol with a plain FP64 Jacobian (rounded to the block type after evaluation)
-VDP_FP64_JAC = VDP[:VDP.index("// the Jacobian as a template")] + r"""__device__ void tvi_jac(const double* y, const double* p, double* J) {
+VDP_FP64_JAC = VDP[:VDP.index("// the Jacobian as a template")] + r"""
+__device__ void tvi_jac(const double* y, double t, const double* p, double* J) {
   J[0] = 0.0;
   J[1] = 1.0;
   J[2] = -2.0 * p[0] * y[0] * y[1] - 1.0;
@@ -43,17 +48,18 @@ VDP_FP64_JAC = VDP[:VDP.index("// the Jacobian as a template")] + r"""__device__
 
 LINEAR = r"""
 // h = A y with A = p as a row-major TVI_N x TVI_N matrix
-__device__ void tvi_rhs(const double* y, const double* p, double* h) {
+__device__ void tvi_rhs(const double* y, double t, const double* p, double* h) {
   for (int i = 0; i < TVI_N; ++i) {
     double s = 0.0;
     for (int j = 0; j < TVI_N; ++j) s += p[i * TVI_N + j] * y[j];
     h[i] = s;
   }
 }
-__device__ void tvi_jac(const double* y, const double* p, double* J) {
+__device__ void tvi_jac(const double* y, double t, const double* p, double* J) {
   for (int k = 0; k < TVI_N * TVI_N; ++k) J[k] = p[k];
 }
-__device__ void tvi_vjp_p(const double* y, const double* p, const double* a, double* g) {
+__device__ void tvi_vjp_p(const double* y, double t, const double* p, const double* a,
+                          double* g) {
   for (int i = 0; i < TVI_N; ++i)
     for (int j = 0; j < TVI_N; ++j) g[i * TVI_N + j] = a[i] * y[j];
 }
@@ -90,14 +96,14 @@ __device__ void mlp_eval(const double* y, const double* p, MlpState& s) {
   }
 }
 
-__device__ void tvi_rhs(const double* y, const double* p, double* h) {
+__device__ void tvi_rhs(const double* y, double t, const double* p, double* h) {
   MlpState s;
   mlp_eval(y, p, s);
   for (int i = 0; i < TVI_N; ++i) h[i] = s.h[i];
 }
 
 // row i of J = d3_i W3[i,:] D2 W2 D1 W1
-__device__ void tvi_jac(const double* y, const double* p, double* J) {
+__device__ void tvi_jac(const double* y, double t, const double* p, double* J) {
   const double* W1 = p;
   const double* W2 = W1 + H1 * TVI_N + H1;
   const double* W3 = W2 + H2 * H1 + H2;
@@ -121,7 +127,8 @@ __device__ void tvi_jac(const double* y, const double* p, double* J) {
 }
 
 // back-propagation of a through the three layers
-__device__ void tvi_vjp_p(const double* y, const double* p, const double* a, double* g) {
+__device__ void tvi_vjp_p(const double* y, double t, const double* p, const double* a,
+                          double* g) {
   const double* W2 = p + H1 * TVI_N + H1;
   const double* W3 = W2 + H2 * H1 + H2;
   double* gW1 = g;
@@ -158,3 +165,75 @@ __device__ void tvi_vjp_p(const double* y, const double* p, const double* a, dou
 
 def mlp_param_count(n, h1, h2):
     return h1 * n + h1 + h2 * h1 + h2 + n * h2 + n
+
+
+MDS = r"""
+// mass-damper-spring chain of kU = TVI_N / 2 units, y = [d_1..d_u, v_1..v_u],
+// p = [K_1..K_u, C_1..C_u, M_1..M_u, f_a, T]: spring and damper i join mass i
+// to mass i+1 (the fixed wall for i = u); the force f_a sin(2 pi t / T) acts
+// on mass 1 (the free end)
+constexpr int kU = TVI_N / 2;
+
+// F_i = K_i (d_{i+1} - d_i) + C_i (v_{i+1} - v_i), F_{-1} = 0
+__device__ double mds_force(const double* y, const double* p, int i) {
+  if (i < 0) return 0.0;
+  const double dn = i + 1 < kU ? y[i + 1] : 0.0;
+  const double vn = i + 1 < kU ? y[kU + i + 1] : 0.0;
+  return p[i] * (dn - y[i]) + p[kU + i] * (vn - y[kU + i]);
+}
+
+__device__ void tvi_rhs(const double* y, double t, const double* p, double* h) {
+  for (int i = 0; i < kU; ++i) {
+    h[i] = y[kU + i];
+    h[kU + i] = (mds_force(y, p, i) - mds_force(y, p, i - 1)) / p[2 * kU + i];
+  }
+  h[kU] += p[3 * kU] * sin(6.283185307179586 * t / p[3 * kU + 1]);
+}
+
+// constant in y: evaluated in the block type
+template <typename T>
+__device__ void tvi_jac(const T* y, double t, const double* p, T* J) {
+  for (int k = 0; k < TVI_N * TVI_N; ++k) J[k] = T(0);
+  for (int i = 0; i < kU; ++i) {
+    J[i * TVI_N + kU + i] = T(1);
+    T* row = J + (kU + i) * TVI_N;
+    const T inv_m = T(1) / static_cast<T>(p[2 * kU + i]);
+    const T k0 = static_cast<T>(p[i]) * inv_m, c0 = static_cast<T>(p[kU + i]) * inv_m;
+    row[i] -= k0;
+    row[kU + i] -= c0;
+    if (i + 1 < kU) {
+      row[i + 1] += k0;
+      row[kU + i + 1] += c0;
+    }
+    if (i > 0) {
+      const T k1 = static_cast<T>(p[i - 1]) * inv_m, c1 = static_cast<T>(p[kU + i - 1]) * inv_m;
+      row[i] -= k1;
+      row[i - 1] += k1;
+      row[kU + i] -= c1;
+      row[kU + i - 1] += c1;
+    }
+  }
+}
+
+__device__ void tvi_vjp_p(const double* y, double t, const double* p, const double* a,
+                          double* g) {
+  const double* av = a + kU;
+  for (int i = 0; i < kU; ++i) {
+    const double dn = i + 1 < kU ? y[i + 1] : 0.0;
+    const double vn = i + 1 < kU ? y[kU + i + 1] : 0.0;
+    // F_i enters v_i' as +F_i / M_i and v_{i+1}' as -F_i / M_{i+1}
+    const double w = av[i] / p[2 * kU + i] - (i + 1 < kU ? av[i + 1] / p[2 * kU + i + 1] : 0.0);
+    g[i] = w * (dn - y[i]);
+    g[kU + i] = w * (vn - y[kU + i]);
+    const double m = p[2 * kU + i];
+    g[2 * kU + i] = -av[i] * (mds_force(y, p, i) - mds_force(y, p, i - 1)) / (m * m);
+  }
+  const double ph = 6.283185307179586 * t / p[3 * kU + 1];
+  g[3 * kU] = av[0] * sin(ph);
+  g[3 * kU + 1] = -av[0] * p[3 * kU] * cos(ph) * ph / p[3 * kU + 1];
+}
+"""
+
+
+def mds_param_count(n_unit):
+    return 3 * n_unit + 2

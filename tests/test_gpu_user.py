@@ -16,8 +16,8 @@ import pytest
 import workloads
 from oracle import Model as OModel
 from test_gpu_euler import fe_error_estimate
-from paper_2310_08649_gb300.user_sources import LINEAR, VDP, VDP_FP64_JAC, mlp_param_count, \
-    mlp_tanh
+from paper_2310_08649_gb300.user_sources import LINEAR, MDS, VDP, VDP_FP64_JAC, \
+    mds_param_count, mlp_param_count, mlp_tanh
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -40,7 +40,9 @@ def users(tvi):
     made = {"vdp": tvi.UserModel(2, 1, VDP), "vdp64": tvi.UserModel(2, 1, VDP_FP64_JAC),
             "lin1": tvi.UserModel(1, 1, LINEAR),
             "lin3": tvi.UserModel(3, 9, LINEAR),
-            "mlp3": tvi.UserModel(3, mlp_param_count(3, 2, 2), mlp_tanh(2, 2))}
+            "mlp3": tvi.UserModel(3, mlp_param_count(3, 2, 2), mlp_tanh(2, 2)),
+            "mds1": tvi.UserModel(2, mds_param_count(1), MDS),
+            "mds2": tvi.UserModel(4, mds_param_count(2), MDS)}
     yield made
     torch.cuda.synchronize()
     for u in made.values():
@@ -172,6 +174,32 @@ def test_user_forward_euler(tvi, users, oracle_lib, precision):
     dp_ref, dy0_ref = oracle_lib.adjoint_euler(m, w["times"], w["params"], ref, g)
     dp, dy0 = adjoint(tvi, model, w, o, ref, g)
     assert relerr(dp, dp_ref) <= GATE[precision]
+    assert relerr(dy0, dy0_ref) <= GATE[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("u,chunk", [(1, 100), (2, 1000), (2, 7)])
+def test_user_mds_matches_oracle(tvi, users, oracle_lib, precision, u, chunk):
+    """Time-dependent right-hand side (the forcing f_a sin(2 pi t / T)): the
+    mass-damper-spring chain of the paper's timing study, per-series parameters
+    (table values, jittered so that series differ), zero initial state."""
+    w = workloads.mds(B=16, N=2000, n_unit=u, jitter=0.1, seed=70 + u)
+    m = OModel.from_spec(w["spec"])
+    ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], tol_abs=1e-18,
+                                    max_iter=4)
+    assert not st.any()
+    model = users[f"mds{u}"].model(per_series=True)
+    # |v| reaches 5e-3, so FP64 residuals bottom out near 1e-18: stop at 1e-17
+    o = tvi.Options(chunk=chunk, tol_abs=1e-17, max_iter=20, precision=precision,
+                    adjoint_refine=3)
+    y, _, status, rc = forward(tvi, model, w, o)
+    assert rc == 0 and not status.any()
+    assert relerr_series(y, ref).max() <= GATE[precision]
+    g = workloads.random_grad_out(96 + u, 16, 2000, 2 * u)
+    dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g)
+    dp, dy0 = adjoint(tvi, model, w, o, ref, g)
+    e_p = np.abs(dp - dp_ref).max(axis=1) / np.abs(dp_ref).max(axis=1)
+    assert e_p.max() <= GATE[precision], (e_p.argmax(), e_p.max())
     assert relerr(dy0, dy0_ref) <= GATE[precision]
 
 
