@@ -49,6 +49,10 @@ WORKLOADS = {
     # the same van der Pol workload through a user model (device source compiled at run time)
     "vdp_user": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 128, "N": 10000,
                  "refine": 1},
+    # mass-damper-spring chain of the paper's timing study (2 units, 100 series, 2000
+    # steps) as a time-dependent user model; |v| <= 5e-3, residuals bottom out near 1e-18
+    "mds_user": {"chunk": 1000, "precision": "fp32", "tol": 1e-17, "B": 100, "N": 2000,
+                 "refine": 2},
     "node16": {"chunk": 200, "precision": "bf16", "tol": 1e-8, "B": 64, "N": 2000, "refine": 2},
     "node32": {"chunk": 1000, "precision": "bf16", "tol": 1e-8, "B": 512, "N": 20000,
                "refine": 2},
@@ -82,7 +86,7 @@ def parse():
     for k, v in WORKLOADS[args.workload].items():
         if getattr(args, k) is None:
             setattr(args, k, v)
-    if not args.workload.startswith("vdp"):
+    if args.workload.startswith("node"):
         args.no_chunk1 = True  # the one-step MLP scheme reads status back every Newton update
     return args
 
@@ -98,6 +102,8 @@ def make_workload(args, rank=0):
         w = workloads.vdp(B=args.B, N=args.N, seed=workloads.SEED_VDP + 1000 * rank)
     elif args.workload == "vdp_pred":
         w = workloads.vdp(B=args.B, N=args.N, seed=PRED_EVAL_SEED + rank)
+    elif args.workload == "mds_user":
+        w = workloads.mds(B=args.B, N=args.N, n_unit=2)  # the table's parameters, no draw
     elif args.workload == "node16":
         w = workloads.mlp_ode(B=args.B, N=args.N, seed=workloads.SEED_MLP + 1000 * rank)
     else:
@@ -136,6 +142,9 @@ def workload_config(args):
                         "(MLP 103-256-256-200)",
             "vdp_user": "van der Pol n=2 as a user model (device source compiled at run time), "
                         "mu log-uniform [10,1000], log-spaced steps",
+            "mds_user": "mass-damper-spring chain, 2 units (n=4), forcing f_a sin(2 pi t/T) with "
+                        "T linspace [0.01,1] over the series, as a user model; uniform steps on "
+                        "[0,1]",
             "node16": "neural ODE n=16, MLP 16-64-64-16 tanh, uniform steps on [0,10]",
             "node32": "neural ODE n=32, MLP 32-128-128-32 SiLU, per-series lengths "
                       "U[2000,N] padded, uniform steps on [0,10]"}[args.workload]
@@ -292,7 +301,16 @@ def roofline(args, w, stats, fwd_ms, adj_ms, refine):
     upd = stats[:, 0].astype(np.float64)
     nchk = stats[:, 1].astype(np.float64)
     spc = N / np.maximum(nchk, 1)  # steps per solved chunk
-    if args.workload.startswith("vdp"):
+    if args.workload == "mds_user":
+        # residual: h of the 2-unit chain (two spring-damper forces 6, the two mass
+        # divisions and a difference 3, forcing sin, multiply, divide, add 4: 13) + R (8)
+        # = 21; update y -= d: 4.  Adjoint per step: per refinement sweep the residual
+        # (A^T a, 16 + 8) = 24, parameter VJP (3 per unit and force terms, sin, cos) 20
+        fwd_ops = float(np.sum(((upd + nchk) * 21.0 + upd * 4.0) * spc))
+        adj_ops = float(B * N * (refine * 24.0 + 20.0))
+        names = (f"forward_small_kernel<TviUserModel(mds),{args.precision}>",
+                 f"adjoint_small_kernel<TviUserModel(mds),{args.precision}>")
+    elif args.workload.startswith("vdp"):
         # residual on the stored iterate y: h (3) + R (4) = 7; update y -= d: 2
         fwd_ops = float(np.sum(((upd + nchk) * 7.0 + upd * 2.0) * spc))
         # adjoint per step: per refinement sweep 14, parameter VJP 4
@@ -360,6 +378,12 @@ def run_ours(args):
     if args.workload == "vdp_user":
         from paper_2310_08649_gb300.user_sources import VDP
         user = tvi.UserModel(2, 1, VDP).prepare(args.precision)  # compiled before timing
+        model = user.model(per_series=True)
+    elif args.workload == "mds_user":
+        from paper_2310_08649_gb300.user_sources import MDS, mds_param_count
+        user = tvi.UserModel(4, mds_param_count(2), MDS).prepare(args.precision)
+        if not args.no_chunk1:
+            user.prepare("fp64")  # the chunk = 1 FP64 leg
         model = user.model(per_series=True)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
