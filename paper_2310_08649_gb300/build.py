@@ -24,7 +24,8 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompil
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC, "-I", OUT_DIR] + ARCH
 
 # headers the run-time compiled user-model kernels include (tvi_jit.cu)
-JIT_HEADERS = ["tvi_device.cuh", "tvi_internal.h", "tvi_predictor.cuh", "tvi_small_kernels.cuh"]
+JIT_HEADERS = ["tvi_device.cuh", "tvi_internal.h", "tvi_predictor.cuh", "tvi_small_kernels.cuh",
+               "tvi_large_kernels.cuh"]
 
 
 def nvcc():

@@ -53,6 +53,11 @@ bool is_mlp(const tvi_model* m) {
   return m->kind == TVI_MODEL_MLP_TANH || m->kind == TVI_MODEL_MLP_SILU;
 }
 
+// user models with n > 4 take the large-state route (workspace, no halving)
+bool is_large_user(const tvi_model* m) {
+  return m->kind == TVI_MODEL_USER && tvi::user_large(m->user);
+}
+
 // a user-model error from tvi_jit.cu: the full text (a compiler log can be long)
 tvi_status jit_fail(int kind, const std::string& text) {
   g_last_error = text;
@@ -109,10 +114,10 @@ tvi_status check_model(const tvi_model* m) {
 
 // BF16 block products run on the tensor cores of the MLP path only
 tvi_status check_precision(const tvi_model* m, const tvi_options* o) {
-  if (o->scheme == TVI_FORWARD_EULER && (is_mlp(m) || o->predictor))
+  if (o->scheme == TVI_FORWARD_EULER && (is_mlp(m) || o->predictor || is_large_user(m)))
     return fail(TVI_EUNSUPPORTED,
-                "forward Euler is built for the linear and van der Pol models, without a "
-                "predictor");
+                "forward Euler is built for the small-state engine (linear, van der Pol and "
+                "user models with n <= 4), without a predictor");
   if (m->kind == TVI_MODEL_USER && o->precision == tvi::kPrecBf16)
     return fail(TVI_EUNSUPPORTED, "user models run with FP64 or FP32 blocks");
   if (o->precision != tvi::kPrecBf16) return TVI_OK;
@@ -202,6 +207,10 @@ size_t tvi_workspace_bytes(const tvi_model* model, const tvi_options* opt, int B
     return tvi::mlp_workspace_bytes(model->n, model->hidden1, model->hidden2, B, mlp_chunk(opt, N),
                                     opt->precision);
   }
+  if (is_large_user(model)) {
+    if (!opt) return 0;
+    return tvi::user_workspace_bytes(model->user, B, mlp_chunk(opt, N), opt->precision);
+  }
   return layout(B, P).total;
 }
 
@@ -260,6 +269,18 @@ tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, 
                                      opt->sync_status ? &worst : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "tvi_integrate (MLP path)");
     if (worst == 3) return fail(TVI_ETIMEOUT, "a tensor-core wait gave up; results are invalid");
+    if (worst == 2) return fail(TVI_ENONFINITE, "a series produced a non-finite residual");
+    if (worst == 1) return fail(TVI_ENOTCONV, "a series hit the Newton iteration limit");
+    return TVI_OK;
+  }
+  if (is_large_user(model)) {
+    a.chunk = mlp_chunk(opt, N);
+    int worst = 0;
+    std::string err;
+    int rc = tvi::user_large_forward(model->user, opt->precision, a, workspace, s,
+                                     opt->sync_status ? &worst : nullptr, &err);
+    if (rc != tvi::kJitOk) return jit_fail(rc, "tvi_integrate: " + err);
+    if (worst == 3) return fail(TVI_ETIMEOUT, "a bounded wait gave up; results are invalid");
     if (worst == 2) return fail(TVI_ENONFINITE, "a series produced a non-finite residual");
     if (worst == 1) return fail(TVI_ENOTCONV, "a series hit the Newton iteration limit");
     return TVI_OK;
@@ -325,6 +346,12 @@ tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, in
     cudaError_t e = tvi::mlp_adjoint(model->kind, model->n, model->hidden1, model->hidden2,
                                      opt->precision, a, workspace, s);
     return e == cudaSuccess ? TVI_OK : cuda_fail(e, "tvi_adjoint (MLP path)");
+  }
+  if (is_large_user(model)) {
+    a.chunk = mlp_chunk(opt, N);
+    std::string err;
+    int rc = tvi::user_large_adjoint(model->user, opt->precision, a, workspace, s, &err);
+    return rc == tvi::kJitOk ? TVI_OK : jit_fail(rc, "tvi_adjoint: " + err);
   }
   if (N == 0) {
     // no steps: dL/dp = 0 and dL/dy0 = grad_out[:, 0]
@@ -440,8 +467,10 @@ extern "C" tvi_status tvi_adjoint_noalloc(const tvi_model* model, const tvi_opti
   g_last_error.clear();
   tvi_status r = check_model(model);
   if (r != TVI_OK) return r;
-  if (is_mlp(model))
-    return fail(TVI_EUNSUPPORTED, "tvi_adjoint_noalloc covers the linear and van der Pol models");
+  if (is_mlp(model) || is_large_user(model))
+    return fail(TVI_EUNSUPPORTED,
+                "tvi_adjoint_noalloc covers the small-state engine (linear, van der Pol and user "
+                "models with n <= 4)");
   if ((r = check_opt(opt)) != TVI_OK) return r;
   if ((r = check_precision(model, opt)) != TVI_OK) return r;
   if (B < 0 || N < 0) return fail(TVI_EINVAL, "B and N must be >= 0 (got %d, %d)", B, N);

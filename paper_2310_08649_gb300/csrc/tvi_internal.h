@@ -63,6 +63,42 @@ struct AdjArgs {
   int scheme;        // kSchemeBackward / kSchemeForward
 };
 
+// Block chain solve of the large-state engines (mlp_chain_kernel): per series
+// d_j = M_j (d_{j-1} + rhs_j), j = 0..L-1, with x updated by mode.
+struct ChainArgs {
+  int B, n, L, c, N, i0, reverse;
+  const void* M;           // [B][c][n][n] in T, each block transposed
+  const double* rhs_buf;   // [B][c][n] rhs by row, or null
+  const double* rhs_traj;  // [B][N+1][n] rhs by step (adjoint dL/dy), or null
+  const double* x_init;    // [B][n] d_{-1}, or null (zero)
+  const int* active;       // [B] or null
+  double* x;               // [B][c][n]
+  int mode;                // 0: x -= d   1: x = d   2: x += d
+  int* err;                // set when a bounded wait for staged data gives up
+};
+
+// Argument block of the run-time compiled kernels of user models with n > 4
+// (tvi_large_kernels.cuh).  Rows j of the chunk are steps i0 + 1 + j (forward)
+// or i0 + L - j (reverse, the adjoint); state vectors are padded to n4 (a
+// multiple of 4) in the workspace buffers.
+struct LargeArgs {
+  int B, N, i0, L, c, n4, per_series, reverse;
+  const double* times;      // [B][N+1]
+  const int* lengths;       // [B] or null
+  const double* params;     // [B][P] or [P]
+  const double* yi;         // [B][n4] chunk start (forward)
+  const double* dy;         // [B][c][n4] Newton iterate (forward)
+  const double* ytraj;      // [B][N+1][n] trajectory (adjoint)
+  const double* g;          // [B][N+1][n] dL/dy (adjoint)
+  const double* av;         // [B][c][n4] adjoint rows (adjoint)
+  const double* carry;      // [B][n4] adjoint of the step after the chunk (adjoint)
+  double* R;                // [B][c][n4] residual rows (output)
+  void* J;                  // [B][c] slots of n4 x n4 T; J written n x n row-major
+  double* acc;              // [B][P] gradient accumulators (adjoint)
+  unsigned long long* norm; // [B] max |R| bits (forward)
+  const int* active;        // [B] or null
+};
+
 #ifndef __CUDACC_RTC__
 // Host-side count of the kernels this library has enqueued (every host thread),
 // read through tvi_kernel_launches(); called right before each launch.
@@ -81,7 +117,8 @@ cudaError_t small_sum_partials(const AdjArgs& a, int P, cudaStream_t s);
 // the caller's right-hand side.  Return kJitOk or an error kind, with the text
 // (the compiler log for kJitCompile) in *err.
 enum { kJitOk = 0, kJitNoNvrtc = 1, kJitCompile = 2, kJitCuda = 3 };
-constexpr int kUserMaxN = 4;
+constexpr int kUserSmallMaxN = 4;  // fused one-block-per-series kernels up to here
+constexpr int kUserMaxN = 32;      // large-state kernels above
 constexpr int kUserMaxP = 32;
 bool user_valid(const tvi_user_model* m);
 int user_n(const tvi_user_model* m);
@@ -93,6 +130,13 @@ int user_forward(const tvi_user_model* m, int precision, int rpt, int threads, c
                  cudaStream_t s, std::string* err);
 int user_adjoint(const tvi_user_model* m, int precision, int rpt, int threads, const AdjArgs& a,
                  cudaStream_t s, std::string* err);
+// n > kUserSmallMaxN: the large-state route, with a caller workspace
+bool user_large(const tvi_user_model* m);
+size_t user_workspace_bytes(const tvi_user_model* m, int B, int chunk, int precision);
+int user_large_forward(const tvi_user_model* m, int precision, const FwdArgs& a, void* workspace,
+                       cudaStream_t s, int* host_worst, std::string* err);
+int user_large_adjoint(const tvi_user_model* m, int precision, const AdjArgs& a, void* workspace,
+                       cudaStream_t s, std::string* err);
 
 // Neural-ODE (MLP right-hand side) path: shared parameters, n <= 32 and hidden
 // widths <= 128, all multiples of 4.  The chunk in the argument blocks is the
@@ -106,6 +150,30 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
                         void* workspace, cudaStream_t s, int* host_worst);
 cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const AdjArgs& a,
                         void* workspace, cudaStream_t s);
+// pieces of the MLP engine shared with large-state user models
+cudaError_t mlp_launch_chain(int precision, const ChainArgs& ch, cudaStream_t s);
+cudaError_t mlp_launch_check(int B, int it, int max_iter, double tol_abs, double tol_rel,
+                             unsigned long long* norm, double* norm0, int* active, int* status,
+                             int* iters, int* remaining, cudaStream_t s);
+// M slot of each active pair: J (n x n) in, block (n4 x n4) of A = I - dt J out
+// (A^-1 stored transposed, or A^-T when reverse), as the chain reads it
+cudaError_t user_invert_blocks(int precision, int B, int N, int i0, int L, int c, int n, int n4,
+                               int reverse, const double* times, const int* lengths,
+                               const int* active, void* M, cudaStream_t s);
+
+// Large-state user models (tvi_large.cu): n in 5..32, the run-time compiled
+// kernels of tvi_large_kernels.cuh around the pieces above.
+struct LargeKernels {
+  const void* residual;      // large_residual_kernel<Model>
+  const void* jacobian;      // large_jacobian_kernel<Model, T>
+  const void* adj_residual;  // large_adj_residual_kernel<Model>
+  const void* param;         // large_param_kernel<Model>
+};
+size_t large_workspace_bytes(int n, int P, int B, int chunk, int precision);
+cudaError_t large_forward(const LargeKernels& k, int n, int P, int precision, const FwdArgs& a,
+                          void* workspace, cudaStream_t s, int* host_worst);
+cudaError_t large_adjoint(const LargeKernels& k, int n, int P, int precision, const AdjArgs& a,
+                          void* workspace, cudaStream_t s);
 
 #endif  // __CUDACC_RTC__
 

@@ -9,10 +9,12 @@
 // side runs inside the same one-block-per-series solver as the built-in
 // models, with nothing but an inlined function call between them.
 //
-// The cubins are loaded as context-independent libraries (cudaLibraryLoadData)
-// and launched with the same argument blocks as the built-in kernels.  NVRTC is
-// opened with dlopen on first use: the library loads, and every other entry
-// point works, where NVRTC is absent.
+// Models with n > 4 use the large-state kernels instead (tvi_large_kernels.cuh,
+// one program per block precision) inside the Newton and adjoint loops of
+// tvi_large.cu.  The cubins are loaded as context-independent libraries
+// (cudaLibraryLoadData) and launched with the same argument blocks as the
+// built-in kernels.  NVRTC is opened with dlopen on first use: the library
+// loads, and every other entry point works, where NVRTC is absent.
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 #include <nvrtc.h>
@@ -50,6 +52,12 @@ struct tvi_user_model {
   std::string fwd_name[kPrecCount][kRptCount], adj_name[kPrecCount][kRptCount];
   cudaLibrary_t lib[kPrecCount][kRptCount];
   cudaKernel_t fwd[kPrecCount][kRptCount], adj[kPrecCount][kRptCount];
+  // large-state kernels (n > 4): residual, Jacobian, adjoint residual, parameter VJP
+  bool lcompiled[kPrecCount];
+  std::vector<char> lcubin[kPrecCount];
+  std::string lname[kPrecCount][4];
+  cudaLibrary_t llib[kPrecCount];
+  cudaKernel_t lk[kPrecCount][4];
 };
 
 namespace tvi {
@@ -170,6 +178,21 @@ struct TviUserModel {
           A[r][c] = fma(-dt, tvi::narrow<T>(J[r * NS + c]), r == c ? T(1) : T(0));
     }
   }
+  // J = dh/dy at (y, t), row-major n x n, in T (the large-state kernels)
+  template <typename T>
+  __device__ __forceinline__ void jacobian(const double (&y)[NS], double t, T* J) const {
+    if constexpr (TviTypedJac<T>::value) {
+      T yt[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) yt[s] = tvi::narrow<T>(y[s]);
+      tvi_jac(yt, t, p, J);
+    } else {
+      double Jd[NS * NS];
+      tvi_jac(y, t, p, Jd);
+#pragma unroll
+      for (int k = 0; k < NS * NS; ++k) J[k] = tvi::narrow<T>(Jd[k]);
+    }
+  }
   // acc += scale (dh/dp)^T a
   __device__ __forceinline__ void vjp_p(const double (&y)[NS], double t, const double (&a)[NS],
                                         double scale, double (&acc)[NP]) const {
@@ -196,16 +219,31 @@ __global__ void tvi_user_check(const double* y, double t, const double* p, const
 }
 )tvi_src";
 
+bool is_large(const tvi_user_model& m) { return m.n > kUserSmallMaxN; }
+
+// solver = false: the check kernel only; true: the adapter, with the kernel
+// templates of the model's route
 std::string program_text(const tvi_user_model& m, bool solver) {
   std::string s;
   s += "#define TVI_N " + std::to_string(m.n) + "\n";
   s += "#define TVI_P " + std::to_string(m.P) + "\n";
-  s += "#include \"tvi_small_kernels.cuh\"\n";
+  s += is_large(m) ? "#include \"tvi_large_kernels.cuh\"\n" : "#include \"tvi_small_kernels.cuh\"\n";
   s += "#line 1 \"user_model.cu\"\n";
   s += m.source;
   s += "\n#line 1 \"tvi_user_adapter.cu\"\n";
   s += solver ? kAdapter : kCheck;
   return s;
+}
+
+std::string large_kernel_name(int which, int precision) {
+  switch (which) {
+    case 0: return "tvi::klarge::large_residual_kernel<TviUserModel>";
+    case 1:
+      return std::string("tvi::klarge::large_jacobian_kernel<TviUserModel, ") +
+             (precision == kPrecFp64 ? "double>" : "float>");
+    case 2: return "tvi::klarge::large_adj_residual_kernel<TviUserModel>";
+    default: return "tvi::klarge::large_param_kernel<TviUserModel>";
+  }
 }
 
 std::string kernel_name(bool forward, int precision, int rpt) {
@@ -313,6 +351,54 @@ int kernels(const tvi_user_model* cm, int precision, int rpt, cudaKernel_t* fwd,
   return kJitOk;
 }
 
+// Compile the large-state kernels of one precision unless done; caller holds m->mu.
+int ensure_large_compiled(tvi_user_model* m, int pi, std::string* err) {
+  if (m->lcompiled[pi]) return kJitOk;
+  const int precision = pi == 0 ? kPrecFp64 : kPrecFp32;
+  std::vector<std::string> names;
+  for (int w = 0; w < 4; ++w) names.push_back(large_kernel_name(w, precision));
+  std::vector<std::string> low;
+  std::vector<char> cubin;
+  int rc = compile(program_text(*m, true), names, &cubin, &low, err);
+  if (rc != kJitOk) return rc;
+  m->lcubin[pi].swap(cubin);
+  for (int w = 0; w < 4; ++w) m->lname[pi][w] = low[w];
+  m->lcompiled[pi] = true;
+  return kJitOk;
+}
+
+int large_kernels(const tvi_user_model* cm, int precision, LargeKernels* out, std::string* err) {
+  tvi_user_model* m = const_cast<tvi_user_model*>(cm);
+  if (precision != kPrecFp64 && precision != kPrecFp32) {
+    *err = "user models run with FP64 or FP32 blocks";
+    return kJitCompile;
+  }
+  const int pi = precision == kPrecFp64 ? 0 : 1;
+  std::lock_guard<std::mutex> lock(m->mu);
+  if (!m->llib[pi]) {
+    int rc = ensure_large_compiled(m, pi, err);
+    if (rc != kJitOk) return rc;
+    cudaLibrary_t lib = nullptr;
+    cudaError_t e = cudaLibraryLoadData(&lib, m->lcubin[pi].data(), nullptr, nullptr, 0,
+                                        nullptr, nullptr, 0);
+    cudaKernel_t k[4] = {};
+    for (int w = 0; w < 4 && e == cudaSuccess; ++w)
+      e = cudaLibraryGetKernel(&k[w], lib, m->lname[pi][w].c_str());
+    if (e != cudaSuccess) {
+      if (lib) cudaLibraryUnload(lib);
+      *err = std::string("loading the user model's kernels: ") + cudaGetErrorString(e);
+      return kJitCuda;
+    }
+    for (int w = 0; w < 4; ++w) m->lk[pi][w] = k[w];
+    m->llib[pi] = lib;
+  }
+  out->residual = reinterpret_cast<const void*>(m->lk[pi][0]);
+  out->jacobian = reinterpret_cast<const void*>(m->lk[pi][1]);
+  out->adj_residual = reinterpret_cast<const void*>(m->lk[pi][2]);
+  out->param = reinterpret_cast<const void*>(m->lk[pi][3]);
+  return kJitOk;
+}
+
 }  // namespace
 
 bool user_valid(const tvi_user_model* m) { return m && m->magic == kUserMagic; }
@@ -325,12 +411,16 @@ int user_create(int n, int P, const char* source, tvi_user_model** out, std::str
   m->n = n;
   m->P = P;
   m->source = source;
-  for (int i = 0; i < kPrecCount; ++i)
+  for (int i = 0; i < kPrecCount; ++i) {
     for (int j = 0; j < kRptCount; ++j) {
       m->compiled[i][j] = false;
       m->lib[i][j] = nullptr;
       m->fwd[i][j] = m->adj[i][j] = nullptr;
     }
+    m->lcompiled[i] = false;
+    m->llib[i] = nullptr;
+    for (int w = 0; w < 4; ++w) m->lk[i][w] = nullptr;
+  }
   int rc = compile(program_text(*m, false), {}, nullptr, nullptr, err);
   if (rc != kJitOk) {
     m->magic = 0;
@@ -343,9 +433,11 @@ int user_create(int n, int P, const char* source, tvi_user_model** out, std::str
 
 void user_destroy(tvi_user_model* m) {
   if (!user_valid(m)) return;
-  for (int i = 0; i < kPrecCount; ++i)
+  for (int i = 0; i < kPrecCount; ++i) {
     for (int j = 0; j < kRptCount; ++j)
       if (m->lib[i][j]) cudaLibraryUnload(m->lib[i][j]);
+    if (m->llib[i]) cudaLibraryUnload(m->llib[i]);
+  }
   m->magic = 0;
   delete m;
 }
@@ -358,6 +450,7 @@ int user_prepare(tvi_user_model* m, int precision, std::string* err) {
   }
   const int pi = precision == kPrecFp64 ? 0 : 1;
   std::lock_guard<std::mutex> lock(m->mu);
+  if (is_large(*m)) return ensure_large_compiled(m, pi, err);
   int rc[kRptCount] = {kJitOk, kJitOk, kJitOk, kJitOk};
   std::string errs[kRptCount];
   std::vector<std::thread> pool;
@@ -402,6 +495,38 @@ int user_adjoint(const tvi_user_model* m, int precision, int rpt, int threads, c
   if (e == cudaSuccess && !a.per_series) e = small_sum_partials(a, m->P, s);
   if (e != cudaSuccess) {
     *err = std::string("user model adjoint launch: ") + cudaGetErrorString(e);
+    return kJitCuda;
+  }
+  return kJitOk;
+}
+
+bool user_large(const tvi_user_model* m) { return is_large(*m); }
+
+size_t user_workspace_bytes(const tvi_user_model* m, int B, int chunk, int precision) {
+  return large_workspace_bytes(m->n, m->P, B, chunk, precision);
+}
+
+int user_large_forward(const tvi_user_model* m, int precision, const FwdArgs& a, void* workspace,
+                       cudaStream_t s, int* host_worst, std::string* err) {
+  LargeKernels k{};
+  int rc = large_kernels(m, precision, &k, err);
+  if (rc != kJitOk) return rc;
+  cudaError_t e = large_forward(k, m->n, m->P, precision, a, workspace, s, host_worst);
+  if (e != cudaSuccess) {
+    *err = std::string("user model forward (large-state kernels): ") + cudaGetErrorString(e);
+    return kJitCuda;
+  }
+  return kJitOk;
+}
+
+int user_large_adjoint(const tvi_user_model* m, int precision, const AdjArgs& a, void* workspace,
+                       cudaStream_t s, std::string* err) {
+  LargeKernels k{};
+  int rc = large_kernels(m, precision, &k, err);
+  if (rc != kJitOk) return rc;
+  cudaError_t e = large_adjoint(k, m->n, m->P, precision, a, workspace, s);
+  if (e != cudaSuccess) {
+    *err = std::string("user model adjoint (large-state kernels): ") + cudaGetErrorString(e);
     return kJitCuda;
   }
   return kJitOk;

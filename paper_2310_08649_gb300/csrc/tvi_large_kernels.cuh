@@ -1,0 +1,177 @@
+// tvi_large_kernels.cuh -- the model-dependent kernels of user models with
+// 4 < n <= 32, compiled at run time together with the user's functions.
+//
+// Above n = 4 a step's n x n block no longer fits one thread's registers, so
+// these models take the large-state route of the MLP engine: every (series,
+// step) pair of the chunk is a thread here, the blocks are inverted by one warp
+// each and the chunk system is solved by block forward substitution
+// (mlp_chain_kernel; Thomas's algorithm, which the paper finds faster than PCR
+// for larger systems, Sec. 5.3).  One Newton iteration (Alg. 1):
+//   large_residual_kernel    R_j = dy_j - dy_{j-1} - dt_k h(y_i + dy_j, t_k) in
+//                            FP64, per-series max |R| (integer atomics on bits)
+//   large_jacobian_kernel    J = dh/dy at (y_j, t_k) in the block type into the
+//                            pair's block slot (inverted by user_invert_blocks)
+// and the adjoint (App. A.2), chunks in reverse over the stored trajectory:
+//   large_jacobian_kernel    (reverse rows) blocks for A^-T
+//   large_adj_residual_kernel  r_j = g_k + a_{j-1} - a_j + dt_k J^T a_j in FP64
+//                            (refinement of the mixed-precision solve)
+//   large_param_kernel       acc_b += sum_j dt_k (dh/dp)^T a_j, one block per
+//                            series, fixed summation order
+// Model is the adapter of the user's functions (tvi_jit.cu).
+#pragma once
+
+#include "tvi_device.cuh"
+#include "tvi_internal.h"
+
+namespace tvi {
+namespace klarge {
+
+constexpr int kLargeThreads = 128;
+
+__device__ __forceinline__ int step_index(int reverse, int i0, int L, int j) {
+  return reverse ? i0 + L - j : i0 + 1 + j;
+}
+
+__device__ __forceinline__ int series_len(const LargeArgs& a, int b) {
+  return a.lengths ? min(max(a.lengths[b], 0), a.N) : a.N;
+}
+
+// dt of step k; padded steps (k > len) have dt = 0 (identity rows)
+__device__ __forceinline__ double step_dt_of(const double* tb, int len, int k) {
+  return k <= len ? tb[k] - tb[k - 1] : 0.0;
+}
+
+template <class Model>
+__global__ void __launch_bounds__(kLargeThreads) large_residual_kernel(LargeArgs a) {
+  constexpr int NS = Model::NS;
+  const int b = blockIdx.y;
+  if (a.active && !a.active[b]) return;  // block-uniform
+  const int j = blockIdx.x * kLargeThreads + threadIdx.x;
+  unsigned long long mx = 0ull;
+  if (j < a.L) {
+    Model mdl;
+    mdl.load(a.params, b, a.per_series);
+    const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
+    const int k = a.i0 + 1 + j;
+    const double dt = step_dt_of(tb, series_len(a, b), k);
+    const double* yi = a.yi + static_cast<size_t>(b) * a.n4;
+    const double* dyj = a.dy + (static_cast<size_t>(b) * a.c + j) * a.n4;
+    double y[NS], h[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) y[s] = yi[s] + dyj[s];
+    mdl.rhs(y, tb[k], h);
+    double* Rj = a.R + (static_cast<size_t>(b) * a.c + j) * a.n4;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const double prev = j > 0 ? dyj[s - a.n4] : 0.0;
+      const double R = fma(-dt, h[s], dyj[s] - prev);
+      Rj[s] = R;
+      mx = umax64(mx, abs_bits(R));
+    }
+    for (int s = NS; s < a.n4; ++s) Rj[s] = 0.0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = umax64(mx, __shfl_xor_sync(kFull, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(a.norm + b, mx);
+}
+
+template <class Model, typename T>
+__global__ void __launch_bounds__(kLargeThreads) large_jacobian_kernel(LargeArgs a) {
+  constexpr int NS = Model::NS;
+  const int b = blockIdx.y;
+  if (a.active && !a.active[b]) return;
+  const int j = blockIdx.x * kLargeThreads + threadIdx.x;
+  if (j >= a.L) return;
+  Model mdl;
+  mdl.load(a.params, b, a.per_series);
+  const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
+  const int k = step_index(a.reverse, a.i0, a.L, j);
+  double y[NS];
+  if (a.reverse) {
+    const double* yk = a.ytraj + (static_cast<size_t>(b) * (a.N + 1) + k) * NS;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) y[s] = yk[s];
+  } else {
+    const double* yi = a.yi + static_cast<size_t>(b) * a.n4;
+    const double* dyj = a.dy + (static_cast<size_t>(b) * a.c + j) * a.n4;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) y[s] = yi[s] + dyj[s];
+  }
+  T* J = static_cast<T*>(a.J) + (static_cast<size_t>(b) * a.c + j) * a.n4 * a.n4;
+  mdl.template jacobian<T>(y, tb[k], J);
+}
+
+template <class Model>
+__global__ void __launch_bounds__(kLargeThreads) large_adj_residual_kernel(LargeArgs a) {
+  constexpr int NS = Model::NS;
+  const int b = blockIdx.y;
+  const int j = blockIdx.x * kLargeThreads + threadIdx.x;
+  if (j >= a.L) return;
+  Model mdl;
+  mdl.load(a.params, b, a.per_series);
+  const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
+  const int k = a.i0 + a.L - j;
+  const double dt = step_dt_of(tb, series_len(a, b), k);
+  double y[NS], J[NS * NS];
+  const double* yk = a.ytraj + (static_cast<size_t>(b) * (a.N + 1) + k) * NS;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) y[s] = yk[s];
+  mdl.template jacobian<double>(y, tb[k], J);
+  const double* aj = a.av + (static_cast<size_t>(b) * a.c + j) * a.n4;
+  const double* ap = j > 0 ? aj - a.n4 : a.carry + static_cast<size_t>(b) * a.n4;
+  const double* gk = a.g + (static_cast<size_t>(b) * (a.N + 1) + k) * NS;
+  double* rj = a.R + (static_cast<size_t>(b) * a.c + j) * a.n4;
+  for (int p = 0; p < NS; ++p) {
+    double s = 0.0;
+    for (int q = 0; q < NS; ++q) s = fma(J[q * NS + p], aj[q], s);  // (J^T a)_p
+    rj[p] = fma(dt, s, gk[p] + ap[p] - aj[p]);
+  }
+  for (int p = NS; p < a.n4; ++p) rj[p] = 0.0;
+}
+
+template <class Model>
+__global__ void __launch_bounds__(kLargeThreads) large_param_kernel(LargeArgs a) {
+  constexpr int NS = Model::NS;
+  constexpr int NP = Model::NP;
+  __shared__ double s_part[kLargeThreads / 32][NP];
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  Model mdl;
+  mdl.load(a.params, b, a.per_series);
+  const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
+  const int len = series_len(a, b);
+  double acc[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) acc[q] = 0.0;
+  for (int j = tid; j < a.L; j += kLargeThreads) {
+    const int k = a.i0 + a.L - j;
+    const double dt = step_dt_of(tb, len, k);
+    if (dt == 0.0) continue;
+    double y[NS], av[NS];
+    const double* yk = a.ytraj + (static_cast<size_t>(b) * (a.N + 1) + k) * NS;
+    const double* aj = a.av + (static_cast<size_t>(b) * a.c + j) * a.n4;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      y[s] = yk[s];
+      av[s] = aj[s];
+    }
+    mdl.vjp_p(y, tb[k], av, dt, acc);
+  }
+  // deterministic block sum: warp tree, then the warps in order
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    double v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (lane == 0) s_part[warp][q] = v;
+  }
+  __syncthreads();
+  if (tid < NP) {
+    double v = 0.0;
+    for (int w = 0; w < kLargeThreads / 32; ++w) v += s_part[w][tid];
+    a.acc[static_cast<size_t>(b) * NP + tid] += v;
+  }
+}
+
+}  // namespace klarge
+}  // namespace tvi

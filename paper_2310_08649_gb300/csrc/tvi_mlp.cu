@@ -924,18 +924,8 @@ __global__ void __launch_bounds__(kTcThreads) mlp_blocks_tc_kernel(BlocksArgs a,
 // of shared-memory slots by bulk copies, and d_{j-1} + rhs_j is broadcast
 // through shared memory.
 // ---------------------------------------------------------------------------
-struct ChainArgs {
-  int B, n, L, c, N, i0, reverse;
-  const void* M;           // [B][c][n][n] in T, each block transposed
-  const double* rhs_buf;   // [B][c][n] rhs by row, or null
-  const double* rhs_traj;  // [B][N+1][n] rhs by step (adjoint dL/dy), or null
-  const double* x_init;    // [B][n] d_{-1}, or null (zero)
-  const int* active;       // [B] or null
-  double* x;               // [B][c][n]
-  int mode;                // 0: x -= d   1: x = d   2: x += d
-  int* err;                // set when a bounded wait for staged data gives up
-};
-
+// (ChainArgs is declared in tvi_internal.h: the large-state user models use
+// this kernel too.)
 constexpr int kChainWarps = 4;
 constexpr int kChainWaitLimit = 1 << 22;
 
@@ -1531,7 +1521,71 @@ cudaError_t launch_chain(const ChainArgs& ch, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Gauss-Jordan inverse of A = I - dt J for user-model blocks: one warp per pair
+// of the chunk; the pair's slot holds J (n x n row-major, T) on entry and the
+// chain's block (n4 x n4, padded with the identity) on exit, as mlp_blocks_kernel
+// stores it.
+template <typename T>
+__global__ void __launch_bounds__(128) user_invert_kernel(int B, int N, int i0, int L, int c,
+                                                          int n, int n4, int reverse,
+                                                          const double* times, const int* lengths,
+                                                          const int* active, void* M) {
+  extern __shared__ __align__(16) unsigned char inv_smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.y;
+  const int j = blockIdx.x * 4 + warp;
+  if (j >= L || (active && !active[b])) return;  // warp-uniform
+  T* Ap = reinterpret_cast<T*>(inv_smem) + static_cast<size_t>(warp) * n4 * 2 * n4;
+  T* slot = static_cast<T*>(M) + (static_cast<size_t>(b) * c + j) * n4 * n4;
+  const int len = lengths ? min(max(lengths[b], 0), N) : N;
+  const T dt = static_cast<T>(step_dt(times + static_cast<size_t>(b) * (N + 1), len,
+                                      step_of(reverse, i0, L, j)));
+  for (int e = lane; e < n4 * n4; e += 32) {
+    const int r = e / n4, col = e - r * n4;
+    const T J = (r < n && col < n) ? slot[r * n + col] : T(0);
+    Ap[r * 2 * n4 + col] = fma(-dt, J, r == col ? T(1) : T(0));
+    Ap[r * 2 * n4 + n4 + col] = r == col ? T(1) : T(0);
+  }
+  __syncwarp();  // every read of J precedes the in-place store
+  gj_invert_store<T>(Ap, n4, lane, slot, reverse);
+}
+
 }  // namespace
+
+cudaError_t mlp_launch_chain(int precision, const ChainArgs& ch, cudaStream_t s) {
+  return precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s);
+}
+
+cudaError_t user_invert_blocks(int precision, int B, int N, int i0, int L, int c, int n, int n4,
+                               int reverse, const double* times, const int* lengths,
+                               const int* active, void* M, cudaStream_t s) {
+  const dim3 grid((L + 3) / 4, B);
+  const size_t tsz = precision == kPrecFp64 ? sizeof(double) : sizeof(float);
+  const size_t sm = 4 * tsz * n4 * 2 * n4;  // [A | I] per warp: up to 64 KB at n4 = 32, FP64
+  if (precision == kPrecFp64) {
+    cudaError_t e = set_smem(user_invert_kernel<double>, sm);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    user_invert_kernel<double><<<grid, 128, sm, s>>>(B, N, i0, L, c, n, n4, reverse, times,
+                                                     lengths, active, M);
+  } else {
+    cudaError_t e = set_smem(user_invert_kernel<float>, sm);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    user_invert_kernel<float><<<grid, 128, sm, s>>>(B, N, i0, L, c, n, n4, reverse, times,
+                                                    lengths, active, M);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_launch_check(int B, int it, int max_iter, double tol_abs, double tol_rel,
+                             unsigned long long* norm, double* norm0, int* active, int* status,
+                             int* iters, int* remaining, cudaStream_t s) {
+  CheckArgs ck{B, it, max_iter, tol_abs, tol_rel, norm, norm0, active, status, iters, remaining};
+  note_launch();
+  mlp_check_kernel<<<(B + 127) / 128, 128, 0, s>>>(ck);
+  return cudaGetLastError();
+}
 
 bool mlp_supported(int n, int h1, int h2) {
   const bool n_ok = n == 4 || n == 8 || n == 16 || n == 32;  // index math uses shifts

@@ -42,7 +42,13 @@ def users(tvi):
             "lin3": tvi.UserModel(3, 9, LINEAR),
             "mlp3": tvi.UserModel(3, mlp_param_count(3, 2, 2), mlp_tanh(2, 2)),
             "mds1": tvi.UserModel(2, mds_param_count(1), MDS),
-            "mds2": tvi.UserModel(4, mds_param_count(2), MDS)}
+            "mds2": tvi.UserModel(4, mds_param_count(2), MDS),
+            # n > 4: the large-state route
+            "mds3": tvi.UserModel(6, mds_param_count(3), MDS),
+            "mds5": tvi.UserModel(10, mds_param_count(5), MDS),
+            "mds10": tvi.UserModel(20, mds_param_count(10), MDS),
+            "lin5": tvi.UserModel(5, 25, LINEAR),
+            "mlp5": tvi.UserModel(5, mlp_param_count(5, 2, 1), mlp_tanh(2, 1))}
     yield made
     torch.cuda.synchronize()
     for u in made.values():
@@ -178,11 +184,14 @@ def test_user_forward_euler(tvi, users, oracle_lib, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("u,chunk", [(1, 100), (2, 1000), (2, 7)])
+@pytest.mark.parametrize("u,chunk", [(1, 100), (2, 1000), (2, 7), (3, 300), (5, 1000), (10, 64),
+                                     (10, 2000)])
 def test_user_mds_matches_oracle(tvi, users, oracle_lib, precision, u, chunk):
     """Time-dependent right-hand side (the forcing f_a sin(2 pi t / T)): the
     mass-damper-spring chain of the paper's timing study, per-series parameters
-    (table values, jittered so that series differ), zero initial state."""
+    (table values, jittered so that series differ), zero initial state.  Up to
+    2 units (n <= 4) on the fused small-state kernels, above on the large-state
+    route (n = 6, 10, 20: the paper's n_unit 3, 5, 10)."""
     w = workloads.mds(B=16, N=2000, n_unit=u, jitter=0.1, seed=70 + u)
     m = OModel.from_spec(w["spec"])
     ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], tol_abs=1e-18,
@@ -201,6 +210,67 @@ def test_user_mds_matches_oracle(tvi, users, oracle_lib, precision, u, chunk):
     e_p = np.abs(dp - dp_ref).max(axis=1) / np.abs(dp_ref).max(axis=1)
     assert e_p.max() <= GATE[precision], (e_p.argmax(), e_p.max())
     assert relerr(dy0, dy0_ref) <= GATE[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("which,chunk", [("lin5", 64), ("mlp5", 250)])
+def test_user_large_shared_params(tvi, users, oracle_lib, precision, which, chunk):
+    """Large-state route with shared parameters and a padded width (n = 5,
+    vectors padded to 8): a linear system and a nonlinear tanh MLP."""
+    if which == "lin5":
+        w = workloads.linear_stiff(B=8, N=500, n=5, lam_decades=(0.0, 3.0))
+    else:
+        w = workloads.mlp_ode(B=8, N=500, n=5, hidden=(2, 1), seed=73, t_end=5.0)
+        w["params"] = w["params"] + 0.3 * np.random.default_rng(74).standard_normal(
+            w["params"].shape)
+    m = OModel.from_spec(w["spec"])
+    ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], tol_abs=1e-13)
+    assert not st.any()
+    model = users[which].model(per_series=False)
+    o = tvi.Options(chunk=chunk, tol_abs=1e-13, precision=precision, adjoint_refine=2)
+    y, stats, status, rc = forward(tvi, model, w, o)
+    assert rc == 0 and not status.any()
+    assert relerr_series(y, ref).max() <= GATE[precision]
+    g = workloads.random_grad_out(75, 8, 500, 5)
+    dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g)
+    dp, dy0 = adjoint(tvi, model, w, o, ref, g)
+    assert relerr(dp, dp_ref) <= GATE[precision]
+    assert relerr(dy0, dy0_ref) <= GATE[precision]
+
+
+def test_user_large_padded_lengths_and_rejections(tvi, users, oracle_lib):
+    import paper_2310_08649_gb300._lib as L
+    w = workloads.mds(B=4, N=700, n_unit=3, jitter=0.1, seed=76)
+    lens = np.array([700, 1, 0, 333], dtype=np.int32)
+    m = OModel.from_spec(w["spec"])
+    ref, _, _ = oracle_lib.forward(m, w["y0"], w["times"], w["params"], lengths=lens,
+                                   tol_abs=1e-18, max_iter=4)
+    model = users["mds3"].model(per_series=True)
+    o = tvi.Options(chunk=128, tol_abs=1e-17, max_iter=20, precision="fp64")
+    y, _, status, rc = forward(tvi, model, w, o, lengths=lens)
+    assert rc == 0 and not status.any()
+    for b, L_ in enumerate(lens):
+        assert np.all(y[b, L_ + 1:] == y[b, L_])
+    assert relerr_series(y, ref).max() <= 1e-10
+    g = workloads.random_grad_out(77, 4, 700, 6)
+    for b, L_ in enumerate(lens):
+        g[b, L_ + 1:] = 0.0
+    dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g, lengths=lens)
+    dp, dy0 = adjoint(tvi, model, w, o, ref, g, lengths=lens)
+    e_p = np.abs(dp - dp_ref).max(axis=1) / np.maximum(np.abs(dp_ref).max(axis=1), 1e-300)
+    assert e_p.max() <= 1e-10 and relerr(dy0, dy0_ref) <= 1e-10
+    # forward Euler and the allocation-free adjoint are small-state features
+    with pytest.raises(L.TviError) as e:
+        forward_raise(tvi, model, w, tvi.Options(chunk=10, scheme="forward"))
+    assert e.value.code == -7
+    lib = L.load()
+    cm, co = model.c(), o.c()
+    T, P, Y, G = dev(w["times"]), dev(w["params"]), dev(ref), dev(g)
+    dpn = torch.empty_like(P)
+    rc = lib.tvi_adjoint_noalloc(ctypes.byref(cm), ctypes.byref(co), 4, 700, T.data_ptr(), None,
+                                 P.data_ptr(), Y.data_ptr(), G.data_ptr(), dpn.data_ptr(), None,
+                                 None)
+    assert rc == -7
 
 
 def test_user_padded_lengths_and_noalloc(tvi, users, oracle_lib):

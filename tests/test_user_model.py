@@ -6,8 +6,8 @@ import ctypes
 
 import pytest
 
-from paper_2310_08649_gb300.user_sources import LINEAR, VDP, VDP_FP64_JAC, mlp_param_count, \
-    mlp_tanh
+from paper_2310_08649_gb300.user_sources import LINEAR, MDS, VDP, VDP_FP64_JAC, \
+    mds_param_count, mlp_param_count, mlp_tanh
 
 tvi = pytest.importorskip("paper_2310_08649_gb300")
 from paper_2310_08649_gb300 import _lib  # noqa: E402
@@ -62,7 +62,7 @@ def test_missing_function_is_rejected(lib):
     assert rc == EINVAL and "tvi_vjp_p" in _lib.last_error()
 
 
-@pytest.mark.parametrize("n,P", [(0, 1), (5, 1), (2, 0), (2, 33), (-1, -1)])
+@pytest.mark.parametrize("n,P", [(0, 1), (33, 1), (2, 0), (2, 33), (-1, -1)])
 def test_bad_sizes(lib, n, P):
     rc, h = create(lib, n, P, VDP)
     assert rc == EINVAL and h.value is None
@@ -95,6 +95,19 @@ def test_prepare_both_jacobian_forms(lib, src):
     u = tvi.UserModel(2, 1, src)
     u.prepare("fp32")
     u.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_prepare_large_state_route(lib, precision):
+    """n > 4 compiles the large-state kernels: a time-dependent model with a
+    template Jacobian (mass-damper-spring, n = 20) and one with an FP64 Jacobian
+    and a padded width (linear, n = 5)."""
+    u = tvi.UserModel(20, mds_param_count(10), MDS)
+    u.prepare(precision)
+    u.close()
+    v = tvi.UserModel(5, 25, LINEAR)
+    v.prepare(precision)
+    v.close()
 
 
 def test_prepare_rejects_bf16(lib):
