@@ -49,8 +49,10 @@ WORKLOADS = {
     # the same van der Pol workload through a user model (device source compiled at run time)
     "vdp_user": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 128, "N": 10000,
                  "refine": 1},
-    # mass-damper-spring chain of the paper's timing study (2 units, 100 series, 2000
-    # steps) as a time-dependent user model; |v| <= 5e-3, residuals bottom out near 1e-18
+    # mass-damper-spring chain of the paper's timing study (--n-unit units, 100 series,
+    # 2000 steps) as a time-dependent user model; |v| <= 5e-3, residuals bottom out
+    # near 1e-18.  n_unit <= 2 runs on the fused small-state kernels, more on the
+    # large-state route (10 units, n = 20: the study's largest size)
     "mds_user": {"chunk": 1000, "precision": "fp32", "tol": 1e-17, "B": 100, "N": 2000,
                  "refine": 2},
     "node16": {"chunk": 200, "precision": "bf16", "tol": 1e-8, "B": 64, "N": 2000, "refine": 2},
@@ -76,6 +78,8 @@ def parse():
     ap.add_argument("--rpt", type=int, default=0, help="steps per thread (0 = library default)")
     ap.add_argument("--refine", type=int, default=None,
                     help="adjoint refinement sweeps (mixed precision)")
+    ap.add_argument("--n-unit", type=int, default=10,
+                    help="mass-damper-spring units (workload mds_user)")
     ap.add_argument("--B", type=int, default=None)
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--baseline-steps", type=int, default=5)
@@ -103,7 +107,7 @@ def make_workload(args, rank=0):
     elif args.workload == "vdp_pred":
         w = workloads.vdp(B=args.B, N=args.N, seed=PRED_EVAL_SEED + rank)
     elif args.workload == "mds_user":
-        w = workloads.mds(B=args.B, N=args.N, n_unit=2)  # the table's parameters, no draw
+        w = workloads.mds(B=args.B, N=args.N, n_unit=args.n_unit)  # the table's values
     elif args.workload == "node16":
         w = workloads.mlp_ode(B=args.B, N=args.N, seed=workloads.SEED_MLP + 1000 * rank)
     else:
@@ -142,9 +146,9 @@ def workload_config(args):
                         "(MLP 103-256-256-200)",
             "vdp_user": "van der Pol n=2 as a user model (device source compiled at run time), "
                         "mu log-uniform [10,1000], log-spaced steps",
-            "mds_user": "mass-damper-spring chain, 2 units (n=4), forcing f_a sin(2 pi t/T) with "
-                        "T linspace [0.01,1] over the series, as a user model; uniform steps on "
-                        "[0,1]",
+            "mds_user": f"mass-damper-spring chain, {args.n_unit} units (n={2 * args.n_unit}), "
+                        "forcing f_a sin(2 pi t/T) with T linspace [0.01,1] over the series, as a "
+                        "user model; uniform steps on [0,1]",
             "node16": "neural ODE n=16, MLP 16-64-64-16 tanh, uniform steps on [0,10]",
             "node32": "neural ODE n=32, MLP 32-128-128-32 SiLU, per-series lengths "
                       "U[2000,N] padded, uniform steps on [0,10]"}[args.workload]
@@ -302,14 +306,18 @@ def roofline(args, w, stats, fwd_ms, adj_ms, refine):
     nchk = stats[:, 1].astype(np.float64)
     spc = N / np.maximum(nchk, 1)  # steps per solved chunk
     if args.workload == "mds_user":
-        # residual: h of the 2-unit chain (two spring-damper forces 6, the two mass
-        # divisions and a difference 3, forcing sin, multiply, divide, add 4: 13) + R (8)
-        # = 21; update y -= d: 4.  Adjoint per step: per refinement sweep the residual
-        # (A^T a, 16 + 8) = 24, parameter VJP (3 per unit and force terms, sin, cos) 20
-        fwd_ops = float(np.sum(((upd + nchk) * 21.0 + upd * 4.0) * spc))
-        adj_ops = float(B * N * (refine * 24.0 + 20.0))
-        names = (f"forward_small_kernel<TviUserModel(mds),{args.precision}>",
-                 f"adjoint_small_kernel<TviUserModel(mds),{args.precision}>")
+        # u units, n = 2u.  Residual: h (per unit the spring-damper force 4, the force
+        # difference 1, the mass division 1; forcing sin, multiply, divide, add 4:
+        # 6u + 4) + R (2 per component: 4u) = 10u + 4; update y -= d: 2u.  Adjoint per
+        # step: per refinement sweep the residual (J^T a over the 4 non-zeros per unit
+        # row, 3 per component: 8u + 4u) = 12u, parameter VJP (per unit 12; sin, cos,
+        # 6) 12u + 6.  A division, sine or cosine counts as one operation.
+        u = args.n_unit
+        fwd_ops = float(np.sum(((upd + nchk) * (10.0 * u + 4.0) + upd * 2.0 * u) * spc))
+        adj_ops = float(B * N * (refine * 12.0 * u + 12.0 * u + 6.0))
+        route = "small" if u <= 2 else "large"
+        names = (f"tvi_integrate (user mds, {route}-state kernels, {args.precision})",
+                 f"tvi_adjoint (user mds, {route}-state kernels, {args.precision})")
     elif args.workload.startswith("vdp"):
         # residual on the stored iterate y: h (3) + R (4) = 7; update y -= d: 2
         fwd_ops = float(np.sum(((upd + nchk) * 7.0 + upd * 2.0) * spc))
@@ -381,7 +389,8 @@ def run_ours(args):
         model = user.model(per_series=True)
     elif args.workload == "mds_user":
         from paper_2310_08649_gb300.user_sources import MDS, mds_param_count
-        user = tvi.UserModel(4, mds_param_count(2), MDS).prepare(args.precision)
+        user = tvi.UserModel(2 * args.n_unit, mds_param_count(args.n_unit), MDS)
+        user.prepare(args.precision)
         if not args.no_chunk1:
             user.prepare("fp64")  # the chunk = 1 FP64 leg
         model = user.model(per_series=True)

@@ -93,7 +93,7 @@ struct LargeArgs {
   const double* av;         // [B][c][n4] adjoint rows (adjoint)
   const double* carry;      // [B][n4] adjoint of the step after the chunk (adjoint)
   double* R;                // [B][c][n4] residual rows (output)
-  void* J;                  // [B][c] slots of n4 x n4 T; J written n x n row-major
+  void* J;                  // [B][c] block slots of n4 x n4 T (the chain's M)
   double* acc;              // [B][P] gradient accumulators (adjoint)
   unsigned long long* norm; // [B] max |R| bits (forward)
   const int* active;        // [B] or null
@@ -155,17 +155,12 @@ cudaError_t mlp_launch_chain(int precision, const ChainArgs& ch, cudaStream_t s)
 cudaError_t mlp_launch_check(int B, int it, int max_iter, double tol_abs, double tol_rel,
                              unsigned long long* norm, double* norm0, int* active, int* status,
                              int* iters, int* remaining, cudaStream_t s);
-// M slot of each active pair: J (n x n) in, block (n4 x n4) of A = I - dt J out
-// (A^-1 stored transposed, or A^-T when reverse), as the chain reads it
-cudaError_t user_invert_blocks(int precision, int B, int N, int i0, int L, int c, int n, int n4,
-                               int reverse, const double* times, const int* lengths,
-                               const int* active, void* M, cudaStream_t s);
 
 // Large-state user models (tvi_large.cu): n in 5..32, the run-time compiled
 // kernels of tvi_large_kernels.cuh around the pieces above.
 struct LargeKernels {
   const void* residual;      // large_residual_kernel<Model>
-  const void* jacobian;      // large_jacobian_kernel<Model, T>
+  const void* block;         // large_block_kernel<Model, T, n4>
   const void* adj_residual;  // large_adj_residual_kernel<Model>
   const void* param;         // large_param_kernel<Model>
 };

@@ -235,12 +235,13 @@ std::string program_text(const tvi_user_model& m, bool solver) {
   return s;
 }
 
-std::string large_kernel_name(int which, int precision) {
+std::string large_kernel_name(int which, int precision, int n) {
   switch (which) {
     case 0: return "tvi::klarge::large_residual_kernel<TviUserModel>";
     case 1:
-      return std::string("tvi::klarge::large_jacobian_kernel<TviUserModel, ") +
-             (precision == kPrecFp64 ? "double>" : "float>");
+      return std::string("tvi::klarge::large_block_kernel<TviUserModel, ") +
+             (precision == kPrecFp64 ? "double, " : "float, ") + std::to_string((n + 3) / 4 * 4) +
+             ">";
     case 2: return "tvi::klarge::large_adj_residual_kernel<TviUserModel>";
     default: return "tvi::klarge::large_param_kernel<TviUserModel>";
   }
@@ -356,7 +357,7 @@ int ensure_large_compiled(tvi_user_model* m, int pi, std::string* err) {
   if (m->lcompiled[pi]) return kJitOk;
   const int precision = pi == 0 ? kPrecFp64 : kPrecFp32;
   std::vector<std::string> names;
-  for (int w = 0; w < 4; ++w) names.push_back(large_kernel_name(w, precision));
+  for (int w = 0; w < 4; ++w) names.push_back(large_kernel_name(w, precision, m->n));
   std::vector<std::string> low;
   std::vector<char> cubin;
   int rc = compile(program_text(*m, true), names, &cubin, &low, err);
@@ -393,7 +394,7 @@ int large_kernels(const tvi_user_model* cm, int precision, LargeKernels* out, st
     m->llib[pi] = lib;
   }
   out->residual = reinterpret_cast<const void*>(m->lk[pi][0]);
-  out->jacobian = reinterpret_cast<const void*>(m->lk[pi][1]);
+  out->block = reinterpret_cast<const void*>(m->lk[pi][1]);
   out->adj_residual = reinterpret_cast<const void*>(m->lk[pi][2]);
   out->param = reinterpret_cast<const void*>(m->lk[pi][3]);
   return kJitOk;

@@ -4,11 +4,11 @@
 //
 // Forward, per chunk (Alg. 1), all series at once, converged series skipped:
 //   residual (user) -> convergence check (mlp_launch_check; the host reads how
-//   many series still iterate) -> Jacobian (user) -> block inverses
-//   (user_invert_blocks) -> block forward substitution dy -= d (mlp_launch_chain)
+//   many series still iterate) -> blocks: Jacobian and inverse (user) -> block
+//   forward substitution dy -= d (mlp_launch_chain)
 // Adjoint (App. A.2), chunks in reverse: dL/dy rows gathered in row order ->
-// Jacobian at the trajectory (user) -> A^-T blocks -> a = substitution; FP64
-// refinement residuals (user) and corrections; parameter gradient (user).
+// A^-T blocks at the trajectory (user) -> a = substitution; FP64 refinement
+// residuals (user) and corrections; parameter gradient (user).
 // State vectors are padded to n4 = 4 ceil(n / 4) (the chain's vector width).
 #include <cuda_runtime.h>
 
@@ -160,6 +160,9 @@ cudaError_t launch_user(const void* kernel, dim3 grid, const LargeArgs& a, cudaS
   return cudaLaunchKernel(kernel, grid, dim3(kThreads), params, 0, s);
 }
 
+// the block kernel: one warp per pair, four pairs per block
+dim3 block_grid(int L, int B) { return dim3((L + 3) / 4, B); }
+
 #define TVI_TRY(x)                    \
   do {                                \
     cudaError_t e_ = (x);             \
@@ -208,9 +211,7 @@ cudaError_t large_forward(const LargeKernels& k, int n, int P, int precision, co
       TVI_TRY(cudaMemcpyAsync(&remaining, w.remaining, sizeof(int), cudaMemcpyDeviceToHost, s));
       TVI_TRY(cudaStreamSynchronize(s));
       if (remaining == 0) break;
-      TVI_TRY(launch_user(k.jacobian, grid, la, s));
-      TVI_TRY(user_invert_blocks(precision, B, N, i0, L, c, n, n4, 0, a.times, a.lengths,
-                                 w.active, w.M, s));
+      TVI_TRY(launch_user(k.block, block_grid(L, B), la, s));
       ChainArgs ch{};
       ch.B = B; ch.n = n4; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 0; ch.M = w.M;
       ch.rhs_buf = w.R; ch.active = w.active; ch.x = w.dy; ch.mode = 0; ch.err = w.err;
@@ -255,9 +256,7 @@ cudaError_t large_adjoint(const LargeKernels& k, int n, int P, int precision, co
     large_gather_kernel<<<blocks_for(static_cast<size_t>(B) * L * n4, 256), 256, 0, s>>>(
         B, n, n4, N, i0, L, c, a.grad_out, w.R);
     TVI_TRY(cudaGetLastError());
-    TVI_TRY(launch_user(k.jacobian, grid, la, s));
-    TVI_TRY(user_invert_blocks(precision, B, N, i0, L, c, n, n4, 1, a.times, a.lengths, nullptr,
-                               w.M, s));
+    TVI_TRY(launch_user(k.block, block_grid(L, B), la, s));
     // a_j = A^-T (a_{j-1} + g_k), a_{-1} = carry
     ChainArgs ch{};
     ch.B = B; ch.n = n4; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 1; ch.M = w.M;

@@ -9,10 +9,10 @@
 // for larger systems, Sec. 5.3).  One Newton iteration (Alg. 1):
 //   large_residual_kernel    R_j = dy_j - dy_{j-1} - dt_k h(y_i + dy_j, t_k) in
 //                            FP64, per-series max |R| (integer atomics on bits)
-//   large_jacobian_kernel    J = dh/dy at (y_j, t_k) in the block type into the
-//                            pair's block slot (inverted by user_invert_blocks)
+//   large_block_kernel       J = dh/dy at (y_j, t_k) in the block type, A = I -
+//                            dt J inverted in registers (one warp per pair)
 // and the adjoint (App. A.2), chunks in reverse over the stored trajectory:
-//   large_jacobian_kernel    (reverse rows) blocks for A^-T
+//   large_block_kernel       (reverse rows) the A^-T blocks
 //   large_adj_residual_kernel  r_j = g_k + a_{j-1} - a_j + dt_k J^T a_j in FP64
 //                            (refinement of the mixed-precision solve)
 //   large_param_kernel       acc_b += sum_j dt_k (dh/dp)^T a_j, one block per
@@ -75,30 +75,91 @@ __global__ void __launch_bounds__(kLargeThreads) large_residual_kernel(LargeArgs
   if ((threadIdx.x & 31) == 0 && mx) atomicMax(a.norm + b, mx);
 }
 
-template <class Model, typename T>
-__global__ void __launch_bounds__(kLargeThreads) large_jacobian_kernel(LargeArgs a) {
+// Block of pair j: A = I - dt_k J(y_j, t_k) inverted by Gauss-Jordan with
+// partial pivoting, one warp per pair, stored in the pair's slot as the chain
+// reads it (A^-1 transposed; A^-T when reverse), padded to N4 with the identity.
+// Lane 0 evaluates J into shared memory; lane r < N4 then keeps row r of
+// [A | I] in registers.  Pivoting without row swaps: step k takes the unused
+// row of largest |A[r][k]| (a butterfly argmax, first of equal maxima), the
+// pivot row is broadcast by shuffles, and every row takes one FMA per entry:
+// row_r -= (A[r][k] / piv) row_p, and the pivot row -= (1 - 1 / piv) itself,
+// which scales it.  The row that pivoted at step k holds row k of A^-1 in its
+// right half.  The result leaves through shared memory (coalesced stores).
+template <class Model, typename T, int N4>
+__global__ void __launch_bounds__(128) large_block_kernel(LargeArgs a) {
   constexpr int NS = Model::NS;
+  constexpr int LD = N4 + 1;  // padded row stride of the staging buffer
+  __shared__ T s_buf[4][N4 * LD];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int b = blockIdx.y;
-  if (a.active && !a.active[b]) return;
-  const int j = blockIdx.x * kLargeThreads + threadIdx.x;
-  if (j >= a.L) return;
-  Model mdl;
-  mdl.load(a.params, b, a.per_series);
+  const int j = blockIdx.x * 4 + warp;
+  if (j >= a.L || (a.active && !a.active[b])) return;  // warp-uniform
+  T* buf = s_buf[warp];
   const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
   const int k = step_index(a.reverse, a.i0, a.L, j);
-  double y[NS];
-  if (a.reverse) {
-    const double* yk = a.ytraj + (static_cast<size_t>(b) * (a.N + 1) + k) * NS;
+  const T dt = static_cast<T>(step_dt_of(tb, series_len(a, b), k));
+  if (lane == 0) {
+    Model mdl;
+    mdl.load(a.params, b, a.per_series);
+    double y[NS];
+    if (a.reverse) {
+      const double* yk = a.ytraj + (static_cast<size_t>(b) * (a.N + 1) + k) * NS;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) y[s] = yk[s];
-  } else {
-    const double* yi = a.yi + static_cast<size_t>(b) * a.n4;
-    const double* dyj = a.dy + (static_cast<size_t>(b) * a.c + j) * a.n4;
+      for (int s = 0; s < NS; ++s) y[s] = yk[s];
+    } else {
+      const double* yi = a.yi + static_cast<size_t>(b) * a.n4;
+      const double* dyj = a.dy + (static_cast<size_t>(b) * a.c + j) * a.n4;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) y[s] = yi[s] + dyj[s];
+      for (int s = 0; s < NS; ++s) y[s] = yi[s] + dyj[s];
+    }
+    mdl.template jacobian<T>(y, tb[k], buf);  // J, NS x NS row-major
   }
-  T* J = static_cast<T*>(a.J) + (static_cast<size_t>(b) * a.c + j) * a.n4 * a.n4;
-  mdl.template jacobian<T>(y, tb[k], J);
+  __syncwarp();
+  T row[2 * N4];
+#pragma unroll
+  for (int q = 0; q < N4; ++q) {
+    const T Jv = (lane < NS && q < NS) ? buf[lane * NS + q] : T(0);
+    row[q] = lane < N4 ? fma(-dt, Jv, lane == q ? T(1) : T(0)) : T(0);
+    row[N4 + q] = lane == q ? T(1) : T(0);
+  }
+  __syncwarp();  // buf is reused for the result
+  bool used = lane >= N4;  // lanes without a row never pivot
+  int myk = 0;
+#pragma unroll
+  for (int kk = 0; kk < N4; ++kk) {
+    const T x = fabs(row[kk]);
+    // NaN rows sort high (and stay NaN): every lane then agrees on the pivot
+    T v = used ? T(-1) : (x == x ? x : static_cast<T>(__int_as_float(0x7f800000)));
+    int p = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(kFull, v, o);
+      const int op = __shfl_xor_sync(kFull, p, o);
+      if (ov > v || (ov == v && op < p)) {
+        v = ov;
+        p = op;
+      }
+    }
+    if (lane == p) {
+      used = true;
+      myk = kk;
+    }
+    const T inv = T(1) / __shfl_sync(kFull, row[kk], p);
+    const T f = lane == p ? T(1) - inv : row[kk] * inv;
+#pragma unroll
+    for (int q = 0; q < 2 * N4; ++q) row[q] = fma(-f, __shfl_sync(kFull, row[q], p), row[q]);
+  }
+  if (lane < N4) {
+#pragma unroll
+    for (int q = 0; q < N4; ++q) buf[myk * LD + q] = row[N4 + q];  // A^-1[myk][q]
+  }
+  __syncwarp();
+  T* slot = static_cast<T*>(a.J) + (static_cast<size_t>(b) * a.c + j) * N4 * N4;
+  for (int i = lane; i < N4 * N4; i += 32) {
+    const int r = i / N4, q = i - r * N4;
+    // forward: slot[r][q] = A^-1[q][r] (transposed); reverse: slot[r][q] = A^-1[r][q]
+    slot[i] = a.reverse ? buf[r * LD + q] : buf[q * LD + r];
+  }
 }
 
 template <class Model>

@@ -927,98 +927,133 @@ __global__ void __launch_bounds__(kTcThreads) mlp_blocks_tc_kernel(BlocksArgs a,
 // (ChainArgs is declared in tvi_internal.h: the large-state user models use
 // this kernel too.)
 constexpr int kChainWarps = 4;
+constexpr int kChainOneWarpMaxSeries = 256;
 constexpr int kChainWaitLimit = 1 << 22;
 
-template <typename T>
-size_t chain_slot_bytes(int n) {
-  return sizeof(T) * n * n + 2 * sizeof(double) * n;
+// ring slot: the block (N x N in T), the rhs row and the x row (FP64)
+template <typename T, int N>
+constexpr size_t chain_slot_bytes() {
+  return sizeof(T) * N * N + 2 * sizeof(double) * N;
+}
+// the deepest ring (64 .. 4 steps) whose W warps fit in 200 KB: half a ring's
+// copies are in flight while the other half is consumed
+template <typename T, int N, int W>
+constexpr int chain_depth() {
+  return W * 64 * chain_slot_bytes<T, N>() <= 200 * 1024   ? 64
+         : W * 32 * chain_slot_bytes<T, N>() <= 200 * 1024 ? 32
+         : W * 16 * chain_slot_bytes<T, N>() <= 200 * 1024 ? 16
+         : W * 8 * chain_slot_bytes<T, N>() <= 200 * 1024  ? 8
+                                                            : 4;
 }
 
 // Lane 0 of each warp stages step j's block, rhs row and x row into ring slot
-// j % D with bulk copies (the TMA unit) that complete on the slot's mbarrier;
-// the warp waits on the barrier's phase (j / D) & 1 for step j.  Every source is
-// 16-byte aligned and every size a multiple of 16 (n even; workspace buffers by
-// construction, caller arrays checked by the C ABI).
-template <typename T, int D>
-__global__ void __launch_bounds__(32 * kChainWarps) mlp_chain_kernel(ChainArgs a) {
+// j % D with bulk copies (the TMA unit) that complete on the mbarrier of the
+// slot's half of the ring.  Every source is 16-byte aligned and every size a
+// multiple of 16 (N a multiple of 4; workspace buffers by construction, caller
+// arrays checked by the C ABI).  The width N is a template parameter so the
+// mat-vec unrolls: the block's column loads do not depend on d_{j-1} and are
+// issued before it, leaving one shared-memory round trip and N/4 dependent
+// FMAs on the step-to-step path.
+template <typename T, int N, int W>
+__global__ void __launch_bounds__(32 * W) mlp_chain_kernel(ChainArgs a) {
+  constexpr int D = chain_depth<T, N, W>();
+  constexpr int H = D / 2;
+  constexpr uint32_t mbytes = static_cast<uint32_t>(sizeof(T) * N * N);
+  constexpr uint32_t vbytes = static_cast<uint32_t>(sizeof(double) * N);
+  constexpr size_t slot_bytes = chain_slot_bytes<T, N>();
   extern __shared__ __align__(16) unsigned char chain_smem[];
-  __shared__ T s_u[kChainWarps][32];
-  __shared__ __align__(8) uint64_t s_bar[kChainWarps][D];
+  __shared__ T s_u[W][32];
+  __shared__ __align__(8) uint64_t s_bar[W][2];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.x * kChainWarps + wib;
+  const int b = blockIdx.x * W + wib;
   // warp-uniform exit: the kernel synchronises only within a warp
   if (b >= a.B || (a.active && !a.active[b])) return;
-  const int n = a.n;
-  const bool own = lane < n;
-  const uint32_t mbytes = static_cast<uint32_t>(sizeof(T) * n * n);
-  const uint32_t vbytes = static_cast<uint32_t>(sizeof(double) * n);
-  const size_t slot_bytes = mbytes + 2 * vbytes;
+  const bool own = lane < N;
   unsigned char* ring = chain_smem + static_cast<size_t>(wib) * D * slot_bytes;
   uint64_t* bars = s_bar[wib];
   const unsigned char* Mb = static_cast<const unsigned char*>(a.M) +
                             static_cast<size_t>(b) * a.c * mbytes;
-  double* xb = a.x + static_cast<size_t>(b) * a.c * n;
+  double* xb = a.x + static_cast<size_t>(b) * a.c * N;
   T* su = s_u[wib];
   if (lane == 0)
-    for (int k = 0; k < D; ++k) tc::mbar_init(&bars[k], 1);
+    for (int k = 0; k < 2; ++k) tc::mbar_init(&bars[k], 1);
   __syncwarp();
-  auto issue = [&](int j) {  // lane 0: stage step j into slot j % D
-    if (lane != 0 || j >= a.L) return;
-    unsigned char* slot = ring + static_cast<size_t>(j % D) * slot_bytes;
-    const double* gr =
-        a.rhs_buf ? a.rhs_buf + (static_cast<size_t>(b) * a.c + j) * n
-                  : a.rhs_traj + (static_cast<size_t>(b) * (a.N + 1) +
-                                  step_of(a.reverse, a.i0, a.L, j)) * n;
-    tc::fence_smem_to_async();  // the warp's reads of this slot precede the refill
-    tc::mbar_expect_tx(&bars[j % D], mbytes + vbytes + (a.mode != 1 ? vbytes : 0u));
-    tc::bulk_g2s(slot, Mb + static_cast<size_t>(j) * mbytes, mbytes, &bars[j % D]);
-    tc::bulk_g2s(slot + mbytes, gr, vbytes, &bars[j % D]);
-    if (a.mode != 1)
-      tc::bulk_g2s(slot + mbytes + vbytes, xb + static_cast<size_t>(j) * n, vbytes, &bars[j % D]);
+  // The ring is two halves of H steps, each with one mbarrier: a half is staged
+  // by one fence, one expect_tx and its steps' bulk copies, waited on once, and
+  // refilled with the steps D later as soon as its last step is used.
+  const uint32_t step_bytes = mbytes + vbytes + (a.mode != 1 ? vbytes : 0u);
+  unsigned ph = 0u;    // bit h: parity of half h's next phase
+  unsigned pend = 0u;  // bit h: half h staged and not yet waited on
+  auto issue_half = [&](int j0) {  // warp-uniform: stage steps j0 .. j0 + H - 1
+    const int cnt = min(H, a.L - j0);
+    if (cnt <= 0) return;
+    const int h = (j0 % D) / H;
+    pend |= 1u << h;
+    if (lane != 0) return;
+    tc::fence_smem_to_async();  // the warp's reads of these slots precede the refill
+    tc::mbar_expect_tx(&bars[h], step_bytes * static_cast<uint32_t>(cnt));
+    for (int q = 0; q < cnt; ++q) {
+      const int j = j0 + q;
+      unsigned char* slot = ring + static_cast<size_t>(j % D) * slot_bytes;
+      const double* gr =
+          a.rhs_buf ? a.rhs_buf + (static_cast<size_t>(b) * a.c + j) * N
+                    : a.rhs_traj + (static_cast<size_t>(b) * (a.N + 1) +
+                                    step_of(a.reverse, a.i0, a.L, j)) * N;
+      tc::bulk_g2s(slot, Mb + static_cast<size_t>(j) * mbytes, mbytes, &bars[h]);
+      tc::bulk_g2s(slot + mbytes, gr, vbytes, &bars[h]);
+      if (a.mode != 1)
+        tc::bulk_g2s(slot + mbytes + vbytes, xb + static_cast<size_t>(j) * N, vbytes, &bars[h]);
+    }
   };
-#pragma unroll 1
-  for (int j = 0; j < D; ++j) issue(j);
-  T dprev = (a.x_init && own) ? narrow<T>(a.x_init[b * n + lane]) : T(0);
-  int done = 0;  // steps whose staged data has been consumed
+  issue_half(0);
+  issue_half(H);
+  T dprev = (a.x_init && own) ? static_cast<T>(a.x_init[b * N + lane]) : T(0);
 #pragma unroll 1
   for (int j = 0; j < a.L; ++j) {
-    const bool ok = __all_sync(kFull, tc::mbar_wait_bounded(&bars[j % D], (j / D) & 1,
-                                                           kChainWaitLimit));
-    if (!ok) {
-      if (lane == 0) atomicExch(a.err, 1);
-      break;
+    if (j % H == 0) {
+      const int h = (j % D) / H;
+      const bool ok =
+          __all_sync(kFull, tc::mbar_wait_bounded(&bars[h], (ph >> h) & 1u, kChainWaitLimit));
+      if (!ok) {
+        if (lane == 0) atomicExch(a.err, 1);
+        break;
+      }
+      ph ^= 1u << h;
+      pend &= ~(1u << h);
     }
     const unsigned char* slot = ring + static_cast<size_t>(j % D) * slot_bytes;
-    const T* Mt = reinterpret_cast<const T*>(slot);  // Mt[q * n + r] = M_j[r][q]
+    const T* Mt = reinterpret_cast<const T*>(slot);  // Mt[q * N + r] = M_j[r][q]
     const double* rr = reinterpret_cast<const double*>(slot + mbytes);
-    const double r_cur = own ? rr[lane] : 0.0;
-    const double x_cur = (own && a.mode != 1) ? rr[n + lane] : 0.0;
-    su[lane] = dprev + narrow<T>(r_cur);  // component `lane` of d_{j-1} + rhs_j
+    // independent of d_{j-1}: row `lane` of M_j, the rhs and the x entry
+    T m[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) m[q] = own ? Mt[q * N + lane] : T(0);
+    const T rc = own ? static_cast<T>(rr[lane]) : T(0);
+    const double x_cur = (own && a.mode != 1) ? rr[N + lane] : 0.0;
+    su[lane] = dprev + rc;  // component `lane` of d_{j-1} + rhs_j
     __syncwarp();
     T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
-    if (own) {
-      for (int q = 0; q < n; q += 4) {
-        acc0 = fma(Mt[q * n + lane], su[q], acc0);
-        acc1 = fma(Mt[(q + 1) * n + lane], su[q + 1], acc1);
-        acc2 = fma(Mt[(q + 2) * n + lane], su[q + 2], acc2);
-        acc3 = fma(Mt[(q + 3) * n + lane], su[q + 3], acc3);
-      }
+#pragma unroll
+    for (int q = 0; q < N; q += 4) {
+      acc0 = fma(m[q], su[q], acc0);
+      acc1 = fma(m[q + 1], su[q + 1], acc1);
+      acc2 = fma(m[q + 2], su[q + 2], acc2);
+      acc3 = fma(m[q + 3], su[q + 3], acc3);
     }
-    __syncwarp();  // slot j % D and su are free again
-    done = j + 1;
-    issue(j + D);
+    __syncwarp();  // su and (at a half's end) its slots are free again
+    if (j % H == H - 1) issue_half(j + 1 - H + D);
     const T acc = (acc0 + acc1) + (acc2 + acc3);
     dprev = own ? acc : T(0);
     if (own) {
-      const double dd = widen<T>(acc);
-      xb[static_cast<size_t>(j) * n + lane] =
+      const double dd = static_cast<double>(acc);
+      xb[static_cast<size_t>(j) * N + lane] =
           (a.mode == 0) ? x_cur - dd : (a.mode == 1 ? dd : x_cur + dd);
     }
   }
-  // after a timeout: give the copies still in flight (steps done .. done + D - 1)
-  // a second bounded wait before the block's shared memory goes away
-  for (int j = done; j < a.L && j < done + D; ++j)
-    tc::mbar_wait_bounded(&bars[j % D], (j / D) & 1, kChainWaitLimit);
+  // after a timeout: give the halves still in flight a second bounded wait
+  // before the block's shared memory goes away
+  for (int h = 0; h < 2; ++h)
+    if ((pend >> h) & 1u) tc::mbar_wait_bounded(&bars[h], (ph >> h) & 1u, kChainWaitLimit);
 }
 
 // ---------------------------------------------------------------------------
@@ -1500,82 +1535,44 @@ cudaError_t launch_blocks_any(const BlocksArgs& bk, int precision, int* err, cud
   return launch_blocks<float>(bk, precision, s);
 }
 
-template <typename T>
-cudaError_t launch_chain(const ChainArgs& ch, cudaStream_t s) {
-  // ring depth 8 when four warps' rings fit in 200 KB, else 4
-  const size_t slot = chain_slot_bytes<T>(ch.n);
-  const dim3 grid((ch.B + kChainWarps - 1) / kChainWarps);
-  if (kChainWarps * 8 * slot <= 200 * 1024) {
-    const size_t sm = kChainWarps * 8 * slot;
-    cudaError_t e = set_smem(mlp_chain_kernel<T, 8>, sm);
-    if (e != cudaSuccess) return e;
-    note_launch();
-    mlp_chain_kernel<T, 8><<<grid, 32 * kChainWarps, sm, s>>>(ch);
-  } else {
-    const size_t sm = kChainWarps * 4 * slot;
-    cudaError_t e = set_smem(mlp_chain_kernel<T, 4>, sm);
-    if (e != cudaSuccess) return e;
-    note_launch();
-    mlp_chain_kernel<T, 4><<<grid, 32 * kChainWarps, sm, s>>>(ch);
-  }
+template <typename T, int N, int W>
+cudaError_t launch_chain_n(const ChainArgs& ch, cudaStream_t s) {
+  const dim3 grid((ch.B + W - 1) / W);
+  const size_t sm = static_cast<size_t>(W) * chain_depth<T, N, W>() * chain_slot_bytes<T, N>();
+  cudaError_t e = set_smem(mlp_chain_kernel<T, N, W>, sm);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  mlp_chain_kernel<T, N, W><<<grid, 32 * W, sm, s>>>(ch);
   return cudaGetLastError();
 }
 
-// Gauss-Jordan inverse of A = I - dt J for user-model blocks: one warp per pair
-// of the chunk; the pair's slot holds J (n x n row-major, T) on entry and the
-// chain's block (n4 x n4, padded with the identity) on exit, as mlp_blocks_kernel
-// stores it.
-template <typename T>
-__global__ void __launch_bounds__(128) user_invert_kernel(int B, int N, int i0, int L, int c,
-                                                          int n, int n4, int reverse,
-                                                          const double* times, const int* lengths,
-                                                          const int* active, void* M) {
-  extern __shared__ __align__(16) unsigned char inv_smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.y;
-  const int j = blockIdx.x * 4 + warp;
-  if (j >= L || (active && !active[b])) return;  // warp-uniform
-  T* Ap = reinterpret_cast<T*>(inv_smem) + static_cast<size_t>(warp) * n4 * 2 * n4;
-  T* slot = static_cast<T*>(M) + (static_cast<size_t>(b) * c + j) * n4 * n4;
-  const int len = lengths ? min(max(lengths[b], 0), N) : N;
-  const T dt = static_cast<T>(step_dt(times + static_cast<size_t>(b) * (N + 1), len,
-                                      step_of(reverse, i0, L, j)));
-  for (int e = lane; e < n4 * n4; e += 32) {
-    const int r = e / n4, col = e - r * n4;
-    const T J = (r < n && col < n) ? slot[r * n + col] : T(0);
-    Ap[r * 2 * n4 + col] = fma(-dt, J, r == col ? T(1) : T(0));
-    Ap[r * 2 * n4 + n4 + col] = r == col ? T(1) : T(0);
+template <typename T, int W>
+cudaError_t launch_chain_w(const ChainArgs& ch, cudaStream_t s) {
+  switch (ch.n) {
+    case 4: return launch_chain_n<T, 4, W>(ch, s);
+    case 8: return launch_chain_n<T, 8, W>(ch, s);
+    case 12: return launch_chain_n<T, 12, W>(ch, s);
+    case 16: return launch_chain_n<T, 16, W>(ch, s);
+    case 20: return launch_chain_n<T, 20, W>(ch, s);
+    case 24: return launch_chain_n<T, 24, W>(ch, s);
+    case 28: return launch_chain_n<T, 28, W>(ch, s);
+    case 32: return launch_chain_n<T, 32, W>(ch, s);
+    default: return cudaErrorInvalidValue;
   }
-  __syncwarp();  // every read of J precedes the in-place store
-  gj_invert_store<T>(Ap, n4, lane, slot, reverse);
+}
+
+// One warp per series.  With few series, one warp per block spreads them over
+// as many SMs; with many, four per block.
+template <typename T>
+cudaError_t launch_chain(const ChainArgs& ch, cudaStream_t s) {
+  return ch.B <= kChainOneWarpMaxSeries ? launch_chain_w<T, 1>(ch, s)
+                                        : launch_chain_w<T, kChainWarps>(ch, s);
 }
 
 }  // namespace
 
 cudaError_t mlp_launch_chain(int precision, const ChainArgs& ch, cudaStream_t s) {
   return precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s);
-}
-
-cudaError_t user_invert_blocks(int precision, int B, int N, int i0, int L, int c, int n, int n4,
-                               int reverse, const double* times, const int* lengths,
-                               const int* active, void* M, cudaStream_t s) {
-  const dim3 grid((L + 3) / 4, B);
-  const size_t tsz = precision == kPrecFp64 ? sizeof(double) : sizeof(float);
-  const size_t sm = 4 * tsz * n4 * 2 * n4;  // [A | I] per warp: up to 64 KB at n4 = 32, FP64
-  if (precision == kPrecFp64) {
-    cudaError_t e = set_smem(user_invert_kernel<double>, sm);
-    if (e != cudaSuccess) return e;
-    note_launch();
-    user_invert_kernel<double><<<grid, 128, sm, s>>>(B, N, i0, L, c, n, n4, reverse, times,
-                                                     lengths, active, M);
-  } else {
-    cudaError_t e = set_smem(user_invert_kernel<float>, sm);
-    if (e != cudaSuccess) return e;
-    note_launch();
-    user_invert_kernel<float><<<grid, 128, sm, s>>>(B, N, i0, L, c, n, n4, reverse, times,
-                                                    lengths, active, M);
-  }
-  return cudaGetLastError();
 }
 
 cudaError_t mlp_launch_check(int B, int it, int max_iter, double tol_abs, double tol_rel,
