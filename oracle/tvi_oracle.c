@@ -27,6 +27,7 @@ int tvo_param_count(const tvo_model* m) {
     case TVO_LINEAR: return m->n * m->n;
     case TVO_VDP: return m->n == 2 ? 1 : -1;
     case TVO_MDS: return m->n % 2 == 0 ? 3 * (m->n / 2) + 2 : -1;
+    case TVO_CHABOCHE: return m->n >= 3 ? 2 * (m->n - 2) + 8 : -1;
     case TVO_MLP_TANH:
     case TVO_MLP_SILU:
       if (m->h1 <= 0 || m->h2 <= 0) return -1;
@@ -113,8 +114,46 @@ static double mds_force(int u, const double* p, const double* y, int i) {
 
 static const double kTwoPi = 6.283185307179586476925286766559;
 
+/* Chaboche: the plastic strain rate ep and its derivatives.  With s = sigma -
+ * sum X and f = (|s| - K - sigma_0) / eta: ep = max(f, 0)^m sign(s); for f > 0
+ * d ep / d s = (m / eta) f^(m-1), d ep / d K = -(m / eta) f^(m-1) sign(s),
+ * d|ep| / d s = (m / eta) f^(m-1) sign(s), d|ep| / d K = -(m / eta) f^(m-1);
+ * all zero for f <= 0 (elastic). */
+typedef struct {
+  double s, sgn, f, ep, aep, d;  /* d = (m / eta) f^(m-1) when f > 0, else 0 */
+} chab_flow;
+
+static chab_flow chab_eval(int u, const double* p, const double* y) {
+  chab_flow c;
+  double sumX = 0.0;
+  for (int i = 0; i < u; ++i) sumX += y[2 + i];
+  c.s = y[0] - sumX;
+  c.sgn = (c.s > 0.0) ? 1.0 : ((c.s < 0.0) ? -1.0 : 0.0);
+  const double mexp = p[1], eta = p[2], sigma0 = p[3];
+  c.f = (fabs(c.s) - y[1] - sigma0) / eta;
+  if (c.f > 0.0) {
+    c.aep = pow(c.f, mexp);
+    c.d = mexp / eta * pow(c.f, mexp - 1.0);
+  } else {
+    c.aep = 0.0;
+    c.d = 0.0;
+  }
+  c.ep = c.aep * c.sgn;
+  return c;
+}
+
 void tvo_rhs(const tvo_model* m, const double* p, const double* y, double t, double* h) {
   int n = m->n;
+  if (m->kind == TVO_CHABOCHE) {
+    int u = n - 2;
+    const double *C = p + 6, *g = p + 6 + u;
+    const double E = p[0], Kinf = p[4], tau = p[5], eda = p[6 + 2 * u], T = p[7 + 2 * u];
+    chab_flow c = chab_eval(u, p, y);
+    h[0] = E * (eda * sin(kTwoPi * t / T) - c.ep);
+    h[1] = tau * (Kinf - y[1]);
+    for (int i = 0; i < u; ++i) h[2 + i] = 2.0 / 3.0 * C[i] * c.ep - g[i] * y[2 + i] * c.aep;
+    return;
+  }
   if (m->kind == TVO_MDS) {
     int u = n / 2;
     const double* M = p + 2 * u;
@@ -145,6 +184,32 @@ void tvo_rhs(const tvo_model* m, const double* p, const double* y, double t, dou
 void tvo_jac(const tvo_model* m, const double* p, const double* y, double t, double* j) {
   (void)t;
   int n = m->n;
+  if (m->kind == TVO_CHABOCHE) {
+    int u = n - 2;
+    const double *C = p + 6, *g = p + 6 + u;
+    const double E = p[0], tau = p[5];
+    chab_flow c = chab_eval(u, p, y);
+    /* gradients over y of ep and |ep|: s depends on sigma (+1) and X_i (-1) */
+    double dep[32 + 2], daep[32 + 2];
+    dep[0] = c.d;
+    daep[0] = c.d * c.sgn;
+    dep[1] = -c.d * c.sgn;
+    daep[1] = -c.d;
+    for (int i = 0; i < u; ++i) {
+      dep[2 + i] = -c.d;
+      daep[2 + i] = -c.d * c.sgn;
+    }
+    memset(j, 0, sizeof(double) * n * n);
+    for (int col = 0; col < n; ++col) j[col] = -E * dep[col];
+    j[n + 1] = -tau;
+    for (int i = 0; i < u; ++i) {
+      double* row = j + (2 + i) * n;
+      for (int col = 0; col < n; ++col)
+        row[col] = 2.0 / 3.0 * C[i] * dep[col] - g[i] * y[2 + i] * daep[col];
+      row[2 + i] -= g[i] * c.aep;
+    }
+    return;
+  }
   if (m->kind == TVO_MDS) {
     /* h is linear in y: column c of j is h(e_c) without the forcing */
     int u = n / 2;
@@ -205,6 +270,38 @@ void tvo_jac(const tvo_model* m, const double* p, const double* y, double t, dou
 void tvo_vjp_p(const tvo_model* m, const double* p, const double* y, double t, const double* a,
                double scale, double* gp) {
   int n = m->n;
+  if (m->kind == TVO_CHABOCHE) {
+    /* p = [E, m, eta, sigma0, Kinf, tau, C_1..C_u, g_1..g_u, ed_a, T] */
+    int u = n - 2;
+    const double *C = p + 6, *g = p + 6 + u;
+    const double E = p[0], mexp = p[1], eta = p[2], Kinf = p[4], tau = p[5];
+    const double eda = p[6 + 2 * u], T = p[7 + 2 * u];
+    chab_flow c = chab_eval(u, p, y);
+    /* derivatives of |ep| = max(f, 0)^m over m, eta, sigma0 (zero when elastic) */
+    double daep_m = 0.0, daep_eta = 0.0, daep_s0 = 0.0;
+    if (c.f > 0.0) {
+      daep_m = c.aep * log(c.f);
+      daep_eta = -c.d * c.f;  /* d f / d eta = -f / eta; times m f^(m-1) */
+      daep_s0 = -c.d;         /* d f / d sigma0 = -1 / eta */
+    }
+    /* h depends on ep = |ep| sgn and |ep|: weight of d|ep| in a . h */
+    double w = -E * a[0] * c.sgn;  /* sigma' = ... - E ep */
+    for (int i = 0; i < u; ++i) w += a[2 + i] * (2.0 / 3.0 * C[i] * c.sgn - g[i] * y[2 + i]);
+    const double ph = kTwoPi * t / T;
+    gp[0] += scale * a[0] * (eda * sin(ph) - c.ep);        /* E */
+    gp[1] += scale * w * daep_m;                            /* m */
+    gp[2] += scale * w * daep_eta;                          /* eta */
+    gp[3] += scale * w * daep_s0;                           /* sigma0 */
+    gp[4] += scale * a[1] * tau;                            /* K_inf */
+    gp[5] += scale * a[1] * (Kinf - y[1]);                  /* tau */
+    for (int i = 0; i < u; ++i) {
+      gp[6 + i] += scale * a[2 + i] * 2.0 / 3.0 * c.ep;     /* C_i */
+      gp[6 + u + i] += scale * a[2 + i] * (-y[2 + i] * c.aep);  /* g_i */
+    }
+    gp[6 + 2 * u] += scale * a[0] * E * sin(ph);            /* ed_a */
+    gp[7 + 2 * u] += scale * a[0] * E * eda * cos(ph) * (-ph / T);  /* T */
+    return;
+  }
   if (m->kind == TVO_MDS) {
     /* v_i' = (F_i - F_{i-1}) / M_i: F_i enters v_i' with +1/M_i and v_{i+1}' with
      * -1/M_{i+1}; F_i is linear in K_i and C_i. */

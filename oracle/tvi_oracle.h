@@ -35,6 +35,15 @@
  *                   F_i  = K_i (d_{i+1} - d_i) + C_i (v_{i+1} - v_i),
  *                 F_0 = 0 (free end, where the force acts) and d_{u+1} = v_{u+1} = 0
  *                 (the fixed end): spring and damper i join mass i to mass i+1.
+ *   TVO_CHABOCHE  Chaboche viscoplasticity with u = n - 2 backstresses (Sec.
+ *                 5.1.1, Table chaboche-params), y = [sigma, K, X_1..X_u],
+ *                 p = [E, m, eta, sigma_0, K_inf, tau, C_1..C_u, g_1..g_u, ed_a, T]
+ *                 (P = 2u + 8; m is the flow exponent the paper calls n):
+ *                   s = sigma - sum X,  f = (|s| - K - sigma_0) / eta,
+ *                   ep = max(f, 0)^m sign(s)            (plastic strain rate)
+ *                   sigma' = E (ed_a sin(2 pi t / T) - ep)
+ *                   K'     = tau (K_inf - K)
+ *                   X_i'   = 2/3 C_i ep - g_i X_i |ep|
  * MLP parameter layout (flat, FP64): W1[h1][n] b1[h1] W2[h2][h1] b2[h2]
  * W3[n][h2] b3[n]; W are row-major (out x in).
  *
@@ -51,11 +60,13 @@
 extern "C" {
 #endif
 
-enum { TVO_LINEAR = 0, TVO_VDP = 1, TVO_MLP_TANH = 2, TVO_MLP_SILU = 3, TVO_MDS = 4 };
+enum { TVO_LINEAR = 0, TVO_VDP = 1, TVO_MLP_TANH = 2, TVO_MLP_SILU = 3, TVO_MDS = 4,
+       TVO_CHABOCHE = 5 };
 enum { TVO_OK = 0, TVO_NOT_CONVERGED = 1, TVO_NONFINITE = 2, TVO_SINGULAR = 3, TVO_BADARG = -1 };
 
 typedef struct {
-  int kind;        /* TVO_LINEAR / TVO_VDP / TVO_MLP_TANH / TVO_MLP_SILU / TVO_MDS */
+  int kind;        /* TVO_LINEAR / TVO_VDP / TVO_MLP_TANH / TVO_MLP_SILU / TVO_MDS /
+                      TVO_CHABOCHE */
   int n;           /* state size */
   int h1, h2;      /* MLP hidden widths (ignored otherwise) */
   int per_series;  /* 1: params [B][P]; 0: one shared parameter vector [P] */

@@ -21,11 +21,13 @@ Default sizes are the paper-shaped workloads:
                 steps with per-series lengths uniform in [2000, 20000]
   mds           mass-damper-spring chain (n = 2 n_unit), the parameter table of the
                 paper's timing study, 100 series, 2000 uniform steps on [0, 1]
+  chaboche      Chaboche viscoplasticity (n = 2 + n_unit), the paper's parameter
+                table, 50 series, 2000 uniform steps on [0, 10]
 """
 import numpy as np
 
 SEED_LINEAR, SEED_VDP, SEED_MLP, SEED_PREDICTOR, SEED_MLP_LARGE = 1001, 1002, 1003, 1004, 1005
-SEED_MDS = 1006
+SEED_MDS, SEED_CHABOCHE = 1006, 1007
 
 
 def _rng(seed):
@@ -134,6 +136,26 @@ def mds(seed=SEED_MDS, B=100, N=2000, n_unit=2, t_max=1.0, jitter=0.0):
         params = params * np.exp(jitter * _rng(seed).standard_normal(params.shape))
     return {"spec": {"kind": "mds", "n": 2 * u, "hidden": (0, 0), "per_series": True},
             "y0": np.zeros((B, 2 * u)), "times": uniform_times(B, N, t_max),
+            "params": params, "lengths": None}
+
+
+def chaboche(seed=SEED_CHABOCHE, B=50, N=2000, n_unit=3, t_max=10.0, jitter=0.0):
+    """Chaboche viscoplasticity (Sec. 5.1.1, Table chaboche-params): E = 10,
+    flow exponent 5, eta = 2, sigma_0 = 1, K_inf = 10, tau = 1, C_i and g_i
+    linspace over the backstresses in [0.1, 1] and [0.1, 0.5], strain-rate
+    amplitude linspace over the series in [0.1, 1], period T = 1; zero initial
+    state; N uniform steps on [0, t_max].  Per-series parameter vectors
+    [E, m, eta, sigma_0, K_inf, tau, C_1..C_u, g_1..g_u, ed_a, T].  jitter > 0
+    multiplies every parameter by a seeded factor exp(jitter * N(0, 1))."""
+    u = int(n_unit)
+    base = np.concatenate([[10.0, 5.0, 2.0, 1.0, 10.0, 1.0], np.linspace(0.1, 1.0, u),
+                           np.linspace(0.1, 0.5, u)])
+    eda = np.linspace(0.1, 1.0, B)
+    params = np.concatenate([np.tile(base, (B, 1)), eda[:, None], np.ones((B, 1))], axis=1)
+    if jitter > 0.0:
+        params = params * np.exp(jitter * _rng(seed).standard_normal(params.shape))
+    return {"spec": {"kind": "chaboche", "n": 2 + u, "hidden": (0, 0), "per_series": True},
+            "y0": np.zeros((B, 2 + u)), "times": uniform_times(B, N, t_max),
             "params": params, "lengths": None}
 
 
