@@ -116,15 +116,16 @@ def test_steady_state_under_constant_strain_rate(oracle_lib, u):
     assert abs((yN[0] - yN[2:].sum()) - s_inf) <= 1e-6 * s_inf
 
 
+@pytest.mark.parametrize("side", [1.0, -1.0])  # sign of sigma - sum X
 @pytest.mark.parametrize("u", [1, 4])
-def test_jacobian_and_vjp_are_derivatives(oracle_lib, u):
+def test_jacobian_and_vjp_are_derivatives(oracle_lib, u, side):
     g = np.random.default_rng(150 + u)
     m = _model(u)
     p = _params(u, 160 + u)
     # a plastic state well away from the yield surface and from s = 0
     X = g.normal(0, 0.3, u)
     K = 2.0
-    y = np.concatenate([[X.sum() + (K + p[3] + 1.5 * p[2]) * 1.3], [K], X])
+    y = np.concatenate([[X.sum() + side * (K + p[3] + 1.5 * p[2]) * 1.3], [K], X])
     t = 0.37
     J = oracle_lib.jac(m, p, y, t)
     for c in range(2 + u):
