@@ -55,6 +55,11 @@ WORKLOADS = {
     # large-state route (10 units, n = 20: the study's largest size)
     "mds_user": {"chunk": 1000, "precision": "fp32", "tol": 1e-17, "B": 100, "N": 2000,
                  "refine": 2},
+    # Chaboche viscoplasticity of the paper's timing study (--n-unit backstresses, 50
+    # series, 2000 steps on [0, 10]) as a user model; 5 backstresses (n = 7) is the
+    # study's largest size
+    "chaboche_user": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 50, "N": 2000,
+                      "refine": 2},
     "node16": {"chunk": 200, "precision": "bf16", "tol": 1e-8, "B": 64, "N": 2000, "refine": 2},
     "node32": {"chunk": 1000, "precision": "bf16", "tol": 1e-8, "B": 512, "N": 20000,
                "refine": 2},
@@ -78,8 +83,9 @@ def parse():
     ap.add_argument("--rpt", type=int, default=0, help="steps per thread (0 = library default)")
     ap.add_argument("--refine", type=int, default=None,
                     help="adjoint refinement sweeps (mixed precision)")
-    ap.add_argument("--n-unit", type=int, default=10,
-                    help="mass-damper-spring units (workload mds_user)")
+    ap.add_argument("--n-unit", type=int, default=None,
+                    help="units: mass-damper-spring (mds_user, default 10) or Chaboche "
+                         "backstresses (chaboche_user, default 5)")
     ap.add_argument("--B", type=int, default=None)
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--baseline-steps", type=int, default=5)
@@ -90,6 +96,8 @@ def parse():
     for k, v in WORKLOADS[args.workload].items():
         if getattr(args, k) is None:
             setattr(args, k, v)
+    if args.n_unit is None:
+        args.n_unit = 5 if args.workload == "chaboche_user" else 10
     if args.workload.startswith("node"):
         args.no_chunk1 = True  # the one-step MLP scheme reads status back every Newton update
     return args
@@ -108,6 +116,8 @@ def make_workload(args, rank=0):
         w = workloads.vdp(B=args.B, N=args.N, seed=PRED_EVAL_SEED + rank)
     elif args.workload == "mds_user":
         w = workloads.mds(B=args.B, N=args.N, n_unit=args.n_unit)  # the table's values
+    elif args.workload == "chaboche_user":
+        w = workloads.chaboche(B=args.B, N=args.N, n_unit=args.n_unit)  # the table's values
     elif args.workload == "node16":
         w = workloads.mlp_ode(B=args.B, N=args.N, seed=workloads.SEED_MLP + 1000 * rank)
     else:
@@ -149,6 +159,10 @@ def workload_config(args):
             "mds_user": f"mass-damper-spring chain, {args.n_unit} units (n={2 * args.n_unit}), "
                         "forcing f_a sin(2 pi t/T) with T linspace [0.01,1] over the series, as a "
                         "user model; uniform steps on [0,1]",
+            "chaboche_user": f"Chaboche viscoplasticity, {args.n_unit} backstresses "
+                             f"(n={2 + args.n_unit}), strain rate ed_a sin(2 pi t) with ed_a "
+                             "linspace [0.1,1] over the series, as a user model; uniform steps "
+                             "on [0,10]",
             "node16": "neural ODE n=16, MLP 16-64-64-16 tanh, uniform steps on [0,10]",
             "node32": "neural ODE n=32, MLP 32-128-128-32 SiLU, per-series lengths "
                       "U[2000,N] padded, uniform steps on [0,10]"}[args.workload]
@@ -318,6 +332,20 @@ def roofline(args, w, stats, fwd_ms, adj_ms, refine):
         route = "small" if u <= 2 else "large"
         names = (f"tvi_integrate (user mds, {route}-state kernels, {args.precision})",
                  f"tvi_adjoint (user mds, {route}-state kernels, {args.precision})")
+    elif args.workload == "chaboche_user":
+        # u backstresses, n = u + 2.  Residual: h (s = sigma - sum X: u; yield f: 3;
+        # the power and the flow rate: 2, counted as 2; sigma': sin, 3; K': 2;
+        # X_i': 4 each) = 5u + 10, + R (2 per component: 2u + 4) = 7u + 14; update
+        # y -= d: u + 2.  Adjoint per step: per refinement sweep J^T a over the
+        # dense flow-rule rows (n^2 + 2n), parameter VJP (log, power, sin, cos, and
+        # 4 per backstress) 4u + 20.  A power, sine, cosine or log counts as one.
+        u = args.n_unit
+        nn = u + 2
+        fwd_ops = float(np.sum(((upd + nchk) * (7.0 * u + 14.0) + upd * nn) * spc))
+        adj_ops = float(B * N * (refine * (nn * nn + 2.0 * nn) + 4.0 * u + 20.0))
+        route = "small" if nn <= 4 else "large"
+        names = (f"tvi_integrate (user chaboche, {route}-state kernels, {args.precision})",
+                 f"tvi_adjoint (user chaboche, {route}-state kernels, {args.precision})")
     elif args.workload.startswith("vdp"):
         # residual on the stored iterate y: h (3) + R (4) = 7; update y -= d: 2
         fwd_ops = float(np.sum(((upd + nchk) * 7.0 + upd * 2.0) * spc))
@@ -393,6 +421,13 @@ def run_ours(args):
         user.prepare(args.precision)
         if not args.no_chunk1:
             user.prepare("fp64")  # the chunk = 1 FP64 leg
+        model = user.model(per_series=True)
+    elif args.workload == "chaboche_user":
+        from paper_2310_08649_gb300.user_sources import CHABOCHE, chaboche_param_count
+        user = tvi.UserModel(2 + args.n_unit, chaboche_param_count(args.n_unit), CHABOCHE)
+        user.prepare(args.precision)
+        if not args.no_chunk1:
+            user.prepare("fp64")
         model = user.model(per_series=True)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)

@@ -84,18 +84,25 @@ __global__ void large_chunk_init_kernel(int B, int n4, int c, double* dy, int* a
   }
 }
 
-// y_{i0+1..i0+L} = y_i + dy; carry y_{i0+L}; one block per series
-__global__ void large_store_kernel(int n, int n4, int L, int c, int Np1, int i0, const double* dy,
-                                   double* yi, double* y_out, const int* iters, int* stats) {
+// y_{i0+1..i0+L} = y_i + dy; carry y_{i0+L}; one block per series.  Padded
+// steps (k > length) keep the last real state exactly (reading C-14), whatever
+// rounding Newton left in their identity rows.
+__global__ void large_store_kernel(int n, int n4, int L, int c, int N, int i0, const int* lengths,
+                                   const double* dy, double* yi, double* y_out, const int* iters,
+                                   int* stats) {
   const int b = blockIdx.x;
+  const int len = lengths ? min(max(lengths[b], 0), N) : N;
+  const int jl = min(L, max(len - i0, 0)) - 1;  // last real row of the chunk, -1 if none
   const double* dyb = dy + static_cast<size_t>(b) * c * n4;
-  double* yb = y_out + static_cast<size_t>(b) * Np1 * n;
+  double* yb = y_out + static_cast<size_t>(b) * (N + 1) * n;
   for (int e = threadIdx.x; e < L * n; e += blockDim.x) {
     const int j = e / n, s = e % n;
-    yb[static_cast<size_t>(i0 + 1 + j) * n + s] = yi[b * n4 + s] + dyb[j * n4 + s];
+    const int jr = min(j, jl);
+    yb[static_cast<size_t>(i0 + 1 + j) * n + s] =
+        yi[b * n4 + s] + (jr >= 0 ? dyb[jr * n4 + s] : 0.0);
   }
   __syncthreads();
-  if (threadIdx.x < n) yi[b * n4 + threadIdx.x] += dyb[(L - 1) * n4 + threadIdx.x];
+  if (threadIdx.x < n && jl >= 0) yi[b * n4 + threadIdx.x] += dyb[jl * n4 + threadIdx.x];
   if (threadIdx.x == 0 && stats) {
     int* o = stats + b * kStats;
     o[0] += iters[b];
@@ -218,8 +225,8 @@ cudaError_t large_forward(const LargeKernels& k, int n, int P, int precision, co
       TVI_TRY(mlp_launch_chain(precision, ch, s));
     }
     note_launch();
-    large_store_kernel<<<B, 128, 0, s>>>(n, n4, L, c, N + 1, i0, w.dy, w.yi, a.y_out, w.iters,
-                                         a.stats);
+    large_store_kernel<<<B, 128, 0, s>>>(n, n4, L, c, N, i0, a.lengths, w.dy, w.yi, a.y_out,
+                                         w.iters, a.stats);
     TVI_TRY(cudaGetLastError());
   }
   note_launch();

@@ -1308,17 +1308,24 @@ __global__ void mlp_chunk_init_kernel(int B, int n, int c, double* dy, int* acti
 }
 
 // Write y_{i0+1..i0+L} = y_i + dy and carry y_{i0+L}; one block per series.
-__global__ void mlp_store_kernel(int n, int L, int c, int Np1, int i0, const double* dy,
-                                 double* yi, double* y_out, const int* iters, int* stats) {
+// Padded steps (k > length) keep the last real state exactly (reading C-14),
+// whatever rounding Newton left in their identity rows.
+__global__ void mlp_store_kernel(int n, int L, int c, int N, int i0, const int* lengths,
+                                 const double* dy, double* yi, double* y_out, const int* iters,
+                                 int* stats) {
   const int b = blockIdx.x;
+  const int len = lengths ? min(max(lengths[b], 0), N) : N;
+  const int jl = min(L, max(len - i0, 0)) - 1;  // last real row of the chunk, -1 if none
   const double* dyb = dy + static_cast<size_t>(b) * c * n;
-  double* yb = y_out + static_cast<size_t>(b) * Np1 * n;
+  double* yb = y_out + static_cast<size_t>(b) * (N + 1) * n;
   for (int e = threadIdx.x; e < L * n; e += blockDim.x) {
     const int j = e / n, s = e % n;
-    yb[static_cast<size_t>(i0 + 1 + j) * n + s] = yi[b * n + s] + dyb[e];
+    const int jr = min(j, jl);
+    yb[static_cast<size_t>(i0 + 1 + j) * n + s] =
+        yi[b * n + s] + (jr >= 0 ? dyb[jr * n + s] : 0.0);
   }
   __syncthreads();
-  if (threadIdx.x < n) yi[b * n + threadIdx.x] += dyb[(L - 1) * n + threadIdx.x];
+  if (threadIdx.x < n && jl >= 0) yi[b * n + threadIdx.x] += dyb[jl * n + threadIdx.x];
   if (threadIdx.x == 0 && stats) {
     int* o = stats + b * kStats;
     o[0] += iters[b];
@@ -1535,6 +1542,143 @@ cudaError_t launch_blocks_any(const BlocksArgs& bk, int precision, int* err, cud
   return launch_blocks<float>(bk, precision, s);
 }
 
+// ---------------------------------------------------------------------------
+// Tiled chain solve (the hybrid of Sec. 3.3): the chunk's L steps are split
+// into W tiles, one warp each.
+//   pass A (tiles in parallel)  warp w composes its tile's affine map
+//                               d_end = P_w d_in + q_w  (P <- M_j P, q <- M_j (q + r_j))
+//   pass B (one warp)           d_in of every tile from x_init by the W maps
+//   pass C (tiles in parallel)  warp w sweeps its tile from its d_in:
+//                               d_j = M_j (d_{j-1} + r_j), x updated by mode
+// Sequential depth per series: L / W + W steps instead of L, for n^3 / 32
+// FMAs a lane per step in pass A.  Blocks and rhs rows are read from global
+// memory (pass C reads them a second time, mostly from L2).  Shared memory per
+// warp: P (two buffers), the staged block M_j (rows padded to N + 1), q, d_in.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+constexpr size_t tile_warp_bytes() {
+  return sizeof(T) * (2 * N * N + N * (N + 1) + 2 * N + 32);
+}
+
+template <typename T, int N, int W>
+__global__ void __launch_bounds__(32 * W) tile_chain_kernel(ChainArgs a) {
+  constexpr int LDM = N + 1;
+  extern __shared__ __align__(16) unsigned char tile_smem[];
+  const int b = blockIdx.x;
+  if (a.active && !a.active[b]) return;  // block-uniform
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* wbase = reinterpret_cast<T*>(tile_smem + static_cast<size_t>(warp) * tile_warp_bytes<T, N>());
+  T* P0 = wbase;
+  T* P1 = P0 + N * N;
+  T* sM = P1 + N * N;    // [N][LDM]
+  T* sq = sM + N * LDM;  // [N]
+  T* sd = sq + N;        // [N] d_in of the tile
+  T* su = sd + N;        // [32] q + r_j
+  const int Lt = (a.L + W - 1) / W;
+  const int j0 = min(a.L, warp * Lt), j1 = min(a.L, j0 + Lt);
+  const T* Mb = static_cast<const T*>(a.M) + static_cast<size_t>(b) * a.c * N * N;
+  double* xb = a.x + static_cast<size_t>(b) * a.c * N;
+  auto rhs_row = [&](int j) -> const double* {
+    return a.rhs_buf ? a.rhs_buf + (static_cast<size_t>(b) * a.c + j) * N
+                     : a.rhs_traj + (static_cast<size_t>(b) * (a.N + 1) +
+                                     step_of(a.reverse, a.i0, a.L, j)) * N;
+  };
+  // ---- pass A: (P, q) = composite of the tile's maps, starting from (I, 0) ----
+  for (int e = lane; e < N * N; e += 32) P0[e] = (e / N == e % N) ? T(1) : T(0);
+  if (lane < N) sq[lane] = T(0);
+  __syncwarp();
+  T* Pc = P0;
+  T* Pn = P1;
+#pragma unroll 1
+  for (int j = j0; j < j1; ++j) {
+    const T* Mt = Mb + static_cast<size_t>(j) * N * N;  // Mt[k * N + r] = M_j[r][k]
+    for (int e = lane; e < N * N; e += 32) {
+      const int k = e / N, r = e - k * N;
+      sM[r * LDM + k] = Mt[e];
+    }
+    if (lane < N) su[lane] = sq[lane] + static_cast<T>(rhs_row(j)[lane]);
+    __syncwarp();
+    for (int e = lane; e < N * N; e += 32) {
+      const int r = e / N, c = e - r * N;
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < N; ++k) acc = fma(sM[r * LDM + k], Pc[k * N + c], acc);
+      Pn[e] = acc;
+    }
+    if (lane < N) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < N; ++k) acc = fma(sM[lane * LDM + k], su[k], acc);
+      sq[lane] = acc;
+    }
+    __syncwarp();
+    T* t = Pc;
+    Pc = Pn;
+    Pn = t;
+  }
+  if (Pc != P0) {
+    for (int e = lane; e < N * N; e += 32) P0[e] = Pc[e];
+    __syncwarp();
+  }
+  __syncthreads();
+  // ---- pass B: tile inputs d_in, in tile order ----
+  if (warp == 0) {
+    T d = (a.x_init && lane < N) ? static_cast<T>(a.x_init[b * N + lane]) : T(0);
+    for (int w = 0; w < W; ++w) {
+      T* wb = reinterpret_cast<T*>(tile_smem + static_cast<size_t>(w) * tile_warp_bytes<T, N>());
+      const T* Pw = wb;
+      const T* qw = wb + 2 * N * N + N * LDM;
+      T* dw = wb + 2 * N * N + N * LDM + N;
+      if (lane < N) dw[lane] = d;
+      T acc = lane < N ? qw[lane] : T(0);
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T dk = __shfl_sync(kFull, d, k);
+        if (lane < N) acc = fma(Pw[lane * N + k], dk, acc);
+      }
+      d = acc;
+    }
+  }
+  __syncthreads();
+  // ---- pass C: sweep the tile from its input ----
+  T d = lane < N ? sd[lane] : T(0);
+#pragma unroll 1
+  for (int j = j0; j < j1; ++j) {
+    const T* Mt = Mb + static_cast<size_t>(j) * N * N;
+    const double* rr = rhs_row(j);
+    const T u = lane < N ? d + static_cast<T>(rr[lane]) : T(0);
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const T uk = __shfl_sync(kFull, u, k);
+      if (lane < N) acc = fma(Mt[k * N + lane], uk, acc);
+    }
+    d = acc;
+    if (lane < N) {
+      double* xr = xb + static_cast<size_t>(j) * N + lane;
+      const double dd = static_cast<double>(acc);
+      *xr = (a.mode == 0) ? *xr - dd : (a.mode == 1 ? dd : *xr + dd);
+    }
+  }
+}
+
+template <typename T, int N, int W>
+cudaError_t launch_tile_chain(const ChainArgs& ch, cudaStream_t s) {
+  const size_t sm = static_cast<size_t>(W) * tile_warp_bytes<T, N>();
+  cudaError_t e = set_smem(tile_chain_kernel<T, N, W>, sm);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  tile_chain_kernel<T, N, W><<<ch.B, 32 * W, sm, s>>>(ch);
+  return cudaGetLastError();
+}
+
+// tiles per series: 16 warps while their shared memory fits 200 KB, else 8
+template <typename T, int N>
+cudaError_t launch_tile_n(const ChainArgs& ch, cudaStream_t s) {
+  if (16 * tile_warp_bytes<T, N>() <= 200 * 1024) return launch_tile_chain<T, N, 16>(ch, s);
+  return launch_tile_chain<T, N, 8>(ch, s);
+}
+
 template <typename T, int N, int W>
 cudaError_t launch_chain_n(const ChainArgs& ch, cudaStream_t s) {
   const dim3 grid((ch.B + W - 1) / W);
@@ -1564,9 +1708,30 @@ cudaError_t launch_chain_w(const ChainArgs& ch, cudaStream_t s) {
 // One warp per series.  With few series, one warp per block spreads them over
 // as many SMs; with many, four per block.
 template <typename T>
-cudaError_t launch_chain(const ChainArgs& ch, cudaStream_t s) {
+cudaError_t launch_seq_chain(const ChainArgs& ch, cudaStream_t s) {
   return ch.B <= kChainOneWarpMaxSeries ? launch_chain_w<T, 1>(ch, s)
                                         : launch_chain_w<T, kChainWarps>(ch, s);
+}
+
+// Chain solve, chosen by block width (the paper's Thomas-versus-PCR trade-off,
+// Sec. 5.3): the tiled hybrid (sequential depth L / W + W, n^3 / 32 FMAs a lane
+// per step to compose the tiles) up to n = 16 -- n = 8 in FP64, whose products
+// run on the 1/64-rate pipe -- and the sequential substitution (n^2 per step)
+// above.  Measured on GB300 (FP32 blocks, series*steps/s of a whole step):
+// n = 8 Chaboche 2.26e7 -> 4.38e7, n = 16 neural ODE 5.70e6 -> 6.06e6 with the
+// tiles; n = 20 mass-damper-spring 1.79e7 -> 1.57e7 and n = 32 neural ODE
+// 3.02e6 -> 2.42e6, so the wider blocks keep the sequential solve.
+template <typename T>
+cudaError_t launch_chain(const ChainArgs& ch, cudaStream_t s) {
+  const int tile_max = sizeof(T) == sizeof(double) ? 8 : 16;
+  if (ch.n > tile_max) return launch_seq_chain<T>(ch, s);
+  switch (ch.n) {
+    case 4: return launch_tile_n<T, 4>(ch, s);
+    case 8: return launch_tile_n<T, 8>(ch, s);
+    case 12: return launch_tile_n<T, 12>(ch, s);
+    case 16: return launch_tile_n<T, 16>(ch, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -1649,7 +1814,8 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
       TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s));
     }
     note_launch();
-    mlp_store_kernel<<<B, 128, 0, s>>>(n, L, c, N + 1, i0, w.dy, w.yi, a.y_out, w.iters, a.stats);
+    mlp_store_kernel<<<B, 128, 0, s>>>(n, L, c, N, i0, a.lengths, w.dy, w.yi, a.y_out, w.iters,
+                                       a.stats);
     TVI_TRY(cudaGetLastError());
   }
   note_launch();

@@ -9,6 +9,8 @@ the time t.
     mlp_tanh()   h = tanh(W3 tanh(W2 tanh(W1 y + b1) + b2) + b3)         (any n)
     MDS          mass-damper-spring chain of n/2 units with periodic forcing
                  (time-dependent; p = [K_1.., C_1.., M_1.., f_a, T], P = 3n/2 + 2)
+    CHABOCHE     Chaboche viscoplasticity with n - 2 backstresses under a periodic
+                 strain rate (p = [E, m, eta, sigma_0, K_inf, tau, C.., g.., ed_a, T])
 
     import paper_2310_08649_gb300 as tvi
     from paper_2310_08649_gb300.user_sources import VDP
@@ -237,3 +239,98 @@ __device__ void tvi_vjp_p(const double* y, double t, const double* p, const doub
 
 def mds_param_count(n_unit):
     return 3 * n_unit + 2
+
+
+CHABOCHE = r"""
+// Chaboche viscoplasticity with kU = TVI_N - 2 backstresses, y = [sigma, K,
+// X_1..X_u], p = [E, m, eta, sigma_0, K_inf, tau, C_1..C_u, g_1..g_u, ed_a, T]:
+//   s = sigma - sum X, f = (|s| - K - sigma_0) / eta, ep = max(f, 0)^m sign(s)
+//   sigma' = E (ed_a sin(2 pi t / T) - ep), K' = tau (K_inf - K),
+//   X_i' = 2/3 C_i ep - g_i X_i |ep|
+constexpr int kU = TVI_N - 2;
+
+// sign(s), |ep| and d = (m / eta) f^(m-1) (0 in the elastic range)
+template <typename T>
+__device__ void chaboche_flow(const T* y, const double* p, T& sgn, T& aep, T& d) {
+  T s = y[0];
+  for (int i = 0; i < kU; ++i) s -= y[2 + i];
+  sgn = s > T(0) ? T(1) : (s < T(0) ? T(-1) : T(0));
+  const T mexp = static_cast<T>(p[1]), eta = static_cast<T>(p[2]);
+  const T f = (fabs(s) - y[1] - static_cast<T>(p[3])) / eta;
+  if (f > T(0)) {
+    const T fm1 = pow(f, mexp - T(1));
+    aep = fm1 * f;
+    d = mexp / eta * fm1;
+  } else {
+    aep = T(0);
+    d = T(0);
+  }
+}
+
+__device__ void tvi_rhs(const double* y, double t, const double* p, double* h) {
+  double sgn, aep, d;
+  chaboche_flow(y, p, sgn, aep, d);
+  const double ep = aep * sgn;
+  h[0] = p[0] * (p[6 + 2 * kU] * sin(6.283185307179586 * t / p[7 + 2 * kU]) - ep);
+  h[1] = p[5] * (p[4] - y[1]);
+  for (int i = 0; i < kU; ++i)
+    h[2 + i] = 2.0 / 3.0 * p[6 + i] * ep - p[6 + kU + i] * y[2 + i] * aep;
+}
+
+// Jacobian in the block type: d ep = d (ds, -sgn dK), d|ep| = d (sgn ds, -dK),
+// ds = dsigma - sum dX
+template <typename T>
+__device__ void tvi_jac(const T* y, double t, const double* p, T* J) {
+  T sgn, aep, d;
+  chaboche_flow(y, p, sgn, aep, d);
+  const T E = static_cast<T>(p[0]);
+  for (int k = 0; k < TVI_N * TVI_N; ++k) J[k] = T(0);
+  J[0] = -E * d;
+  J[1] = E * d * sgn;
+  for (int q = 0; q < kU; ++q) J[2 + q] = E * d;
+  J[TVI_N + 1] = -static_cast<T>(p[5]);
+  for (int i = 0; i < kU; ++i) {
+    T* row = J + (2 + i) * TVI_N;
+    const T c = T(2) / T(3) * static_cast<T>(p[6 + i]);
+    const T gx = static_cast<T>(p[6 + kU + i]) * y[2 + i];
+    row[0] = c * d - gx * d * sgn;
+    row[1] = -c * d * sgn + gx * d;
+    for (int q = 0; q < kU; ++q) row[2 + q] = -c * d + gx * d * sgn;
+    row[2 + i] -= static_cast<T>(p[6 + kU + i]) * aep;
+  }
+}
+
+__device__ void tvi_vjp_p(const double* y, double t, const double* p, const double* a,
+                          double* g) {
+  double sgn, aep, d;
+  chaboche_flow(y, p, sgn, aep, d);
+  const double ep = aep * sgn;
+  double s = y[0];
+  for (int i = 0; i < kU; ++i) s -= y[2 + i];
+  const double f = (fabs(s) - y[1] - p[3]) / p[2];
+  // derivatives of |ep| over the flow exponent, eta and sigma_0 (0 when elastic)
+  const double dm = f > 0.0 ? aep * log(f) : 0.0;
+  const double deta = -d * f;
+  const double ds0 = -d;
+  double w = -p[0] * a[0] * sgn;  // weight of |ep| in a . h
+  for (int i = 0; i < kU; ++i)
+    w += a[2 + i] * (2.0 / 3.0 * p[6 + i] * sgn - p[6 + kU + i] * y[2 + i]);
+  const double ph = 6.283185307179586 * t / p[7 + 2 * kU];
+  g[0] = a[0] * (p[6 + 2 * kU] * sin(ph) - ep);
+  g[1] = w * dm;
+  g[2] = w * deta;
+  g[3] = w * ds0;
+  g[4] = a[1] * p[5];
+  g[5] = a[1] * (p[4] - y[1]);
+  for (int i = 0; i < kU; ++i) {
+    g[6 + i] = a[2 + i] * 2.0 / 3.0 * ep;
+    g[6 + kU + i] = -a[2 + i] * y[2 + i] * aep;
+  }
+  g[6 + 2 * kU] = a[0] * p[0] * sin(ph);
+  g[7 + 2 * kU] = -a[0] * p[0] * p[6 + 2 * kU] * cos(ph) * ph / p[7 + 2 * kU];
+}
+"""
+
+
+def chaboche_param_count(n_unit):
+    return 2 * n_unit + 8

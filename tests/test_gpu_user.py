@@ -16,8 +16,8 @@ import pytest
 import workloads
 from oracle import Model as OModel
 from test_gpu_euler import fe_error_estimate
-from paper_2310_08649_gb300.user_sources import LINEAR, MDS, VDP, VDP_FP64_JAC, \
-    mds_param_count, mlp_param_count, mlp_tanh
+from paper_2310_08649_gb300.user_sources import CHABOCHE, LINEAR, MDS, VDP, VDP_FP64_JAC, \
+    chaboche_param_count, mds_param_count, mlp_param_count, mlp_tanh
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -48,6 +48,8 @@ def users(tvi):
             "mds5": tvi.UserModel(10, mds_param_count(5), MDS),
             "mds10": tvi.UserModel(20, mds_param_count(10), MDS),
             "lin5": tvi.UserModel(5, 25, LINEAR),
+            **{f"chab{u}": tvi.UserModel(2 + u, chaboche_param_count(u), CHABOCHE)
+               for u in (1, 2, 3, 5)},
             "mlp5": tvi.UserModel(5, mlp_param_count(5, 2, 1), mlp_tanh(2, 1))}
     yield made
     torch.cuda.synchronize()
@@ -271,6 +273,39 @@ def test_user_large_padded_lengths_and_rejections(tvi, users, oracle_lib):
                                  P.data_ptr(), Y.data_ptr(), G.data_ptr(), dpn.data_ptr(), None,
                                  None)
     assert rc == -7
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("u,chunk", [(1, 100), (2, 1000), (3, 250), (5, 1000)])
+def test_user_chaboche_matches_oracle(tvi, users, oracle_lib, precision, u, chunk):
+    """Chaboche viscoplasticity (nonsmooth flow rule, periodic strain rate): the
+    paper's backstress counts 1 .. 5 (n = 3 .. 7; n > 4 on the large-state
+    route), parameters from its table jittered per series, a loading strong
+    enough to yield.  Gate per series: max(parity gate, 10 x the forward error
+    that residuals of size tol leave after propagation)."""
+    w = workloads.chaboche(B=12, N=2000, n_unit=u, jitter=0.1, seed=180 + u)
+    w["params"][:, 6 + 2 * u] *= 3.0
+    m = OModel.from_spec(w["spec"])
+    tol = 1e-12
+    ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], tol_abs=tol,
+                                    max_iter=100)
+    assert not st.any()
+    assert np.abs(ref[:, :, 2:]).max() > 1e-2  # the backstresses moved: plastic flow
+    est = oracle_lib.forward_error_estimate(m, w["times"], w["params"], ref, tol)
+    model = users[f"chab{u}"].model(per_series=True)
+    o = tvi.Options(chunk=chunk, tol_abs=tol, max_iter=60, precision=precision,
+                    adjoint_refine=3)
+    y, _, status, rc = forward(tvi, model, w, o)
+    assert rc == 0 and not status.any()
+    err = relerr_series(y, ref)
+    bad = np.nonzero(err > np.maximum(GATE[precision], 10.0 * est))[0]
+    assert bad.size == 0, (bad, err[bad], est[bad])
+    g = workloads.random_grad_out(190 + u, 12, 2000, 2 + u)
+    dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g)
+    dp, dy0 = adjoint(tvi, model, w, o, ref, g)
+    e_p = np.abs(dp - dp_ref).max(axis=1) / np.abs(dp_ref).max(axis=1)
+    assert e_p.max() <= GATE[precision], (e_p.argmax(), e_p.max())
+    assert relerr(dy0, dy0_ref) <= GATE[precision]
 
 
 def test_user_padded_lengths_and_noalloc(tvi, users, oracle_lib):
