@@ -267,10 +267,13 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
 /*
  * User-defined models.  The integrator of Sec. 2.2 takes the right-hand side h
  * and its Jacobian j = dh/dy as functions; here they are CUDA C++ device source,
- * compiled at run time (NVRTC, sm_103a) together with the fused small-state
- * solver kernels, so they run inlined in the same one-block-per-series kernels
- * as the built-in linear and van der Pol models.  `source` defines, at global
- * scope, with TVI_N (= n) and TVI_P (= P) #defined before it:
+ * compiled at run time (NVRTC, sm_103a) together with kernel templates: for
+ * n <= 4 the fused small-state solver, so they run inlined in the same
+ * one-block-per-series kernels as the built-in linear and van der Pol models;
+ * for 5 <= n <= 32 the large-state kernels (a thread per (series, step) for the
+ * residual, a warp per step for the Jacobian block and its inverse) around the
+ * chunk solve of the MLP engine.  `source` defines, at global scope, with
+ * TVI_N (= n) and TVI_P (= P) #defined before it:
  *
  *   __device__ void tvi_rhs(const double* y, double t, const double* p, double* h);
  *       h[i] = h_i(y, t; p), i < n: the ODE dy/dt = h(y, t; p) (Sec. 2.1)
@@ -288,12 +291,15 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
  *   template <typename T>
  *   __device__ void tvi_jac(const T* y, double t, const double* p, T* J);
  * and is then evaluated in the block type (FP32 with FP32 blocks, as for the
- * built-in models); a plain FP64 tvi_jac is evaluated in FP64 and rounded.  The library trusts them: J must be the Jacobian of h for Newton
- * to converge quadratically, and g its parameter product for the gradients to
- * be those of the discrete loss.  Sizes 1 <= n <= 4 and 1 <= P <= 32; FP64 or
- * FP32 blocks (BF16: TVI_EUNSUPPORTED); both schemes, retry_halving, per-series
- * or shared parameters, tvi_adjoint_noalloc; no Newton predictor.  Calls on one
- * model from several host threads are safe.  The paper has no counterpart to
+ * built-in models); a plain FP64 tvi_jac is evaluated in FP64 and rounded.
+ * The library trusts them: J must be the Jacobian of h for Newton to converge
+ * quadratically, and g its parameter product for the gradients to be those of
+ * the discrete loss.  Sizes 1 <= n <= 32 and 1 <= P <= 32; FP64 or FP32 blocks
+ * (BF16: TVI_EUNSUPPORTED); per-series or shared parameters; no Newton
+ * predictor.  n <= 4 also has forward Euler, retry_halving and
+ * tvi_adjoint_noalloc; n > 4 needs the workspace of tvi_workspace_bytes, does
+ * not halve, and rejects forward Euler and tvi_adjoint_noalloc
+ * (TVI_EUNSUPPORTED).  Calls on one model from several host threads are safe.  The paper has no counterpart to
  * run-time compilation: it is how an ABI of plain pointers accepts functions.
  */
 
@@ -305,10 +311,10 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
 tvi_status tvi_user_model_create(int n, int P, const char* source, tvi_user_model** out);
 
 /* Compile the solver kernels of one block precision (TVI_PREC_FP64 or
- * TVI_PREC_FP32) for every steps-per-thread tiling now.  Otherwise a tiling is
- * compiled (about a second) and loaded by the first tvi_integrate or
- * tvi_adjoint that needs it; do that first call, or this one, before any stream
- * capture.  No GPU needed. */
+ * TVI_PREC_FP32) now: every steps-per-thread tiling (n <= 4), or the
+ * large-state kernels (n > 4).  Otherwise they are compiled (about a second
+ * each) and loaded by the first tvi_integrate or tvi_adjoint that needs them;
+ * do that first call, or this one, before any stream capture.  No GPU needed. */
 tvi_status tvi_user_model_prepare(tvi_user_model* model, int precision);
 
 /* Free the model and unload its kernels, after all work using it has completed.
