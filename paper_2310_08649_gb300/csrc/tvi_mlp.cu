@@ -1583,38 +1583,71 @@ __global__ void __launch_bounds__(32 * W) tile_chain_kernel(ChainArgs a) {
                      : a.rhs_traj + (static_cast<size_t>(b) * (a.N + 1) +
                                      step_of(a.reverse, a.i0, a.L, j)) * N;
   };
+  // Each pass reads a step's block and rhs row PF steps ahead into registers
+  // (a ring indexed at compile time), so the loads' latency overlaps the
+  // dependent arithmetic of the steps in between.
+  constexpr int PF = N * sizeof(T) <= 32 ? 4 : 2;  // the deeper ring only where it fits
+  constexpr int E = (N * N + 31) / 32;  // block entries a lane stages in pass A
   // ---- pass A: (P, q) = composite of the tile's maps, starting from (I, 0) ----
   for (int e = lane; e < N * N; e += 32) P0[e] = (e / N == e % N) ? T(1) : T(0);
   if (lane < N) sq[lane] = T(0);
   __syncwarp();
   T* Pc = P0;
   T* Pn = P1;
+  {
+    T mreg[PF][E];
+    double rreg[PF];
+    auto load_a = [&](int j, T (&mr)[E], double& rv) {
+      if (j < j1) {
+        const T* Mt = Mb + static_cast<size_t>(j) * N * N;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int e = lane + 32 * i;
+          mr[i] = e < N * N ? Mt[e] : T(0);
+        }
+        rv = lane < N ? rhs_row(j)[lane] : 0.0;
+      }
+    };
+#pragma unroll
+    for (int q = 0; q < PF; ++q) load_a(j0 + q, mreg[q], rreg[q]);
 #pragma unroll 1
-  for (int j = j0; j < j1; ++j) {
-    const T* Mt = Mb + static_cast<size_t>(j) * N * N;  // Mt[k * N + r] = M_j[r][k]
-    for (int e = lane; e < N * N; e += 32) {
-      const int k = e / N, r = e - k * N;
-      sM[r * LDM + k] = Mt[e];
-    }
-    if (lane < N) su[lane] = sq[lane] + static_cast<T>(rhs_row(j)[lane]);
-    __syncwarp();
-    for (int e = lane; e < N * N; e += 32) {
-      const int r = e / N, c = e - r * N;
-      T acc = T(0);
+    for (int jb = j0; jb < j1; jb += PF) {
 #pragma unroll
-      for (int k = 0; k < N; ++k) acc = fma(sM[r * LDM + k], Pc[k * N + c], acc);
-      Pn[e] = acc;
-    }
-    if (lane < N) {
-      T acc = T(0);
+      for (int q = 0; q < PF; ++q) {
+        const int j = jb + q;
+        if (j < j1) {  // warp-uniform
+          // stage M_j row-major (sM[r][k] = M_j[r][k] = Mt[k * N + r]) and u = q + r_j
 #pragma unroll
-      for (int k = 0; k < N; ++k) acc = fma(sM[lane * LDM + k], su[k], acc);
-      sq[lane] = acc;
+          for (int i = 0; i < E; ++i) {
+            const int e = lane + 32 * i;
+            if (e < N * N) {
+              const int k = e / N, r = e - k * N;
+              sM[r * LDM + k] = mreg[q][i];
+            }
+          }
+          if (lane < N) su[lane] = sq[lane] + static_cast<T>(rreg[q]);
+          load_a(j + PF, mreg[q], rreg[q]);
+          __syncwarp();
+          for (int e = lane; e < N * N; e += 32) {
+            const int r = e / N, c = e - r * N;
+            T acc = T(0);
+#pragma unroll
+            for (int k = 0; k < N; ++k) acc = fma(sM[r * LDM + k], Pc[k * N + c], acc);
+            Pn[e] = acc;
+          }
+          if (lane < N) {
+            T acc = T(0);
+#pragma unroll
+            for (int k = 0; k < N; ++k) acc = fma(sM[lane * LDM + k], su[k], acc);
+            sq[lane] = acc;
+          }
+          __syncwarp();
+          T* t = Pc;
+          Pc = Pn;
+          Pn = t;
+        }
+      }
     }
-    __syncwarp();
-    T* t = Pc;
-    Pc = Pn;
-    Pn = t;
   }
   if (Pc != P0) {
     for (int e = lane; e < N * N; e += 32) P0[e] = Pc[e];
@@ -1642,22 +1675,45 @@ __global__ void __launch_bounds__(32 * W) tile_chain_kernel(ChainArgs a) {
   __syncthreads();
   // ---- pass C: sweep the tile from its input ----
   T d = lane < N ? sd[lane] : T(0);
-#pragma unroll 1
-  for (int j = j0; j < j1; ++j) {
-    const T* Mt = Mb + static_cast<size_t>(j) * N * N;
-    const double* rr = rhs_row(j);
-    const T u = lane < N ? d + static_cast<T>(rr[lane]) : T(0);
-    T acc = T(0);
+  {
+    T mrow[PF][N];  // row `lane` of M_j: Mt[k * N + lane]
+    double rreg[PF], xreg[PF];
+    auto load_c = [&](int j, T (&mr)[N], double& rv, double& xv) {
+      if (j < j1 && lane < N) {
+        const T* Mt = Mb + static_cast<size_t>(j) * N * N;
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const T uk = __shfl_sync(kFull, u, k);
-      if (lane < N) acc = fma(Mt[k * N + lane], uk, acc);
-    }
-    d = acc;
-    if (lane < N) {
-      double* xr = xb + static_cast<size_t>(j) * N + lane;
-      const double dd = static_cast<double>(acc);
-      *xr = (a.mode == 0) ? *xr - dd : (a.mode == 1 ? dd : *xr + dd);
+        for (int k = 0; k < N; ++k) mr[k] = Mt[k * N + lane];
+        rv = rhs_row(j)[lane];
+        xv = a.mode != 1 ? xb[static_cast<size_t>(j) * N + lane] : 0.0;
+      }
+    };
+#pragma unroll
+    for (int q = 0; q < PF; ++q) load_c(j0 + q, mrow[q], rreg[q], xreg[q]);
+#pragma unroll 1
+    for (int jb = j0; jb < j1; jb += PF) {
+#pragma unroll
+      for (int q = 0; q < PF; ++q) {
+        const int j = jb + q;
+        if (j < j1) {  // warp-uniform
+          const T u = lane < N ? d + static_cast<T>(rreg[q]) : T(0);
+          T acc0 = T(0), acc1 = T(0);
+#pragma unroll
+          for (int k = 0; k < N; k += 2) {
+            const T u0 = __shfl_sync(kFull, u, k);
+            const T u1 = __shfl_sync(kFull, u, k + 1);
+            acc0 = fma(mrow[q][k], u0, acc0);
+            acc1 = fma(mrow[q][k + 1], u1, acc1);
+          }
+          const T acc = acc0 + acc1;
+          d = lane < N ? acc : T(0);
+          if (lane < N) {
+            const double dd = static_cast<double>(acc);
+            xb[static_cast<size_t>(j) * N + lane] =
+                (a.mode == 0) ? xreg[q] - dd : (a.mode == 1 ? dd : xreg[q] + dd);
+          }
+          load_c(j + PF, mrow[q], rreg[q], xreg[q]);
+        }
+      }
     }
   }
 }
@@ -1718,9 +1774,10 @@ cudaError_t launch_seq_chain(const ChainArgs& ch, cudaStream_t s) {
 // per step to compose the tiles) up to n = 16 -- n = 8 in FP64, whose products
 // run on the 1/64-rate pipe -- and the sequential substitution (n^2 per step)
 // above.  Measured on GB300 (FP32 blocks, series*steps/s of a whole step):
-// n = 8 Chaboche 2.26e7 -> 4.38e7, n = 16 neural ODE 5.70e6 -> 6.06e6 with the
-// tiles; n = 20 mass-damper-spring 1.79e7 -> 1.57e7 and n = 32 neural ODE
-// 3.02e6 -> 2.42e6, so the wider blocks keep the sequential solve.
+// n = 8 Chaboche 2.26e7 -> 4.38e7 (6.0e7 with the blocks read ahead), n = 16
+// neural ODE 5.70e6 -> 6.06e6 with the tiles; n = 20 mass-damper-spring
+// 1.79e7 -> 1.57e7 and n = 32 neural ODE 3.02e6 -> 2.42e6, so the wider blocks
+// keep the sequential solve.
 template <typename T>
 cudaError_t launch_chain(const ChainArgs& ch, cudaStream_t s) {
   const int tile_max = sizeof(T) == sizeof(double) ? 8 : 16;
