@@ -7,7 +7,8 @@ import numpy as np
 
 from . import build as _build
 
-KIND_IDS = {"linear": 0, "vdp": 1, "mlp_tanh": 2, "mlp_silu": 3, "mds": 4, "chaboche": 5}
+KIND_IDS = {"linear": 0, "vdp": 1, "mlp_tanh": 2, "mlp_silu": 3, "mds": 4, "chaboche": 5,
+            "neuron": 6}
 
 _lock = threading.Lock()
 _lib = None

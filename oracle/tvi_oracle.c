@@ -28,6 +28,7 @@ int tvo_param_count(const tvo_model* m) {
     case TVO_VDP: return m->n == 2 ? 1 : -1;
     case TVO_MDS: return m->n % 2 == 0 ? 3 * (m->n / 2) + 2 : -1;
     case TVO_CHABOCHE: return m->n >= 3 ? 2 * (m->n - 2) + 8 : -1;
+    case TVO_NEURON: return m->n % 4 == 0 ? 15 * (m->n / 4) + 1 : -1;
     case TVO_MLP_TANH:
     case TVO_MLP_SILU:
       if (m->h1 <= 0 || m->h2 <= 0) return -1;
@@ -142,8 +143,43 @@ static chab_flow chab_eval(int u, const double* p, const double* y) {
   return c;
 }
 
+/* Coupled neurons: the ionic current sum of neuron i (the bracket of V_i' without
+ * the applied current), its derivatives over V_i, m_i, h_i, n_i. */
+typedef struct {
+  double curr, dV, dm, dh, dn;
+} neuron_terms;
+
+static neuron_terms neuron_eval(const double* q, double V, double mm, double hh, double nn) {
+  /* q: the neuron's 15 parameters */
+  const double gNa = q[1], ENa = q[2], gK = q[3], EK = q[4], gL = q[5], EL = q[6];
+  neuron_terms r;
+  const double m3 = mm * mm * mm, n4 = nn * nn * nn * nn;
+  r.curr = -gNa * m3 * hh * (V - ENa) - gK * n4 * (V - EK) - gL * (V - EL);
+  r.dV = -gNa * m3 * hh - gK * n4 - gL;
+  r.dm = -3.0 * gNa * mm * mm * hh * (V - ENa);
+  r.dh = -gNa * m3 * (V - ENa);
+  r.dn = -4.0 * gK * nn * nn * nn * (V - EK);
+  return r;
+}
+
 void tvo_rhs(const tvo_model* m, const double* p, const double* y, double t, double* h) {
   int n = m->n;
+  if (m->kind == TVO_NEURON) {
+    int u = n / 4;
+    const double Ia = p[15 * u];
+    for (int i = 0; i < u; ++i) {
+      const double* q = p + 15 * i;
+      const double* yi = y + 4 * i;
+      neuron_terms r = neuron_eval(q, yi[0], yi[1], yi[2], yi[3]);
+      double coup = 0.0;
+      for (int j = 0; j < u; ++j) coup += yi[0] - y[4 * j];
+      h[4 * i] = (r.curr + Ia * sin(kTwoPi * t / q[14]) + q[13] * coup) / q[0];
+      h[4 * i + 1] = (q[7] - yi[1]) / q[8];
+      h[4 * i + 2] = (q[9] - yi[2]) / q[10];
+      h[4 * i + 3] = (q[11] - yi[3]) / q[12];
+    }
+    return;
+  }
   if (m->kind == TVO_CHABOCHE) {
     int u = n - 2;
     const double *C = p + 6, *g = p + 6 + u;
@@ -184,6 +220,26 @@ void tvo_rhs(const tvo_model* m, const double* p, const double* y, double t, dou
 void tvo_jac(const tvo_model* m, const double* p, const double* y, double t, double* j) {
   (void)t;
   int n = m->n;
+  if (m->kind == TVO_NEURON) {
+    int u = n / 4;
+    memset(j, 0, sizeof(double) * n * n);
+    for (int i = 0; i < u; ++i) {
+      const double* q = p + 15 * i;
+      const double* yi = y + 4 * i;
+      neuron_terms r = neuron_eval(q, yi[0], yi[1], yi[2], yi[3]);
+      double* rowV = j + (4 * i) * n;
+      /* coupling gC sum_j (V_i - V_j): + gC (u - 1) on V_i, - gC on every other V_j */
+      for (int k = 0; k < u; ++k) rowV[4 * k] = (k == i ? q[13] * (u - 1) : -q[13]) / q[0];
+      rowV[4 * i] += r.dV / q[0];
+      rowV[4 * i + 1] = r.dm / q[0];
+      rowV[4 * i + 2] = r.dh / q[0];
+      rowV[4 * i + 3] = r.dn / q[0];
+      j[(4 * i + 1) * n + 4 * i + 1] = -1.0 / q[8];
+      j[(4 * i + 2) * n + 4 * i + 2] = -1.0 / q[10];
+      j[(4 * i + 3) * n + 4 * i + 3] = -1.0 / q[12];
+    }
+    return;
+  }
   if (m->kind == TVO_CHABOCHE) {
     int u = n - 2;
     const double *C = p + 6, *g = p + 6 + u;
@@ -270,6 +326,41 @@ void tvo_jac(const tvo_model* m, const double* p, const double* y, double t, dou
 void tvo_vjp_p(const tvo_model* m, const double* p, const double* y, double t, const double* a,
                double scale, double* gp) {
   int n = m->n;
+  if (m->kind == TVO_NEURON) {
+    int u = n / 4;
+    const double Ia = p[15 * u];
+    for (int i = 0; i < u; ++i) {
+      const double* q = p + 15 * i;
+      double* g = gp + 15 * i;
+      const double* yi = y + 4 * i;
+      const double V = yi[0], mm = yi[1], hh = yi[2], nn = yi[3];
+      const double m3h = mm * mm * mm * hh, n4 = nn * nn * nn * nn;
+      const double aV = a[4 * i] / q[0];  /* weight of the bracket of V_i' */
+      neuron_terms r = neuron_eval(q, V, mm, hh, nn);
+      double coup = 0.0;
+      for (int k = 0; k < u; ++k) coup += V - y[4 * k];
+      const double s = sin(kTwoPi * t / q[14]);
+      const double bracket = r.curr + Ia * s + q[13] * coup;
+      g[0] += scale * a[4 * i] * (-bracket / (q[0] * q[0]));  /* C */
+      g[1] += scale * aV * (-m3h * (V - q[2]));               /* gNa */
+      g[2] += scale * aV * (q[1] * m3h);                      /* ENa */
+      g[3] += scale * aV * (-n4 * (V - q[4]));                /* gK */
+      g[4] += scale * aV * (q[3] * n4);                       /* EK */
+      g[5] += scale * aV * (-(V - q[6]));                     /* gL */
+      g[6] += scale * aV * q[5];                              /* EL */
+      g[7] += scale * a[4 * i + 1] / q[8];                    /* m_inf */
+      g[8] += scale * a[4 * i + 1] * (-(q[7] - mm) / (q[8] * q[8]));  /* tau_m */
+      g[9] += scale * a[4 * i + 2] / q[10];                   /* h_inf */
+      g[10] += scale * a[4 * i + 2] * (-(q[9] - hh) / (q[10] * q[10]));  /* tau_h */
+      g[11] += scale * a[4 * i + 3] / q[12];                  /* n_inf */
+      g[12] += scale * a[4 * i + 3] * (-(q[11] - nn) / (q[12] * q[12]));  /* tau_n */
+      g[13] += scale * aV * coup;                             /* gC */
+      const double ph = kTwoPi * t / q[14];
+      g[14] += scale * aV * Ia * cos(ph) * (-ph / q[14]);     /* T */
+      gp[15 * u] += scale * aV * s;                           /* I_a */
+    }
+    return;
+  }
   if (m->kind == TVO_CHABOCHE) {
     /* p = [E, m, eta, sigma0, Kinf, tau, C_1..C_u, g_1..g_u, ed_a, T] */
     int u = n - 2;

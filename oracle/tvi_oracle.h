@@ -44,6 +44,13 @@
  *                   sigma' = E (ed_a sin(2 pi t / T) - ep)
  *                   K'     = tau (K_inf - K)
  *                   X_i'   = 2/3 C_i ep - g_i X_i |ep|
+ *   TVO_NEURON    u = n / 4 coupled neurons (Sec. 5.1.1, Table neuron-params),
+ *                 y = [V_1, m_1, h_1, n_1, V_2, ...], per neuron i the 15 values
+ *                 p[15 i ..] = [C, gNa, ENa, gK, EK, gL, EL, m_inf, tau_m, h_inf,
+ *                 tau_h, n_inf, tau_n, gC, T], then p[15 u] = I_a  (P = 15 u + 1):
+ *                   V_i' = (-gNa m^3 h (V - ENa) - gK n^4 (V - EK) - gL (V - EL)
+ *                           + I_a sin(2 pi t / T) + gC sum_j (V_i - V_j)) / C
+ *                   m_i' = (m_inf - m) / tau_m   (h and n alike)
  * MLP parameter layout (flat, FP64): W1[h1][n] b1[h1] W2[h2][h1] b2[h2]
  * W3[n][h2] b3[n]; W are row-major (out x in).
  *
@@ -61,12 +68,12 @@ extern "C" {
 #endif
 
 enum { TVO_LINEAR = 0, TVO_VDP = 1, TVO_MLP_TANH = 2, TVO_MLP_SILU = 3, TVO_MDS = 4,
-       TVO_CHABOCHE = 5 };
+       TVO_CHABOCHE = 5, TVO_NEURON = 6 };
 enum { TVO_OK = 0, TVO_NOT_CONVERGED = 1, TVO_NONFINITE = 2, TVO_SINGULAR = 3, TVO_BADARG = -1 };
 
 typedef struct {
   int kind;        /* TVO_LINEAR / TVO_VDP / TVO_MLP_TANH / TVO_MLP_SILU / TVO_MDS /
-                      TVO_CHABOCHE */
+                      TVO_CHABOCHE / TVO_NEURON */
   int n;           /* state size */
   int h1, h2;      /* MLP hidden widths (ignored otherwise) */
   int per_series;  /* 1: params [B][P]; 0: one shared parameter vector [P] */

@@ -23,11 +23,13 @@ Default sizes are the paper-shaped workloads:
                 paper's timing study, 100 series, 2000 uniform steps on [0, 1]
   chaboche      Chaboche viscoplasticity (n = 2 + n_unit), the paper's parameter
                 table, 50 series, 2000 uniform steps on [0, 10]
+  neuron        coupled neurons (n = 4 n_unit), the paper's parameter table,
+                50 series, 2000 uniform steps on [0, 10]
 """
 import numpy as np
 
 SEED_LINEAR, SEED_VDP, SEED_MLP, SEED_PREDICTOR, SEED_MLP_LARGE = 1001, 1002, 1003, 1004, 1005
-SEED_MDS, SEED_CHABOCHE = 1006, 1007
+SEED_MDS, SEED_CHABOCHE, SEED_NEURON = 1006, 1007, 1008
 
 
 def _rng(seed):
@@ -156,6 +158,29 @@ def chaboche(seed=SEED_CHABOCHE, B=50, N=2000, n_unit=3, t_max=10.0, jitter=0.0)
         params = params * np.exp(jitter * _rng(seed).standard_normal(params.shape))
     return {"spec": {"kind": "chaboche", "n": 2 + u, "hidden": (0, 0), "per_series": True},
             "y0": np.zeros((B, 2 + u)), "times": uniform_times(B, N, t_max),
+            "params": params, "lengths": None}
+
+
+def neuron(seed=SEED_NEURON, B=50, N=2000, n_unit=1, t_max=10.0, jitter=0.0):
+    """Coupled neurons (Sec. 5.1.1, Table neuron-params): per neuron C, gNa, ENa,
+    gK, EK, gL, EL, m_inf, h_inf, n_inf linspace over the neurons in [0.1, 1];
+    tau_m, tau_h, tau_n in [0.5, 5], [1.5, 15], [1, 10]; gC in [1e-3, 1e-2];
+    period T in [0.5, 2]; applied amplitude I_a linspace over the series in
+    [0.1, 1]; zero initial state; N uniform steps on [0, t_max].  Per-series
+    parameter vectors: 15 per neuron [C, gNa, ENa, gK, EK, gL, EL, m_inf, tau_m,
+    h_inf, tau_h, n_inf, tau_n, gC, T], then I_a.  jitter > 0 multiplies every
+    parameter by a seeded factor exp(jitter * N(0, 1))."""
+    u = int(n_unit)
+    ls = lambda a, b: np.linspace(a, b, u)  # noqa: E731
+    cols = [ls(0.1, 1.0)] * 7 + [ls(0.1, 1.0), ls(0.5, 5.0), ls(0.1, 1.0), ls(1.5, 15.0),
+                                 ls(0.1, 1.0), ls(1.0, 10.0), ls(1e-3, 1e-2), ls(0.5, 2.0)]
+    per_unit = np.stack(cols, axis=1).reshape(-1)  # [u][15]
+    Ia = np.linspace(0.1, 1.0, B)
+    params = np.concatenate([np.tile(per_unit, (B, 1)), Ia[:, None]], axis=1)
+    if jitter > 0.0:
+        params = params * np.exp(jitter * _rng(seed).standard_normal(params.shape))
+    return {"spec": {"kind": "neuron", "n": 4 * u, "hidden": (0, 0), "per_series": True},
+            "y0": np.zeros((B, 4 * u)), "times": uniform_times(B, N, t_max),
             "params": params, "lengths": None}
 
 
