@@ -60,6 +60,11 @@ WORKLOADS = {
     # study's largest size
     "chaboche_user": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 50, "N": 2000,
                       "refine": 2},
+    # coupled neurons of the paper's timing study (--n-unit neurons, 50 series, 2000
+    # steps on [0, 10]) as a user model; two neurons (n = 8) by default, the most that
+    # the 32-parameter bound of user models holds
+    "neuron_user": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 50, "N": 2000,
+                    "refine": 2},
     "node16": {"chunk": 200, "precision": "bf16", "tol": 1e-8, "B": 64, "N": 2000, "refine": 2},
     "node32": {"chunk": 1000, "precision": "bf16", "tol": 1e-8, "B": 512, "N": 20000,
                "refine": 2},
@@ -84,8 +89,9 @@ def parse():
     ap.add_argument("--refine", type=int, default=None,
                     help="adjoint refinement sweeps (mixed precision)")
     ap.add_argument("--n-unit", type=int, default=None,
-                    help="units: mass-damper-spring (mds_user, default 10) or Chaboche "
-                         "backstresses (chaboche_user, default 5)")
+                    help="units: mass-damper-spring (mds_user, default 10), Chaboche "
+                         "backstresses (chaboche_user, default 5) or neurons (neuron_user, "
+                         "default 2)")
     ap.add_argument("--B", type=int, default=None)
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--baseline-steps", type=int, default=5)
@@ -97,7 +103,7 @@ def parse():
         if getattr(args, k) is None:
             setattr(args, k, v)
     if args.n_unit is None:
-        args.n_unit = 5 if args.workload == "chaboche_user" else 10
+        args.n_unit = {"chaboche_user": 5, "neuron_user": 2}.get(args.workload, 10)
     if args.workload.startswith("node"):
         args.no_chunk1 = True  # the one-step MLP scheme reads status back every Newton update
     return args
@@ -118,6 +124,8 @@ def make_workload(args, rank=0):
         w = workloads.mds(B=args.B, N=args.N, n_unit=args.n_unit)  # the table's values
     elif args.workload == "chaboche_user":
         w = workloads.chaboche(B=args.B, N=args.N, n_unit=args.n_unit)  # the table's values
+    elif args.workload == "neuron_user":
+        w = workloads.neuron(B=args.B, N=args.N, n_unit=args.n_unit)  # the table's values
     elif args.workload == "node16":
         w = workloads.mlp_ode(B=args.B, N=args.N, seed=workloads.SEED_MLP + 1000 * rank)
     else:
@@ -163,6 +171,9 @@ def workload_config(args):
                              f"(n={2 + args.n_unit}), strain rate ed_a sin(2 pi t) with ed_a "
                              "linspace [0.1,1] over the series, as a user model; uniform steps "
                              "on [0,10]",
+            "neuron_user": f"coupled neurons, {args.n_unit} neurons (n={4 * args.n_unit}), "
+                           "current I_a sin(2 pi t/T) with I_a linspace [0.1,1] over the "
+                           "series, as a user model; uniform steps on [0,10]",
             "node16": "neural ODE n=16, MLP 16-64-64-16 tanh, uniform steps on [0,10]",
             "node32": "neural ODE n=32, MLP 32-128-128-32 SiLU, per-series lengths "
                       "U[2000,N] padded, uniform steps on [0,10]"}[args.workload]
@@ -346,6 +357,19 @@ def roofline(args, w, stats, fwd_ms, adj_ms, refine):
         route = "small" if nn <= 4 else "large"
         names = (f"tvi_integrate (user chaboche, {route}-state kernels, {args.precision})",
                  f"tvi_adjoint (user chaboche, {route}-state kernels, {args.precision})")
+    elif args.workload == "neuron_user":
+        # u neurons, n = 4u.  Residual: h (per neuron the three ionic currents with
+        # their powers 13, coupling 2u, current sin and 2, division 1, three gates 6:
+        # 22 + 2u) + R (2 per component: 8) = 30 + 2u per neuron; update y -= d: 4 per
+        # neuron.  Adjoint per step: per refinement sweep J^T a over the V row's
+        # 4 + u and the gates' 3 non-zeros, 3 per component, per neuron 3(7 + u) + 8;
+        # parameter VJP 40 per neuron.  A division, power or sine counts as one.
+        u = args.n_unit
+        fwd_ops = float(np.sum(((upd + nchk) * u * (30.0 + 2.0 * u) + upd * 4.0 * u) * spc))
+        adj_ops = float(B * N * u * (refine * (3.0 * (7.0 + u) + 8.0) + 40.0))
+        route = "small" if u == 1 else "large"
+        names = (f"tvi_integrate (user neuron, {route}-state kernels, {args.precision})",
+                 f"tvi_adjoint (user neuron, {route}-state kernels, {args.precision})")
     elif args.workload.startswith("vdp"):
         # residual on the stored iterate y: h (3) + R (4) = 7; update y -= d: 2
         fwd_ops = float(np.sum(((upd + nchk) * 7.0 + upd * 2.0) * spc))
@@ -425,6 +449,13 @@ def run_ours(args):
     elif args.workload == "chaboche_user":
         from paper_2310_08649_gb300.user_sources import CHABOCHE, chaboche_param_count
         user = tvi.UserModel(2 + args.n_unit, chaboche_param_count(args.n_unit), CHABOCHE)
+        user.prepare(args.precision)
+        if not args.no_chunk1:
+            user.prepare("fp64")
+        model = user.model(per_series=True)
+    elif args.workload == "neuron_user":
+        from paper_2310_08649_gb300.user_sources import NEURON, neuron_param_count
+        user = tvi.UserModel(4 * args.n_unit, neuron_param_count(args.n_unit), NEURON)
         user.prepare(args.precision)
         if not args.no_chunk1:
             user.prepare("fp64")

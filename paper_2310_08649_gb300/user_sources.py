@@ -11,6 +11,8 @@ the time t.
                  (time-dependent; p = [K_1.., C_1.., M_1.., f_a, T], P = 3n/2 + 2)
     CHABOCHE     Chaboche viscoplasticity with n - 2 backstresses under a periodic
                  strain rate (p = [E, m, eta, sigma_0, K_inf, tau, C.., g.., ed_a, T])
+    NEURON       n / 4 coupled neurons under a periodic current (15 parameters per
+                 neuron, then the current amplitude)
 
     import paper_2310_08649_gb300 as tvi
     from paper_2310_08649_gb300.user_sources import VDP
@@ -334,3 +336,90 @@ __device__ void tvi_vjp_p(const double* y, double t, const double* p, const doub
 
 def chaboche_param_count(n_unit):
     return 2 * n_unit + 8
+
+
+NEURON = r"""
+// kU = TVI_N / 4 coupled neurons, y = [V_1, m_1, h_1, n_1, V_2, ...]; per neuron i
+// the 15 values p[15 i ..] = [C, gNa, ENa, gK, EK, gL, EL, m_inf, tau_m, h_inf,
+// tau_h, n_inf, tau_n, gC, T], then p[15 kU] = I_a:
+//   V' = (-gNa m^3 h (V - ENa) - gK n^4 (V - EK) - gL (V - EL)
+//         + I_a sin(2 pi t / T) + gC sum_j (V_i - V_j)) / C
+//   m' = (m_inf - m) / tau_m, and h, n alike
+constexpr int kU = TVI_N / 4;
+
+__device__ void tvi_rhs(const double* y, double t, const double* p, double* h) {
+  const double Ia = p[15 * kU];
+  for (int i = 0; i < kU; ++i) {
+    const double* q = p + 15 * i;
+    const double V = y[4 * i], m = y[4 * i + 1], hh = y[4 * i + 2], n = y[4 * i + 3];
+    double coup = 0.0;
+    for (int j = 0; j < kU; ++j) coup += V - y[4 * j];
+    const double I = -q[1] * m * m * m * hh * (V - q[2]) - q[3] * n * n * n * n * (V - q[4]) -
+                     q[5] * (V - q[6]) + Ia * sin(6.283185307179586 * t / q[14]) + q[13] * coup;
+    h[4 * i] = I / q[0];
+    h[4 * i + 1] = (q[7] - m) / q[8];
+    h[4 * i + 2] = (q[9] - hh) / q[10];
+    h[4 * i + 3] = (q[11] - n) / q[12];
+  }
+}
+
+template <typename T>
+__device__ void tvi_jac(const T* y, double t, const double* p, T* J) {
+  for (int k = 0; k < TVI_N * TVI_N; ++k) J[k] = T(0);
+  for (int i = 0; i < kU; ++i) {
+    const double* q = p + 15 * i;
+    const T V = y[4 * i], m = y[4 * i + 1], hh = y[4 * i + 2], n = y[4 * i + 3];
+    const T C = static_cast<T>(q[0]), gNa = static_cast<T>(q[1]), ENa = static_cast<T>(q[2]);
+    const T gK = static_cast<T>(q[3]), EK = static_cast<T>(q[4]), gL = static_cast<T>(q[5]);
+    const T gC = static_cast<T>(q[13]);
+    T* row = J + 4 * i * TVI_N;
+    for (int j = 0; j < kU; ++j) row[4 * j] = (j == i ? gC * T(kU - 1) : -gC) / C;
+    row[4 * i] += (-gNa * m * m * m * hh - gK * n * n * n * n - gL) / C;
+    row[4 * i + 1] = -T(3) * gNa * m * m * hh * (V - ENa) / C;
+    row[4 * i + 2] = -gNa * m * m * m * (V - ENa) / C;
+    row[4 * i + 3] = -T(4) * gK * n * n * n * (V - EK) / C;
+    J[(4 * i + 1) * TVI_N + 4 * i + 1] = -T(1) / static_cast<T>(q[8]);
+    J[(4 * i + 2) * TVI_N + 4 * i + 2] = -T(1) / static_cast<T>(q[10]);
+    J[(4 * i + 3) * TVI_N + 4 * i + 3] = -T(1) / static_cast<T>(q[12]);
+  }
+}
+
+__device__ void tvi_vjp_p(const double* y, double t, const double* p, const double* a,
+                          double* g) {
+  const double Ia = p[15 * kU];
+  g[15 * kU] = 0.0;
+  for (int i = 0; i < kU; ++i) {
+    const double* q = p + 15 * i;
+    double* gi = g + 15 * i;
+    const double V = y[4 * i], m = y[4 * i + 1], hh = y[4 * i + 2], n = y[4 * i + 3];
+    const double m3h = m * m * m * hh, n4 = n * n * n * n;
+    double coup = 0.0;
+    for (int j = 0; j < kU; ++j) coup += V - y[4 * j];
+    const double ph = 6.283185307179586 * t / q[14];
+    const double s = sin(ph);
+    const double I = -q[1] * m3h * (V - q[2]) - q[3] * n4 * (V - q[4]) - q[5] * (V - q[6]) +
+                     Ia * s + q[13] * coup;
+    const double aV = a[4 * i] / q[0];
+    gi[0] = -a[4 * i] * I / (q[0] * q[0]);
+    gi[1] = -aV * m3h * (V - q[2]);
+    gi[2] = aV * q[1] * m3h;
+    gi[3] = -aV * n4 * (V - q[4]);
+    gi[4] = aV * q[3] * n4;
+    gi[5] = -aV * (V - q[6]);
+    gi[6] = aV * q[5];
+    gi[7] = a[4 * i + 1] / q[8];
+    gi[8] = -a[4 * i + 1] * (q[7] - m) / (q[8] * q[8]);
+    gi[9] = a[4 * i + 2] / q[10];
+    gi[10] = -a[4 * i + 2] * (q[9] - hh) / (q[10] * q[10]);
+    gi[11] = a[4 * i + 3] / q[12];
+    gi[12] = -a[4 * i + 3] * (q[11] - n) / (q[12] * q[12]);
+    gi[13] = aV * coup;
+    gi[14] = -aV * Ia * cos(ph) * ph / q[14];
+    g[15 * kU] += aV * s;
+  }
+}
+"""
+
+
+def neuron_param_count(n_unit):
+    return 15 * n_unit + 1

@@ -16,8 +16,9 @@ import pytest
 import workloads
 from oracle import Model as OModel
 from test_gpu_euler import fe_error_estimate
-from paper_2310_08649_gb300.user_sources import CHABOCHE, LINEAR, MDS, VDP, VDP_FP64_JAC, \
-    chaboche_param_count, mds_param_count, mlp_param_count, mlp_tanh
+from paper_2310_08649_gb300.user_sources import CHABOCHE, LINEAR, MDS, NEURON, VDP, \
+    VDP_FP64_JAC, chaboche_param_count, mds_param_count, mlp_param_count, mlp_tanh, \
+    neuron_param_count
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -50,6 +51,8 @@ def users(tvi):
             "lin5": tvi.UserModel(5, 25, LINEAR),
             **{f"chab{u}": tvi.UserModel(2 + u, chaboche_param_count(u), CHABOCHE)
                for u in (1, 2, 3, 5)},
+            **{f"neuron{u}": tvi.UserModel(4 * u, neuron_param_count(u), NEURON)
+               for u in (1, 2)},
             "mlp5": tvi.UserModel(5, mlp_param_count(5, 2, 1), mlp_tanh(2, 1))}
     yield made
     torch.cuda.synchronize()
@@ -301,6 +304,34 @@ def test_user_chaboche_matches_oracle(tvi, users, oracle_lib, precision, u, chun
     bad = np.nonzero(err > np.maximum(GATE[precision], 10.0 * est))[0]
     assert bad.size == 0, (bad, err[bad], est[bad])
     g = workloads.random_grad_out(190 + u, 12, 2000, 2 + u)
+    dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g)
+    dp, dy0 = adjoint(tvi, model, w, o, ref, g)
+    e_p = np.abs(dp - dp_ref).max(axis=1) / np.abs(dp_ref).max(axis=1)
+    assert e_p.max() <= GATE[precision], (e_p.argmax(), e_p.max())
+    assert relerr(dy0, dy0_ref) <= GATE[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("u,chunk", [(1, 500), (2, 1000), (2, 64)])
+def test_user_neuron_matches_oracle(tvi, users, oracle_lib, precision, u, chunk):
+    """Coupled neurons under a periodic current: one neuron (n = 4, fused
+    kernels) and two (n = 8, the large-state route); parameters from the
+    paper's table jittered per series."""
+    w = workloads.neuron(B=16, N=2000, n_unit=u, jitter=0.1, seed=230 + u)
+    m = OModel.from_spec(w["spec"])
+    tol = 1e-12
+    ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], tol_abs=tol)
+    assert not st.any()
+    est = oracle_lib.forward_error_estimate(m, w["times"], w["params"], ref, tol)
+    model = users[f"neuron{u}"].model(per_series=True)
+    o = tvi.Options(chunk=chunk, tol_abs=tol, max_iter=60, precision=precision,
+                    adjoint_refine=3)
+    y, _, status, rc = forward(tvi, model, w, o)
+    assert rc == 0 and not status.any()
+    err = relerr_series(y, ref)
+    bad = np.nonzero(err > np.maximum(GATE[precision], 10.0 * est))[0]
+    assert bad.size == 0, (bad, err[bad], est[bad])
+    g = workloads.random_grad_out(240 + u, 16, 2000, 4 * u)
     dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g)
     dp, dy0 = adjoint(tvi, model, w, o, ref, g)
     e_p = np.abs(dp - dp_ref).max(axis=1) / np.abs(dp_ref).max(axis=1)
