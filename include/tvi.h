@@ -294,7 +294,8 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
  * built-in models); a plain FP64 tvi_jac is evaluated in FP64 and rounded.
  * The library trusts them: J must be the Jacobian of h for Newton to converge
  * quadratically, and g its parameter product for the gradients to be those of
- * the discrete loss.  Sizes 1 <= n <= 32 and 1 <= P <= 32; FP64 or FP32 blocks
+ * the discrete loss.  Sizes 1 <= n <= 32; 1 <= P <= 32 for n <= 4, 1 <= P <= 64
+ * above (more than 32 are read from memory, not held in registers); FP64 or FP32 blocks
  * (BF16: TVI_EUNSUPPORTED); per-series or shared parameters; no Newton
  * predictor.  n <= 4 also has forward Euler, retry_halving and
  * tvi_adjoint_noalloc; n > 4 needs the workspace of tvi_workspace_bytes, does

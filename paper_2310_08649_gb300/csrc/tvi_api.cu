@@ -370,9 +370,12 @@ tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, in
 tvi_status tvi_user_model_create(int n, int P, const char* source, tvi_user_model** out) {
   g_last_error.clear();
   if (!out || !source) return fail(TVI_EINVAL, "tvi_user_model_create: NULL source or out");
-  if (n < 1 || n > tvi::kUserMaxN || P < 1 || P > tvi::kUserMaxP)
-    return fail(TVI_EINVAL, "user models take 1 <= n <= %d and 1 <= P <= %d (got n %d, P %d)",
-                tvi::kUserMaxN, tvi::kUserMaxP, n, P);
+  const int pmax = n <= tvi::kUserSmallMaxN ? tvi::kUserMaxP : tvi::kUserMaxPLarge;
+  if (n < 1 || n > tvi::kUserMaxN || P < 1 || P > pmax)
+    return fail(TVI_EINVAL,
+                "user models take 1 <= n <= %d and 1 <= P <= %d (%d for n <= %d; got n %d, "
+                "P %d)",
+                tvi::kUserMaxN, tvi::kUserMaxPLarge, tvi::kUserMaxP, tvi::kUserSmallMaxN, n, P);
   std::string err;
   tvi_user_model* m = nullptr;
   int rc = tvi::user_create(n, P, source, &m, &err);

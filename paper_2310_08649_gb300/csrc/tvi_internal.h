@@ -119,7 +119,9 @@ cudaError_t small_sum_partials(const AdjArgs& a, int P, cudaStream_t s);
 enum { kJitOk = 0, kJitNoNvrtc = 1, kJitCompile = 2, kJitCuda = 3 };
 constexpr int kUserSmallMaxN = 4;  // fused one-block-per-series kernels up to here
 constexpr int kUserMaxN = 32;      // large-state kernels above
-constexpr int kUserMaxP = 32;
+constexpr int kUserMaxP = 32;       // parameters of fused-kernel models (held in registers)
+constexpr int kUserMaxPLarge = 64;  // parameters of large-state models (read from memory
+                                    // above 32)
 bool user_valid(const tvi_user_model* m);
 int user_n(const tvi_user_model* m);
 int user_P(const tvi_user_model* m);

@@ -139,17 +139,32 @@ struct TviTypedJac<T, typename TviVoid<decltype(tvi_jac(tvi_declval<const T*>(),
   static constexpr bool value = true;
 };
 
+// the series' parameters: copied to registers up to 32, else read where they lie
+template <int NP_, bool kInRegs>
+struct TviParams {
+  double v[NP_];
+  __device__ __forceinline__ void load(const double* src) {
+#pragma unroll
+    for (int q = 0; q < NP_; ++q) v[q] = src[q];
+  }
+  __device__ __forceinline__ operator const double*() const { return v; }
+};
+template <int NP_>
+struct TviParams<NP_, false> {
+  const double* v;
+  __device__ __forceinline__ void load(const double* src) { v = src; }
+  __device__ __forceinline__ operator const double*() const { return v; }
+};
+
 struct TviUserModel {
   static constexpr int NS = TVI_N;
   static constexpr int NP = TVI_P;
   static constexpr bool kPredictable = false;  // no learned predictor for user models
-  double p[NP];                                // the series' parameters, in registers
+  TviParams<NP, (NP <= 32)> p;
 
   __device__ __forceinline__ float param_feature() const { return 0.0f; }
   __device__ __forceinline__ void load(const double* params, int b, int per_series) {
-    const double* src = params + (per_series ? static_cast<unsigned long long>(b) * NP : 0ull);
-#pragma unroll
-    for (int q = 0; q < NP; ++q) p[q] = src[q];
+    p.load(params + (per_series ? static_cast<unsigned long long>(b) * NP : 0ull));
   }
   __device__ __forceinline__ void rhs(const double (&y)[NS], double t, double (&h)[NS]) const {
     tvi_rhs(y, t, p, h);

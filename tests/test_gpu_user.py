@@ -1,12 +1,14 @@
-"""GPU parity of user models (device source compiled at run time into the fused
-small-state kernels) with the CPU FP64 oracle, through the C ABI.
+"""GPU parity of user models (device source compiled at run time: n <= 4 into
+the fused small-state kernels, larger n into the large-state kernels) with the
+CPU FP64 oracle, through the C ABI.
 
 Each user source restates one of the oracle's models (van der Pol, linear of
-any size, a tanh MLP), so forward trajectories and adjoint gradients are
-compared with the oracle exactly as for the built-in models: 1e-10 relative
-with FP64 blocks, 1e-5 with FP32 blocks, and for van der Pol max(gate, 10 x the
-propagated forward-error estimate) per series.  The sizes are ones the
-built-in kernels do not have (n = 1, 3) besides van der Pol itself.
+any size, a tanh MLP, the mass-damper-spring chain, Chaboche viscoplasticity,
+coupled neurons), so forward trajectories and adjoint gradients are compared
+with the oracle exactly as for the built-in models: 1e-10 relative with FP64
+blocks, 1e-5 with FP32 blocks, and for nonlinear models max(gate, 10 x the
+propagated forward-error estimate) per series.  Sizes run from n = 1 to 20,
+most of them ones the built-in engines do not have.
 """
 import ctypes
 
@@ -52,7 +54,7 @@ def users(tvi):
             **{f"chab{u}": tvi.UserModel(2 + u, chaboche_param_count(u), CHABOCHE)
                for u in (1, 2, 3, 5)},
             **{f"neuron{u}": tvi.UserModel(4 * u, neuron_param_count(u), NEURON)
-               for u in (1, 2)},
+               for u in (1, 2, 4)},
             "mlp5": tvi.UserModel(5, mlp_param_count(5, 2, 1), mlp_tanh(2, 1))}
     yield made
     torch.cuda.synchronize()
@@ -312,11 +314,12 @@ def test_user_chaboche_matches_oracle(tvi, users, oracle_lib, precision, u, chun
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("u,chunk", [(1, 500), (2, 1000), (2, 64)])
+@pytest.mark.parametrize("u,chunk", [(1, 500), (2, 1000), (2, 64), (4, 1000)])
 def test_user_neuron_matches_oracle(tvi, users, oracle_lib, precision, u, chunk):
     """Coupled neurons under a periodic current: one neuron (n = 4, fused
-    kernels) and two (n = 8, the large-state route); parameters from the
-    paper's table jittered per series."""
+    kernels), two and four (n = 8 and 16, the large-state route; four neurons
+    have 61 parameters, read from memory); parameters from the paper's table
+    jittered per series."""
     w = workloads.neuron(B=16, N=2000, n_unit=u, jitter=0.1, seed=230 + u)
     m = OModel.from_spec(w["spec"])
     tol = 1e-12

@@ -62,7 +62,7 @@ def test_missing_function_is_rejected(lib):
     assert rc == EINVAL and "tvi_vjp_p" in _lib.last_error()
 
 
-@pytest.mark.parametrize("n,P", [(0, 1), (33, 1), (2, 0), (2, 33), (-1, -1)])
+@pytest.mark.parametrize("n,P", [(0, 1), (33, 1), (2, 0), (2, 33), (5, 65), (-1, -1)])
 def test_bad_sizes(lib, n, P):
     rc, h = create(lib, n, P, VDP)
     assert rc == EINVAL and h.value is None
@@ -108,6 +108,16 @@ def test_prepare_large_state_route(lib, precision):
     v = tvi.UserModel(5, 25, LINEAR)
     v.prepare(precision)
     v.close()
+
+
+def test_large_route_takes_64_parameters(lib):
+    """Above n = 4 up to 64 parameters (read from memory past 32): four coupled
+    neurons, 61 parameters."""
+    from paper_2310_08649_gb300.user_sources import NEURON, neuron_param_count
+    u = tvi.UserModel(16, neuron_param_count(4), NEURON)
+    assert u.model().param_count() == 61
+    u.prepare("fp32")
+    u.close()
 
 
 def test_prepare_rejects_bf16(lib):
