@@ -160,6 +160,7 @@ struct TviUserModel {
   static constexpr int NS = TVI_N;
   static constexpr int NP = TVI_P;
   static constexpr bool kPredictable = false;  // no learned predictor for user models
+  static constexpr bool kUsesTime = true;
   TviParams<NP, (NP <= 32)> p;
 
   __device__ __forceinline__ float param_feature() const { return 0.0f; }

@@ -8,8 +8,8 @@
 //   rhs(y, t, h)                   FP64 h(y, t)                (residual: always FP64)
 //   step_matrix<T>(y, t, dt, A)    A = I - dt j(y, t) in T     (block: FP32 or FP64)
 //   vjp_p(y, t, a, scale, acc)     acc[NP] += scale (dh/dp)^T a at (y, t)   (FP64)
-// The models here are autonomous and ignore t (the kernels' loads of t then
-// compile away); run-time compiled user models may use it.
+// The models here are autonomous (kUsesTime = false: the kernels then pass t =
+// 0 without loading it); run-time compiled user models use it.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,6 +21,7 @@ struct ModelVdp {
   static constexpr int NS = 2;
   static constexpr int NP = 1;
   static constexpr bool kPredictable = true;  // learned Newton predictor available
+  static constexpr bool kUsesTime = false;
   double mu;
   // predictor feature of the parameter
   __device__ __forceinline__ float param_feature() const { return log10f(static_cast<float>(mu)); }
@@ -54,6 +55,7 @@ struct ModelLinear {
   static constexpr int NS = N_;
   static constexpr int NP = N_ * N_;
   static constexpr bool kPredictable = false;
+  static constexpr bool kUsesTime = false;
   double A[N_][N_];
   __device__ __forceinline__ float param_feature() const { return 0.0f; }
 

@@ -11,6 +11,14 @@
 namespace tvi {
 namespace kern {
 
+// time t_k of a model evaluation; models that ignore t (Model::kUsesTime false)
+// get 0 without a load, so the time lookups leave their kernels unchanged
+template <class Model>
+__device__ __forceinline__ double model_time(const double* tb, int k) {
+  if constexpr (Model::kUsesTime) return tb[k];
+  else return 0.0;
+}
+
 // Infinity norm of the chunk residual R_j = dy_j - dy_{j-1} - dt_j h(y_i + dy_j)
 // for increments dyv, over the whole block (every thread calls it; full-block
 // barriers).  Returns the FP64 bit pattern of the max (NaN/Inf compare high).
@@ -39,7 +47,7 @@ __device__ __forceinline__ unsigned long long residual_norm_block(
     double y[NS], h[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) y[s] = yi[s] + dyv[r][s];
-    mdl.rhs(y, act[r] ? tb[k0 + r] : 0.0, h);  // row r is step k0 + r
+    mdl.rhs(y, act[r] ? model_time<Model>(tb, k0 + r) : 0.0, h);  // row r is step k0 + r
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const double pv = (r == 0) ? prev[s] : dyv[r - 1][s];
@@ -254,7 +262,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
             yh[s] = fwd_euler ? yp[s] : yv[r][s];
           }
           const int k = i + 1 + tid * RPT + r;
-          mdl.rhs(yh, act[r] ? tb[fwd_euler ? k - 1 : k] : 0.0, h);
+          mdl.rhs(yh, act[r] ? model_time<Model>(tb, fwd_euler ? k - 1 : k) : 0.0, h);
 #pragma unroll
           for (int s = 0; s < NS; ++s) {
             R[r][s] = act[r] ? fma(-dt[r], h[s], yv[r][s] - yp[s]) : 0.0;
@@ -317,7 +325,8 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
               }
             }
             const int k = i + 1 + tid * RPT + r;
-            mdl.step_matrix(yt, tb[fwd_euler ? k - 1 : k], dtT[r], A);  // A = I - dt j
+            mdl.step_matrix(yt, model_time<Model>(tb, fwd_euler ? k - 1 : k), dtT[r],
+                            A);  // A = I - dt j
             T Rt[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) Rt[q] = narrow<T>(R[r][q]);
@@ -511,7 +520,8 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
         T yt[NS], A[NS][NS], Ai[NS][NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) yt[s] = narrow<T>(yk[r][s]);
-        mdl.step_matrix(yt, tb[k], narrow<T>(dtb[r]), A);  // A = I - dt j(y_k, t_k)
+        mdl.step_matrix(yt, model_time<Model>(tb, k), narrow<T>(dtb[r]),
+                        A);  // A = I - dt j(y_k, t_k)
         if (fwd_euler) {
           // x_q = (2I - A)^T x_{q-1} + g_k, the carry a_{i+L+1} entering row 0
 #pragma unroll
@@ -577,7 +587,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
       for (int r = 0; r < RPT; ++r) {
         double A[NS][NS];
         const int k = i + L - (tid * RPT + r);
-        mdl.step_matrix(yk[r], act[r] ? tb[k] : 0.0, dtb[r], A);
+        mdl.step_matrix(yk[r], act[r] ? model_time<Model>(tb, k) : 0.0, dtb[r], A);
         double res[NS];
 #pragma unroll
         for (int p = 0; p < NS; ++p) {
@@ -621,9 +631,9 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) adjoint_small_kernel(A
           double ykm[NS];
 #pragma unroll
           for (int s = 0; s < NS; ++s) ykm[s] = yb[static_cast<size_t>(k - 1) * NS + s];
-          mdl.vjp_p(ykm, tb[k - 1], av[r], dt[r], acc);
+          mdl.vjp_p(ykm, model_time<Model>(tb, k - 1), av[r], dt[r], acc);
         } else {
-          mdl.vjp_p(yk[r], tb[i + L - (tid * RPT + r)], av[r], dt[r], acc);
+          mdl.vjp_p(yk[r], model_time<Model>(tb, i + L - (tid * RPT + r)), av[r], dt[r], acc);
         }
       }
     }  // wact
