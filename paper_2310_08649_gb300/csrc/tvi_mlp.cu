@@ -1776,8 +1776,9 @@ cudaError_t launch_seq_chain(const ChainArgs& ch, cudaStream_t s) {
 // above.  Measured on GB300 (FP32 blocks, series*steps/s of a whole step):
 // n = 8 Chaboche 2.26e7 -> 4.38e7 (6.0e7 with the blocks read ahead), n = 16
 // neural ODE 5.70e6 -> 6.06e6 with the tiles; n = 20 mass-damper-spring
-// 1.79e7 -> 1.57e7 and n = 32 neural ODE 3.02e6 -> 2.42e6, so the wider blocks
-// keep the sequential solve.
+// 1.79e7 -> 1.57e7 (1.84e7 with the blocks read ahead: even, at slightly more
+// Newton updates) and n = 32 neural ODE 3.02e6 -> 2.42e6 (2.46e6), so the wider
+// blocks keep the sequential solve.
 template <typename T>
 cudaError_t launch_chain(const ChainArgs& ch, cudaStream_t s) {
   const int tile_max = sizeof(T) == sizeof(double) ? 8 : 16;
