@@ -76,3 +76,76 @@ def test_argument_errors_are_returned_without_touching_the_gpu(lib):
     assert call(m, Options().c(), ws_bytes=8) == -2
     assert "workspace" in lib.tvi_last_error().decode()
     assert call(m, Options().c(), B=0) == 0
+
+
+C_PROGRAM = r"""
+/* A C99 caller of the ABI: options, parameter counts, argument errors and a
+ * user model compiled from device source, all without a GPU. */
+#include <stdio.h>
+#include <string.h>
+#include "tvi.h"
+
+static const char* kSource =
+    "__device__ void tvi_rhs(const double* y, double t, const double* p, double* h) {\n"
+    "  h[0] = -p[0] * y[0];\n"
+    "}\n"
+    "__device__ void tvi_jac(const double* y, double t, const double* p, double* J) {\n"
+    "  J[0] = -p[0];\n"
+    "}\n"
+    "__device__ void tvi_vjp_p(const double* y, double t, const double* p, const double* a,\n"
+    "                          double* g) {\n"
+    "  g[0] = -a[0] * y[0];\n"
+    "}\n";
+
+int main(void) {
+  tvi_options o;
+  tvi_model m;
+  tvi_user_model* u = NULL;
+  tvi_default_options(&o);
+  if (o.chunk != 1 || o.precision != TVI_PREC_FP64 || o.scheme != TVI_BACKWARD_EULER) return 1;
+  memset(&m, 0, sizeof m);
+  m.kind = TVI_MODEL_VDP;
+  m.n = 2;
+  if (tvi_param_count(&m) != 1) return 2;
+  if (tvi_integrate(&m, &o, -1, 10, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, 0, NULL)
+      != TVI_EINVAL)
+    return 3;
+  if (tvi_user_model_create(1, 1, kSource, &u) != TVI_OK || u == NULL) {
+    printf("%s\n", tvi_last_error());
+    return 4;
+  }
+  m.kind = TVI_MODEL_USER;
+  m.n = 1;
+  m.user = u;
+  if (tvi_param_count(&m) != 1) return 5;
+  if (tvi_user_model_prepare(u, TVI_PREC_FP32) != TVI_OK) return 6;
+  tvi_user_model_destroy(u);
+  printf("ok %s\n", tvi_version());
+  return 0;
+}
+"""
+
+
+def test_header_is_c99_and_the_library_links_from_c(lib, tmp_path):
+    """include/tvi.h compiles as strict C99 and a C program linked against
+    libtvi.so runs the host side of the ABI (NVRTC needed for the user model)."""
+    import shutil
+    import subprocess
+    from paper_2310_08649_gb300 import _lib
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "caller.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(_lib.LIB_PATH)
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+           "-L", libdir, "-ltvi", "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    if r.returncode == 4 and "could not be loaded" in r.stdout:
+        pytest.skip("NVRTC is not available")
+    assert r.returncode == 0 and r.stdout.startswith("ok tvi"), (r.returncode, r.stdout,
+                                                                  r.stderr)
