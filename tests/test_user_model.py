@@ -126,3 +126,35 @@ def test_prepare_rejects_bf16(lib):
         u.prepare("bf16")
     assert e.value.code == EUNSUPPORTED
     u.close()
+
+
+def test_large_route_host_checks(lib):
+    """Without a GPU: the workspace of a large-state user model grows with the
+    chunk, and forward Euler, BF16 blocks and the allocation-free adjoint are
+    rejected on that route before anything is launched."""
+    u = tvi.UserModel(20, mds_param_count(10), MDS)
+    m = u.model(per_series=True).c()
+    o = _lib.TviOptions()
+    lib.tvi_default_options(ctypes.byref(o))
+    o.precision = 1
+    o.chunk = 100
+    w100 = lib.tvi_workspace_bytes(ctypes.byref(m), ctypes.byref(o), 8, 1000)
+    o.chunk = 1000
+    w1000 = lib.tvi_workspace_bytes(ctypes.byref(m), ctypes.byref(o), 8, 1000)
+    assert 0 < w100 < w1000
+    # 8 series x 1000 steps x 20 x 20 FP32 blocks at least
+    assert w1000 >= 8 * 1000 * 20 * 20 * 4
+    o.scheme = 1  # forward Euler
+    rc = lib.tvi_integrate(ctypes.byref(m), ctypes.byref(o), 8, 1000, None, None, None, None,
+                           None, None, None, None, 0, None)
+    assert rc == EUNSUPPORTED and "forward Euler" in _lib.last_error()
+    o.scheme = 0
+    o.precision = 2  # BF16
+    rc = lib.tvi_integrate(ctypes.byref(m), ctypes.byref(o), 8, 1000, None, None, None, None,
+                           None, None, None, None, 0, None)
+    assert rc == EUNSUPPORTED
+    o.precision = 1
+    rc = lib.tvi_adjoint_noalloc(ctypes.byref(m), ctypes.byref(o), 8, 1000, None, None, None,
+                                 None, None, None, None, None)
+    assert rc == EUNSUPPORTED and "noalloc" in _lib.last_error()
+    u.close()
