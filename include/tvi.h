@@ -126,7 +126,7 @@ typedef struct {
                               used for chunk attempts of exactly this length */
   int predictor_hidden;    /* hidden width of the predictor MLP (even, <= 256) */
   int scheme;              /* tvi_scheme: TVI_BACKWARD_EULER (default) or
-                              TVI_FORWARD_EULER (linear and van der Pol models) */
+                              TVI_FORWARD_EULER (linear, van der Pol and user models) */
 } tvi_options;
 
 /* Fill *opt with defaults: chunk 1, tol_abs 1e-8, tol_rel 0, max_iter 50, FP64,
@@ -297,10 +297,9 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
  * the discrete loss.  Sizes 1 <= n <= 32; 1 <= P <= 32 for n <= 4, 1 <= P <= 64
  * above (more than 32 are read from memory, not held in registers); FP64 or FP32 blocks
  * (BF16: TVI_EUNSUPPORTED); per-series or shared parameters; no Newton
- * predictor.  n <= 4 also has forward Euler, retry_halving and
+ * predictor; both schemes.  n <= 4 also has retry_halving and
  * tvi_adjoint_noalloc; n > 4 needs the workspace of tvi_workspace_bytes, does
- * not halve, and rejects forward Euler and tvi_adjoint_noalloc
- * (TVI_EUNSUPPORTED).  Calls on one model from several host threads are safe.  The paper has no counterpart to
+ * not halve, and rejects tvi_adjoint_noalloc (TVI_EUNSUPPORTED).  Calls on one model from several host threads are safe.  The paper has no counterpart to
  * run-time compilation: it is how an ABI of plain pointers accepts functions.
  */
 

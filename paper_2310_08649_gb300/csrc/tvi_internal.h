@@ -75,6 +75,7 @@ struct ChainArgs {
   double* x;               // [B][c][n]
   int mode;                // 0: x -= d   1: x = d   2: x += d
   int* err;                // set when a bounded wait for staged data gives up
+  int post_add;            // 1: d_j = M_j d_{j-1} + rhs_j (forward Euler's recurrence)
 };
 
 // Argument block of the run-time compiled kernels of user models with n > 4
@@ -83,6 +84,7 @@ struct ChainArgs {
 // multiple of 4) in the workspace buffers.
 struct LargeArgs {
   int B, N, i0, L, c, n4, per_series, reverse;
+  int fwd_euler;            // scheme: forward Euler (h at y_{k-1}; blocks I + dt J)
   const double* times;      // [B][N+1]
   const int* lengths;       // [B] or null
   const double* params;     // [B][P] or [P]
@@ -97,6 +99,7 @@ struct LargeArgs {
   double* acc;              // [B][P] gradient accumulators (adjoint)
   unsigned long long* norm; // [B] max |R| bits (forward)
   const int* active;        // [B] or null
+  double* dy0;              // [B][n] dL/dy0 (forward Euler's final adjoint row)
 };
 
 #ifndef __CUDACC_RTC__
@@ -165,6 +168,7 @@ struct LargeKernels {
   const void* block;         // large_block_kernel<Model, T, n4>
   const void* adj_residual;  // large_adj_residual_kernel<Model>
   const void* param;         // large_param_kernel<Model>
+  const void* fe_dy0;        // large_fe_dy0_kernel<Model>
 };
 size_t large_workspace_bytes(int n, int P, int B, int chunk, int precision);
 cudaError_t large_forward(const LargeKernels& k, int n, int P, int precision, const FwdArgs& a,

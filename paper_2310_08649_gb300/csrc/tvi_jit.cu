@@ -35,6 +35,9 @@ namespace {
 constexpr unsigned kUserMagic = 0x74766975u;
 constexpr int kRptCount = 4;  // steps per thread 1, 2, 4, 8
 constexpr int kPrecCount = 2; // FP64, FP32 blocks
+// large-state kernels: residual, block, adjoint residual, parameter VJP, forward
+// Euler's dL/dy0
+constexpr int kLargeKernels = 5;
 
 int rpt_index(int rpt) { return rpt == 1 ? 0 : rpt == 2 ? 1 : rpt == 4 ? 2 : rpt == 8 ? 3 : -1; }
 
@@ -55,9 +58,9 @@ struct tvi_user_model {
   // large-state kernels (n > 4): residual, Jacobian, adjoint residual, parameter VJP
   bool lcompiled[kPrecCount];
   std::vector<char> lcubin[kPrecCount];
-  std::string lname[kPrecCount][4];
+  std::string lname[kPrecCount][kLargeKernels];
   cudaLibrary_t llib[kPrecCount];
-  cudaKernel_t lk[kPrecCount][4];
+  cudaKernel_t lk[kPrecCount][kLargeKernels];
 };
 
 namespace tvi {
@@ -259,7 +262,8 @@ std::string large_kernel_name(int which, int precision, int n) {
              (precision == kPrecFp64 ? "double, " : "float, ") + std::to_string((n + 3) / 4 * 4) +
              ">";
     case 2: return "tvi::klarge::large_adj_residual_kernel<TviUserModel>";
-    default: return "tvi::klarge::large_param_kernel<TviUserModel>";
+    case 3: return "tvi::klarge::large_param_kernel<TviUserModel>";
+    default: return "tvi::klarge::large_fe_dy0_kernel<TviUserModel>";
   }
 }
 
@@ -373,13 +377,13 @@ int ensure_large_compiled(tvi_user_model* m, int pi, std::string* err) {
   if (m->lcompiled[pi]) return kJitOk;
   const int precision = pi == 0 ? kPrecFp64 : kPrecFp32;
   std::vector<std::string> names;
-  for (int w = 0; w < 4; ++w) names.push_back(large_kernel_name(w, precision, m->n));
+  for (int w = 0; w < kLargeKernels; ++w) names.push_back(large_kernel_name(w, precision, m->n));
   std::vector<std::string> low;
   std::vector<char> cubin;
   int rc = compile(program_text(*m, true), names, &cubin, &low, err);
   if (rc != kJitOk) return rc;
   m->lcubin[pi].swap(cubin);
-  for (int w = 0; w < 4; ++w) m->lname[pi][w] = low[w];
+  for (int w = 0; w < kLargeKernels; ++w) m->lname[pi][w] = low[w];
   m->lcompiled[pi] = true;
   return kJitOk;
 }
@@ -398,21 +402,22 @@ int large_kernels(const tvi_user_model* cm, int precision, LargeKernels* out, st
     cudaLibrary_t lib = nullptr;
     cudaError_t e = cudaLibraryLoadData(&lib, m->lcubin[pi].data(), nullptr, nullptr, 0,
                                         nullptr, nullptr, 0);
-    cudaKernel_t k[4] = {};
-    for (int w = 0; w < 4 && e == cudaSuccess; ++w)
+    cudaKernel_t k[kLargeKernels] = {};
+    for (int w = 0; w < kLargeKernels && e == cudaSuccess; ++w)
       e = cudaLibraryGetKernel(&k[w], lib, m->lname[pi][w].c_str());
     if (e != cudaSuccess) {
       if (lib) cudaLibraryUnload(lib);
       *err = std::string("loading the user model's kernels: ") + cudaGetErrorString(e);
       return kJitCuda;
     }
-    for (int w = 0; w < 4; ++w) m->lk[pi][w] = k[w];
+    for (int w = 0; w < kLargeKernels; ++w) m->lk[pi][w] = k[w];
     m->llib[pi] = lib;
   }
   out->residual = reinterpret_cast<const void*>(m->lk[pi][0]);
   out->block = reinterpret_cast<const void*>(m->lk[pi][1]);
   out->adj_residual = reinterpret_cast<const void*>(m->lk[pi][2]);
   out->param = reinterpret_cast<const void*>(m->lk[pi][3]);
+  out->fe_dy0 = reinterpret_cast<const void*>(m->lk[pi][4]);
   return kJitOk;
 }
 
@@ -436,7 +441,7 @@ int user_create(int n, int P, const char* source, tvi_user_model** out, std::str
     }
     m->lcompiled[i] = false;
     m->llib[i] = nullptr;
-    for (int w = 0; w < 4; ++w) m->lk[i][w] = nullptr;
+    for (int w = 0; w < kLargeKernels; ++w) m->lk[i][w] = nullptr;
   }
   int rc = compile(program_text(*m, false), {}, nullptr, nullptr, err);
   if (rc != kJitOk) {

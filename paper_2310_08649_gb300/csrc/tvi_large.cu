@@ -141,15 +141,19 @@ __global__ void large_carry_kernel(int B, int n4, int L, int c, const double* av
 
 // dL/dy0 = a_1 + dL/dy_0; dL/dp per series, or summed over the series in order
 // (shared parameters); NaN when a bounded wait gave up
+// (forward Euler: dL/dy0 was written by large_fe_dy0_kernel and is only
+// replaced by NaN here)
 __global__ void large_adjoint_end_kernel(int B, int n, int n4, int Np1, int P, int per_series,
-                                         const double* carry, const double* g, const double* acc,
-                                         double* dy0, double* dparams, const int* err) {
+                                         int fwd_euler, const double* carry, const double* g,
+                                         const double* acc, double* dy0, double* dparams,
+                                         const int* err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool bad = *err != 0;
   const double nan = __longlong_as_double(0x7ff8000000000000LL);
   if (dy0 && i < B * n) {
     const int b = i / n, s = i % n;
-    dy0[i] = bad ? nan : carry[b * n4 + s] + g[static_cast<size_t>(b) * Np1 * n + s];
+    if (bad) dy0[i] = nan;
+    else if (!fwd_euler) dy0[i] = carry[b * n4 + s] + g[static_cast<size_t>(b) * Np1 * n + s];
   }
   if (per_series) {
     if (i < B * P) dparams[i] = bad ? nan : acc[i];
@@ -205,7 +209,7 @@ cudaError_t large_forward(const LargeKernels& k, int n, int P, int precision, co
     TVI_TRY(cudaGetLastError());
     LargeArgs la{};
     la.B = B; la.N = N; la.i0 = i0; la.L = L; la.c = c; la.n4 = n4;
-    la.per_series = a.per_series; la.reverse = 0;
+    la.per_series = a.per_series; la.reverse = 0; la.fwd_euler = a.scheme == kSchemeForward;
     la.times = a.times; la.lengths = a.lengths; la.params = a.params;
     la.yi = w.yi; la.dy = w.dy; la.R = w.R; la.J = w.M; la.norm = w.norm; la.active = w.active;
     const dim3 grid((L + kThreads - 1) / kThreads, B);
@@ -222,6 +226,7 @@ cudaError_t large_forward(const LargeKernels& k, int n, int P, int precision, co
       ChainArgs ch{};
       ch.B = B; ch.n = n4; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 0; ch.M = w.M;
       ch.rhs_buf = w.R; ch.active = w.active; ch.x = w.dy; ch.mode = 0; ch.err = w.err;
+      ch.post_add = la.fwd_euler;  // forward Euler: d_j = (I + dt J) d_{j-1} + R_j
       TVI_TRY(mlp_launch_chain(precision, ch, s));
     }
     note_launch();
@@ -254,7 +259,7 @@ cudaError_t large_adjoint(const LargeKernels& k, int n, int P, int precision, co
     const int L = (N - i0 < c) ? N - i0 : c;
     LargeArgs la{};
     la.B = B; la.N = N; la.i0 = i0; la.L = L; la.c = c; la.n4 = n4;
-    la.per_series = a.per_series; la.reverse = 1;
+    la.per_series = a.per_series; la.reverse = 1; la.fwd_euler = a.scheme == kSchemeForward;
     la.times = a.times; la.lengths = a.lengths; la.params = a.params;
     la.ytraj = a.y; la.g = a.grad_out; la.av = w.dy; la.carry = w.carry; la.R = w.R; la.J = w.M;
     la.acc = w.acc;
@@ -264,10 +269,12 @@ cudaError_t large_adjoint(const LargeKernels& k, int n, int P, int precision, co
         B, n, n4, N, i0, L, c, a.grad_out, w.R);
     TVI_TRY(cudaGetLastError());
     TVI_TRY(launch_user(k.block, block_grid(L, B), la, s));
-    // a_j = A^-T (a_{j-1} + g_k), a_{-1} = carry
+    // a_j = A^-T (a_{j-1} + g_k) (backward Euler) or (I + dt J)^T a_{j-1} + g_k
+    // (forward Euler), a_{-1} = carry
     ChainArgs ch{};
     ch.B = B; ch.n = n4; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 1; ch.M = w.M;
     ch.rhs_buf = w.R; ch.x_init = w.carry; ch.x = w.dy; ch.mode = 1; ch.err = w.err;
+    ch.post_add = la.fwd_euler;
     TVI_TRY(mlp_launch_chain(precision, ch, s));
     for (int it = 0; it < refine; ++it) {
       TVI_TRY(launch_user(k.adj_residual, grid, la, s));
@@ -282,11 +289,20 @@ cudaError_t large_adjoint(const LargeKernels& k, int n, int P, int precision, co
         B, n4, L, c, w.dy, w.carry);
     TVI_TRY(cudaGetLastError());
   }
+  const bool fe = a.scheme == kSchemeForward;
+  if (fe && a.dy0) {  // dL/dy0 = g_0 + (I + dt_1 J(y_0))^T a_1
+    LargeArgs la{};
+    la.B = B; la.N = N; la.n4 = n4; la.per_series = a.per_series; la.fwd_euler = 1;
+    la.times = a.times; la.lengths = a.lengths; la.params = a.params;
+    la.ytraj = a.y; la.g = a.grad_out; la.carry = w.carry; la.dy0 = a.dy0;
+    TVI_TRY(launch_user(k.fe_dy0, dim3(blocks_for(B, kThreads)), la, s));
+  }
   const int per = a.per_series ? B * P : P;
   const int cnt = B * n > per ? B * n : per;
   note_launch();
   large_adjoint_end_kernel<<<blocks_for(cnt, 256), 256, 0, s>>>(
-      B, n, n4, N + 1, P, a.per_series, w.carry, a.grad_out, w.acc, a.dy0, a.dparams, w.err);
+      B, n, n4, N + 1, P, a.per_series, fe ? 1 : 0, w.carry, a.grad_out, w.acc, a.dy0,
+      a.dparams, w.err);
   return cudaGetLastError();
 }
 

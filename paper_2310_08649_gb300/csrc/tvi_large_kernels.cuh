@@ -57,9 +57,15 @@ __global__ void __launch_bounds__(kLargeThreads) large_residual_kernel(LargeArgs
     const double* yi = a.yi + static_cast<size_t>(b) * a.n4;
     const double* dyj = a.dy + (static_cast<size_t>(b) * a.c + j) * a.n4;
     double y[NS], h[NS];
+    // backward Euler evaluates h at (y_k, t_k), forward Euler at (y_{k-1}, t_{k-1})
+    if (a.fwd_euler) {
 #pragma unroll
-    for (int s = 0; s < NS; ++s) y[s] = yi[s] + dyj[s];
-    mdl.rhs(y, tb[k], h);
+      for (int s = 0; s < NS; ++s) y[s] = yi[s] + (j > 0 ? dyj[s - a.n4] : 0.0);
+    } else {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) y[s] = yi[s] + dyj[s];
+    }
+    mdl.rhs(y, a.fwd_euler ? tb[k - 1] : tb[k], h);
     double* Rj = a.R + (static_cast<size_t>(b) * a.c + j) * a.n4;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
@@ -97,11 +103,15 @@ __global__ void __launch_bounds__(128) large_block_kernel(LargeArgs a) {
   T* buf = s_buf[warp];
   const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
   const int k = step_index(a.reverse, a.i0, a.L, j);
-  const T dt = static_cast<T>(step_dt_of(tb, series_len(a, b), k));
+  // forward Euler couples a_k to a_{k+1} through step k+1 in the adjoint
+  const int len = series_len(a, b);
+  const T dt = static_cast<T>(step_dt_of(tb, len, a.fwd_euler && a.reverse ? k + 1 : k));
   if (lane == 0) {
     Model mdl;
     mdl.load(a.params, b, a.per_series);
     double y[NS];
+    // J at (y_k, t_k), except forward Euler's forward blocks: at (y_{k-1}, t_{k-1})
+    const bool prev = a.fwd_euler && !a.reverse;
     if (a.reverse) {
       const double* yk = a.ytraj + (static_cast<size_t>(b) * (a.N + 1) + k) * NS;
 #pragma unroll
@@ -109,12 +119,25 @@ __global__ void __launch_bounds__(128) large_block_kernel(LargeArgs a) {
     } else {
       const double* yi = a.yi + static_cast<size_t>(b) * a.n4;
       const double* dyj = a.dy + (static_cast<size_t>(b) * a.c + j) * a.n4;
+      const int jj = prev ? j - 1 : j;
 #pragma unroll
-      for (int s = 0; s < NS; ++s) y[s] = yi[s] + dyj[s];
+      for (int s = 0; s < NS; ++s) y[s] = yi[s] + (jj >= 0 ? dyj[(jj - j) * a.n4 + s] : 0.0);
     }
-    mdl.template jacobian<T>(y, tb[k], buf);  // J, NS x NS row-major
+    mdl.template jacobian<T>(y, prev ? tb[k - 1] : tb[k], buf);  // J, NS x NS row-major
   }
   __syncwarp();
+  if (a.fwd_euler) {
+    // no inverse: the block is B = I + dt J (forward, stored transposed as the chain
+    // reads it) or B^T (adjoint), slot[r][q] = B[q][r] or B[r][q]
+    T* slot = static_cast<T*>(a.J) + (static_cast<size_t>(b) * a.c + j) * N4 * N4;
+    for (int i = lane; i < N4 * N4; i += 32) {
+      const int r = i / N4, q = i - r * N4;
+      const int rr = a.reverse ? r : q, cc = a.reverse ? q : r;  // B[rr][cc]
+      const T Jv = (rr < NS && cc < NS) ? buf[rr * NS + cc] : T(0);
+      slot[i] = fma(dt, Jv, rr == cc ? T(1) : T(0));
+    }
+    return;
+  }
   T row[2 * N4];
 #pragma unroll
   for (int q = 0; q < N4; ++q) {
@@ -172,7 +195,9 @@ __global__ void __launch_bounds__(kLargeThreads) large_adj_residual_kernel(Large
   mdl.load(a.params, b, a.per_series);
   const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
   const int k = a.i0 + a.L - j;
-  const double dt = step_dt_of(tb, series_len(a, b), k);
+  // backward Euler: (I - dt_k J_k)^T a_k = a_{k+1} + g_k; forward Euler:
+  // a_k = g_k + (I + dt_{k+1} J_k)^T a_{k+1}, J_k = dh/dy at (y_k, t_k) in both
+  const double dt = step_dt_of(tb, series_len(a, b), a.fwd_euler ? k + 1 : k);
   double y[NS], J[NS * NS];
   const double* yk = a.ytraj + (static_cast<size_t>(b) * (a.N + 1) + k) * NS;
 #pragma unroll
@@ -181,10 +206,11 @@ __global__ void __launch_bounds__(kLargeThreads) large_adj_residual_kernel(Large
   const double* aj = a.av + (static_cast<size_t>(b) * a.c + j) * a.n4;
   const double* ap = j > 0 ? aj - a.n4 : a.carry + static_cast<size_t>(b) * a.n4;
   const double* gk = a.g + (static_cast<size_t>(b) * (a.N + 1) + k) * NS;
+  const double* ax = a.fwd_euler ? ap : aj;  // the adjoint row J^T multiplies
   double* rj = a.R + (static_cast<size_t>(b) * a.c + j) * a.n4;
   for (int p = 0; p < NS; ++p) {
     double s = 0.0;
-    for (int q = 0; q < NS; ++q) s = fma(J[q * NS + p], aj[q], s);  // (J^T a)_p
+    for (int q = 0; q < NS; ++q) s = fma(J[q * NS + p], ax[q], s);  // (J^T a)_p
     rj[p] = fma(dt, s, gk[p] + ap[p] - aj[p]);
   }
   for (int p = NS; p < a.n4; ++p) rj[p] = 0.0;
@@ -209,14 +235,16 @@ __global__ void __launch_bounds__(kLargeThreads) large_param_kernel(LargeArgs a)
     const double dt = step_dt_of(tb, len, k);
     if (dt == 0.0) continue;
     double y[NS], av[NS];
-    const double* yk = a.ytraj + (static_cast<size_t>(b) * (a.N + 1) + k) * NS;
+    // step k evaluates h at (y_k, t_k) (backward Euler) or (y_{k-1}, t_{k-1})
+    const int ke = a.fwd_euler ? k - 1 : k;
+    const double* yk = a.ytraj + (static_cast<size_t>(b) * (a.N + 1) + ke) * NS;
     const double* aj = a.av + (static_cast<size_t>(b) * a.c + j) * a.n4;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       y[s] = yk[s];
       av[s] = aj[s];
     }
-    mdl.vjp_p(y, tb[k], av, dt, acc);
+    mdl.vjp_p(y, tb[ke], av, dt, acc);
   }
   // deterministic block sum: warp tree, then the warps in order
 #pragma unroll
@@ -231,6 +259,31 @@ __global__ void __launch_bounds__(kLargeThreads) large_param_kernel(LargeArgs a)
     double v = 0.0;
     for (int w = 0; w < kLargeThreads / 32; ++w) v += s_part[w][tid];
     a.acc[static_cast<size_t>(b) * NP + tid] += v;
+  }
+}
+
+// Forward Euler's dL/dy0 = g_0 + (I + dt_1 J(y_0, t_0))^T a_1, a_1 = the carry
+// after the first chunk; one thread per series.
+template <class Model>
+__global__ void __launch_bounds__(kLargeThreads) large_fe_dy0_kernel(LargeArgs a) {
+  constexpr int NS = Model::NS;
+  const int b = blockIdx.x * kLargeThreads + threadIdx.x;
+  if (b >= a.B) return;
+  Model mdl;
+  mdl.load(a.params, b, a.per_series);
+  const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
+  const double dt = a.N >= 1 ? step_dt_of(tb, series_len(a, b), 1) : 0.0;
+  double y[NS], J[NS * NS];
+  const double* y0 = a.ytraj + static_cast<size_t>(b) * (a.N + 1) * NS;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) y[s] = y0[s];
+  mdl.template jacobian<double>(y, tb[0], J);
+  const double* cr = a.carry + static_cast<size_t>(b) * a.n4;
+  const double* g0 = a.g + static_cast<size_t>(b) * (a.N + 1) * NS;
+  for (int p = 0; p < NS; ++p) {
+    double s = 0.0;
+    for (int q = 0; q < NS; ++q) s = fma(J[q * NS + p], cr[q], s);
+    a.dy0[static_cast<size_t>(b) * NS + p] = fma(dt, s, g0[p] + cr[p]);
   }
 }
 

@@ -1030,7 +1030,8 @@ __global__ void __launch_bounds__(32 * W) mlp_chain_kernel(ChainArgs a) {
     for (int q = 0; q < N; ++q) m[q] = own ? Mt[q * N + lane] : T(0);
     const T rc = own ? static_cast<T>(rr[lane]) : T(0);
     const double x_cur = (own && a.mode != 1) ? rr[N + lane] : 0.0;
-    su[lane] = dprev + rc;  // component `lane` of d_{j-1} + rhs_j
+    // component `lane` of d_{j-1} + rhs_j (of d_{j-1} alone with post_add)
+    su[lane] = a.post_add ? dprev : dprev + rc;
     __syncwarp();
     T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
 #pragma unroll
@@ -1042,7 +1043,7 @@ __global__ void __launch_bounds__(32 * W) mlp_chain_kernel(ChainArgs a) {
     }
     __syncwarp();  // su and (at a half's end) its slots are free again
     if (j % H == H - 1) issue_half(j + 1 - H + D);
-    const T acc = (acc0 + acc1) + (acc2 + acc3);
+    const T acc = (acc0 + acc1) + (acc2 + acc3) + (a.post_add ? rc : T(0));
     dprev = own ? acc : T(0);
     if (own) {
       const double dd = static_cast<double>(acc);
@@ -1546,7 +1547,8 @@ cudaError_t launch_blocks_any(const BlocksArgs& bk, int precision, int* err, cud
 // Tiled chain solve (the hybrid of Sec. 3.3): the chunk's L steps are split
 // into W tiles, one warp each.
 //   pass A (tiles in parallel)  warp w composes its tile's affine map
-//                               d_end = P_w d_in + q_w  (P <- M_j P, q <- M_j (q + r_j))
+//                               d_end = P_w d_in + q_w  (P <- M_j P, q <- M_j (q + r_j);
+//                               q <- M_j q + r_j for forward Euler's recurrence)
 //   pass B (one warp)           d_in of every tile from x_init by the W maps
 //   pass C (tiles in parallel)  warp w sweeps its tile from its d_in:
 //                               d_j = M_j (d_{j-1} + r_j), x updated by mode
@@ -1625,7 +1627,9 @@ __global__ void __launch_bounds__(32 * W) tile_chain_kernel(ChainArgs a) {
               sM[r * LDM + k] = mreg[q][i];
             }
           }
-          if (lane < N) su[lane] = sq[lane] + static_cast<T>(rreg[q]);
+          const T rj = lane < N ? static_cast<T>(rreg[q]) : T(0);
+          // u = q + r_j, or q alone with post_add (then r_j is added after the product)
+          if (lane < N) su[lane] = a.post_add ? sq[lane] : sq[lane] + rj;
           load_a(j + PF, mreg[q], rreg[q]);
           __syncwarp();
           for (int e = lane; e < N * N; e += 32) {
@@ -1636,7 +1640,7 @@ __global__ void __launch_bounds__(32 * W) tile_chain_kernel(ChainArgs a) {
             Pn[e] = acc;
           }
           if (lane < N) {
-            T acc = T(0);
+            T acc = a.post_add ? rj : T(0);
 #pragma unroll
             for (int k = 0; k < N; ++k) acc = fma(sM[lane * LDM + k], su[k], acc);
             sq[lane] = acc;
@@ -1695,8 +1699,9 @@ __global__ void __launch_bounds__(32 * W) tile_chain_kernel(ChainArgs a) {
       for (int q = 0; q < PF; ++q) {
         const int j = jb + q;
         if (j < j1) {  // warp-uniform
-          const T u = lane < N ? d + static_cast<T>(rreg[q]) : T(0);
-          T acc0 = T(0), acc1 = T(0);
+          const T rj = lane < N ? static_cast<T>(rreg[q]) : T(0);
+          const T u = lane < N ? (a.post_add ? d : d + rj) : T(0);
+          T acc0 = a.post_add ? rj : T(0), acc1 = T(0);
 #pragma unroll
           for (int k = 0; k < N; k += 2) {
             const T u0 = __shfl_sync(kFull, u, k);

@@ -266,10 +266,7 @@ def test_user_large_padded_lengths_and_rejections(tvi, users, oracle_lib):
     dp, dy0 = adjoint(tvi, model, w, o, ref, g, lengths=lens)
     e_p = np.abs(dp - dp_ref).max(axis=1) / np.maximum(np.abs(dp_ref).max(axis=1), 1e-300)
     assert e_p.max() <= 1e-10 and relerr(dy0, dy0_ref) <= 1e-10
-    # forward Euler and the allocation-free adjoint are small-state features
-    with pytest.raises(L.TviError) as e:
-        forward_raise(tvi, model, w, tvi.Options(chunk=10, scheme="forward"))
-    assert e.value.code == -7
+    # the allocation-free adjoint is a small-state feature
     lib = L.load()
     cm, co = model.c(), o.c()
     T, P, Y, G = dev(w["times"]), dev(w["params"]), dev(ref), dev(g)
@@ -336,6 +333,37 @@ def test_user_neuron_matches_oracle(tvi, users, oracle_lib, precision, u, chunk)
     assert bad.size == 0, (bad, err[bad], est[bad])
     g = workloads.random_grad_out(240 + u, 16, 2000, 4 * u)
     dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g)
+    dp, dy0 = adjoint(tvi, model, w, o, ref, g)
+    e_p = np.abs(dp - dp_ref).max(axis=1) / np.abs(dp_ref).max(axis=1)
+    assert e_p.max() <= GATE[precision], (e_p.argmax(), e_p.max())
+    assert relerr(dy0, dy0_ref) <= GATE[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("which,chunk", [("chab3", 64), ("chab3", 1000), ("neuron2", 250)])
+def test_user_large_forward_euler(tvi, users, oracle_lib, precision, which, chunk):
+    """Forward Euler on the large-state route (blocks I + dt J without an
+    inverse, the recurrence d_j = B_j d_{j-1} + R_j in the chain) against the
+    step-by-step forward-Euler oracle: trajectory and both gradients."""
+    if which == "chab3":
+        w = workloads.chaboche(B=12, N=2000, n_unit=3, jitter=0.1, seed=250)
+        w["params"][:, 12] *= 3.0  # strain-rate amplitude: the loading yields
+    else:
+        w = workloads.neuron(B=12, N=2000, n_unit=2, jitter=0.1, seed=251)
+    m = OModel.from_spec(w["spec"])
+    ref, st = oracle_lib.forward_euler(m, w["y0"], w["times"], w["params"])
+    assert not st.any()
+    model = users[which].model(per_series=True)
+    o = tvi.Options(chunk=chunk, tol_abs=1e-12, precision=precision, scheme="forward",
+                    max_iter=60, adjoint_refine=3)
+    y, _, status, rc = forward(tvi, model, w, o)
+    assert rc == 0 and not status.any()
+    est = fe_error_estimate(oracle_lib, m, w, ref, 1e-12)
+    err = relerr_series(y, ref)
+    assert np.all(err <= np.maximum(GATE[precision], 10.0 * est)), (err.max(), est.max())
+    n = w["spec"]["n"]
+    g = workloads.random_grad_out(252, 12, 2000, n)
+    dp_ref, dy0_ref = oracle_lib.adjoint_euler(m, w["times"], w["params"], ref, g)
     dp, dy0 = adjoint(tvi, model, w, o, ref, g)
     e_p = np.abs(dp - dp_ref).max(axis=1) / np.abs(dp_ref).max(axis=1)
     assert e_p.max() <= GATE[precision], (e_p.argmax(), e_p.max())

@@ -130,8 +130,8 @@ def test_prepare_rejects_bf16(lib):
 
 def test_large_route_host_checks(lib):
     """Without a GPU: the workspace of a large-state user model grows with the
-    chunk, and forward Euler, BF16 blocks and the allocation-free adjoint are
-    rejected on that route before anything is launched."""
+    chunk; BF16 blocks and the allocation-free adjoint are rejected on that route
+    before anything is launched, and forward Euler passes the scheme check."""
     u = tvi.UserModel(20, mds_param_count(10), MDS)
     m = u.model(per_series=True).c()
     o = _lib.TviOptions()
@@ -144,10 +144,10 @@ def test_large_route_host_checks(lib):
     assert 0 < w100 < w1000
     # 8 series x 1000 steps x 20 x 20 FP32 blocks at least
     assert w1000 >= 8 * 1000 * 20 * 20 * 4
-    o.scheme = 1  # forward Euler
+    o.scheme = 1  # forward Euler: accepted, then the NULL arrays are the error
     rc = lib.tvi_integrate(ctypes.byref(m), ctypes.byref(o), 8, 1000, None, None, None, None,
                            None, None, None, None, 0, None)
-    assert rc == EUNSUPPORTED and "forward Euler" in _lib.last_error()
+    assert rc == EINVAL and "must not be NULL" in _lib.last_error()
     o.scheme = 0
     o.precision = 2  # BF16
     rc = lib.tvi_integrate(ctypes.byref(m), ctypes.byref(o), 8, 1000, None, None, None, None,
