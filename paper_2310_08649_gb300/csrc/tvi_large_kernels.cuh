@@ -3,20 +3,24 @@
 //
 // Above n = 4 a step's n x n block no longer fits one thread's registers, so
 // these models take the large-state route of the MLP engine: every (series,
-// step) pair of the chunk is a thread here, the blocks are inverted by one warp
-// each and the chunk system is solved by block forward substitution
-// (mlp_chain_kernel; Thomas's algorithm, which the paper finds faster than PCR
-// for larger systems, Sec. 5.3).  One Newton iteration (Alg. 1):
+// step) pair of the chunk is a thread here, the blocks are formed by one warp
+// each, and the chunk system is solved by the chain solve of tvi_mlp.cu, chosen
+// by width (the tiled hybrid of Sec. 3.3 up to n = 16, block forward
+// substitution -- Thomas's algorithm, which the paper finds faster for larger
+// systems, Sec. 5.3 -- above).  One Newton iteration (Alg. 1):
 //   large_residual_kernel    R_j = dy_j - dy_{j-1} - dt_k h(y_i + dy_j, t_k) in
-//                            FP64, per-series max |R| (integer atomics on bits)
-//   large_block_kernel       J = dh/dy at (y_j, t_k) in the block type, A = I -
-//                            dt J inverted in registers (one warp per pair)
+//                            FP64 (forward Euler: h at y_{k-1}, t_{k-1}),
+//                            per-series max |R| (integer atomics on bits)
+//   large_block_kernel       J = dh/dy in the block type; A = I - dt J inverted
+//                            in registers, one warp per pair (forward Euler:
+//                            B = I + dt J, no inverse)
 // and the adjoint (App. A.2), chunks in reverse over the stored trajectory:
-//   large_block_kernel       (reverse rows) the A^-T blocks
-//   large_adj_residual_kernel  r_j = g_k + a_{j-1} - a_j + dt_k J^T a_j in FP64
+//   large_block_kernel       (reverse rows) the A^-T blocks (B^T)
+//   large_adj_residual_kernel  the FP64 residual of the adjoint recurrence
 //                            (refinement of the mixed-precision solve)
-//   large_param_kernel       acc_b += sum_j dt_k (dh/dp)^T a_j, one block per
+//   large_param_kernel       acc_b += sum_k dt_k (dh/dp)^T a_k, one block per
 //                            series, fixed summation order
+//   large_fe_dy0_kernel      forward Euler's dL/dy0 through the first step
 // Model is the adapter of the user's functions (tvi_jit.cu).
 #pragma once
 
