@@ -171,8 +171,13 @@ cudaError_t launch_user(const void* kernel, dim3 grid, const LargeArgs& a, cudaS
   return cudaLaunchKernel(kernel, grid, dim3(kThreads), params, 0, s);
 }
 
-// the block kernel: one warp per pair, four pairs per block
-dim3 block_grid(int L, int B) { return dim3((L + 3) / 4, B); }
+// the block kernel: four warps per block, each forming 32 / SEG blocks (SEG the
+// lanes of one block: 8, 16 or 32 for n4 up to 8, 16, 32)
+dim3 block_grid(int L, int B, int n4) {
+  const int per_warp = n4 <= 8 ? 4 : (n4 <= 16 ? 2 : 1);
+  const int per_block = 4 * per_warp;
+  return dim3((L + per_block - 1) / per_block, B);
+}
 
 #define TVI_TRY(x)                    \
   do {                                \
@@ -222,7 +227,7 @@ cudaError_t large_forward(const LargeKernels& k, int n, int P, int precision, co
       TVI_TRY(cudaMemcpyAsync(&remaining, w.remaining, sizeof(int), cudaMemcpyDeviceToHost, s));
       TVI_TRY(cudaStreamSynchronize(s));
       if (remaining == 0) break;
-      TVI_TRY(launch_user(k.block, block_grid(L, B), la, s));
+      TVI_TRY(launch_user(k.block, block_grid(L, B, n4), la, s));
       ChainArgs ch{};
       ch.B = B; ch.n = n4; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 0; ch.M = w.M;
       ch.rhs_buf = w.R; ch.active = w.active; ch.x = w.dy; ch.mode = 0; ch.err = w.err;
@@ -268,7 +273,7 @@ cudaError_t large_adjoint(const LargeKernels& k, int n, int P, int precision, co
     large_gather_kernel<<<blocks_for(static_cast<size_t>(B) * L * n4, 256), 256, 0, s>>>(
         B, n, n4, N, i0, L, c, a.grad_out, w.R);
     TVI_TRY(cudaGetLastError());
-    TVI_TRY(launch_user(k.block, block_grid(L, B), la, s));
+    TVI_TRY(launch_user(k.block, block_grid(L, B, n4), la, s));
     // a_j = A^-T (a_{j-1} + g_k) (backward Euler) or (I + dt J)^T a_{j-1} + g_k
     // (forward Euler), a_{-1} = carry
     ChainArgs ch{};

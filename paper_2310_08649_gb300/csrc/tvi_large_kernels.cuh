@@ -85,32 +85,50 @@ __global__ void __launch_bounds__(kLargeThreads) large_residual_kernel(LargeArgs
   if ((threadIdx.x & 31) == 0 && mx) atomicMax(a.norm + b, mx);
 }
 
+// lanes that form one block: a power of two >= N4 (a warp holds 32 / SEG blocks)
+template <int N4>
+constexpr int block_lanes() {
+  return N4 <= 8 ? 8 : (N4 <= 16 ? 16 : 32);
+}
+
 // Block of pair j: A = I - dt_k J(y_j, t_k) inverted by Gauss-Jordan with
-// partial pivoting, one warp per pair, stored in the pair's slot as the chain
-// reads it (A^-1 transposed; A^-T when reverse), padded to N4 with the identity.
-// Lane 0 evaluates J into shared memory; lane r < N4 then keeps row r of
-// [A | I] in registers.  Pivoting without row swaps: step k takes the unused
-// row of largest |A[r][k]| (a butterfly argmax, first of equal maxima), the
-// pivot row is broadcast by shuffles, and every row takes one FMA per entry:
-// row_r -= (A[r][k] / piv) row_p, and the pivot row -= (1 - 1 / piv) itself,
-// which scales it.  The row that pivoted at step k holds row k of A^-1 in its
-// right half.  The result leaves through shared memory (coalesced stores).
+// partial pivoting, stored in the pair's slot as the chain reads it (A^-1
+// transposed; A^-T when reverse), padded to N4 with the identity.  A group of
+// SEG lanes forms one block, so a warp forms 32 / SEG at once (4 at N4 = 8).
+// The group's first lane evaluates J into shared memory; lane r < N4 of the
+// group then keeps row r of [A | I] in registers.  Pivoting without row swaps:
+// step k takes the unused row of largest |A[r][k]| (a butterfly argmax within
+// the group, first of equal maxima), the pivot row is broadcast by shuffles,
+// and every row takes one FMA per entry: row_r -= (A[r][k] / piv) row_p, and
+// the pivot row -= (1 - 1 / piv) itself, which scales it.  The row that pivoted
+// at step k holds row k of A^-1 in its right half.  The result leaves through
+// shared memory (coalesced stores).  Forward Euler's blocks B = I + dt J need no
+// inverse.  Groups past the chunk's end run the elimination on the identity
+// (their lanes take part in the shuffles) and store nothing.
 template <class Model, typename T, int N4>
 __global__ void __launch_bounds__(128) large_block_kernel(LargeArgs a) {
   constexpr int NS = Model::NS;
-  constexpr int LD = N4 + 1;  // padded row stride of the staging buffer
-  __shared__ T s_buf[4][N4 * LD];
+  constexpr int SEG = block_lanes<N4>();
+  constexpr int G = 32 / SEG;   // blocks per warp
+  constexpr int LD = N4 + 1;    // padded row stride of the staging buffer
+  __shared__ T s_buf[4][G][N4 * LD];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / SEG, lg = lane - grp * SEG;
   const int b = blockIdx.y;
-  const int j = blockIdx.x * 4 + warp;
-  if (j >= a.L || (a.active && !a.active[b])) return;  // warp-uniform
-  T* buf = s_buf[warp];
+  if (a.active && !a.active[b]) return;  // block-uniform
+  const int jw = (blockIdx.x * 4 + warp) * G;  // first pair of the warp
+  if (jw >= a.L) return;                       // warp-uniform
+  const int j = jw + grp;
+  const bool live = j < a.L;
+  const int jc = live ? j : jw;  // a valid row for the index arithmetic
+  T* buf = s_buf[warp][grp];
   const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
-  const int k = step_index(a.reverse, a.i0, a.L, j);
+  const int k = step_index(a.reverse, a.i0, a.L, jc);
   // forward Euler couples a_k to a_{k+1} through step k+1 in the adjoint
   const int len = series_len(a, b);
-  const T dt = static_cast<T>(step_dt_of(tb, len, a.fwd_euler && a.reverse ? k + 1 : k));
-  if (lane == 0) {
+  const T dt = live ? static_cast<T>(step_dt_of(tb, len, a.fwd_euler && a.reverse ? k + 1 : k))
+                    : T(0);
+  if (lg == 0 && live) {
     Model mdl;
     mdl.load(a.params, b, a.per_series);
     double y[NS];
@@ -130,62 +148,66 @@ __global__ void __launch_bounds__(128) large_block_kernel(LargeArgs a) {
     mdl.template jacobian<T>(y, prev ? tb[k - 1] : tb[k], buf);  // J, NS x NS row-major
   }
   __syncwarp();
+  T* slot = static_cast<T*>(a.J) + (static_cast<size_t>(b) * a.c + j) * N4 * N4;
   if (a.fwd_euler) {
     // no inverse: the block is B = I + dt J (forward, stored transposed as the chain
     // reads it) or B^T (adjoint), slot[r][q] = B[q][r] or B[r][q]
-    T* slot = static_cast<T*>(a.J) + (static_cast<size_t>(b) * a.c + j) * N4 * N4;
-    for (int i = lane; i < N4 * N4; i += 32) {
-      const int r = i / N4, q = i - r * N4;
-      const int rr = a.reverse ? r : q, cc = a.reverse ? q : r;  // B[rr][cc]
-      const T Jv = (rr < NS && cc < NS) ? buf[rr * NS + cc] : T(0);
-      slot[i] = fma(dt, Jv, rr == cc ? T(1) : T(0));
+    if (live) {
+      for (int i = lg; i < N4 * N4; i += SEG) {
+        const int r = i / N4, q = i - r * N4;
+        const int rr = a.reverse ? r : q, cc = a.reverse ? q : r;  // B[rr][cc]
+        const T Jv = (rr < NS && cc < NS) ? buf[rr * NS + cc] : T(0);
+        slot[i] = fma(dt, Jv, rr == cc ? T(1) : T(0));
+      }
     }
     return;
   }
   T row[2 * N4];
 #pragma unroll
   for (int q = 0; q < N4; ++q) {
-    const T Jv = (lane < NS && q < NS) ? buf[lane * NS + q] : T(0);
-    row[q] = lane < N4 ? fma(-dt, Jv, lane == q ? T(1) : T(0)) : T(0);
-    row[N4 + q] = lane == q ? T(1) : T(0);
+    const T Jv = (live && lg < NS && q < NS) ? buf[lg * NS + q] : T(0);
+    row[q] = lg < N4 ? fma(-dt, Jv, lg == q ? T(1) : T(0)) : T(0);
+    row[N4 + q] = lg == q ? T(1) : T(0);
   }
   __syncwarp();  // buf is reused for the result
-  bool used = lane >= N4;  // lanes without a row never pivot
+  bool used = lg >= N4;  // lanes without a row never pivot
   int myk = 0;
 #pragma unroll
   for (int kk = 0; kk < N4; ++kk) {
     const T x = fabs(row[kk]);
-    // NaN rows sort high (and stay NaN): every lane then agrees on the pivot
+    // NaN rows sort high (and stay NaN): every lane of the group agrees on the pivot
     T v = used ? T(-1) : (x == x ? x : static_cast<T>(__int_as_float(0x7f800000)));
-    int p = lane;
+    int p = lg;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T ov = __shfl_xor_sync(kFull, v, o);
-      const int op = __shfl_xor_sync(kFull, p, o);
+    for (int o = SEG / 2; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(kFull, v, o, SEG);
+      const int op = __shfl_xor_sync(kFull, p, o, SEG);
       if (ov > v || (ov == v && op < p)) {
         v = ov;
         p = op;
       }
     }
-    if (lane == p) {
+    if (lg == p) {
       used = true;
       myk = kk;
     }
-    const T inv = T(1) / __shfl_sync(kFull, row[kk], p);
-    const T f = lane == p ? T(1) - inv : row[kk] * inv;
+    const T inv = T(1) / __shfl_sync(kFull, row[kk], p, SEG);
+    const T f = lg == p ? T(1) - inv : row[kk] * inv;
 #pragma unroll
-    for (int q = 0; q < 2 * N4; ++q) row[q] = fma(-f, __shfl_sync(kFull, row[q], p), row[q]);
+    for (int q = 0; q < 2 * N4; ++q)
+      row[q] = fma(-f, __shfl_sync(kFull, row[q], p, SEG), row[q]);
   }
-  if (lane < N4) {
+  if (lg < N4) {
 #pragma unroll
     for (int q = 0; q < N4; ++q) buf[myk * LD + q] = row[N4 + q];  // A^-1[myk][q]
   }
   __syncwarp();
-  T* slot = static_cast<T*>(a.J) + (static_cast<size_t>(b) * a.c + j) * N4 * N4;
-  for (int i = lane; i < N4 * N4; i += 32) {
-    const int r = i / N4, q = i - r * N4;
-    // forward: slot[r][q] = A^-1[q][r] (transposed); reverse: slot[r][q] = A^-1[r][q]
-    slot[i] = a.reverse ? buf[r * LD + q] : buf[q * LD + r];
+  if (live) {
+    for (int i = lg; i < N4 * N4; i += SEG) {
+      const int r = i / N4, q = i - r * N4;
+      // forward: slot[r][q] = A^-1[q][r] (transposed); reverse: slot[r][q] = A^-1[r][q]
+      slot[i] = a.reverse ? buf[r * LD + q] : buf[q * LD + r];
+    }
   }
 }
 
