@@ -78,11 +78,11 @@ def _compile(src, extra):
 
 def build(force=False, verbose_ptxas=False):
     os.makedirs(OUT_DIR, exist_ok=True)
+    write_jit_headers()  # rewritten only when a header changed
     newest = max(os.path.getmtime(p) for p in _deps())
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
-    write_jit_headers()
     srcs = sources()
     with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         results = list(ex.map(lambda s: _compile(s, extra), srcs))
