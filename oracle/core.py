@@ -59,6 +59,10 @@ def _load():
                                         ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                         ctypes.c_int, dp, ip, ip]
             lib.tvo_forward.restype = ctypes.c_int
+            lib.tvo_step_solves.argtypes = [mp, ctypes.c_int, ctypes.c_int, dp, ip, dp, dp,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_int, dp, ip]
+            lib.tvo_step_solves.restype = ctypes.c_int
             lib.tvo_adjoint.argtypes = [mp, ctypes.c_int, ctypes.c_int, dp, ip, dp, dp, dp,
                                         ctypes.c_int, dp, dp]
             lib.tvo_adjoint.restype = ctypes.c_int
@@ -135,6 +139,24 @@ def forward(model, y0, times, params, lengths=None, tol_abs=1e-10, tol_rel=0.0, 
     if rc < 0:
         raise ValueError("tvo_forward rejected its arguments")
     return y, iters, status
+
+
+def step_solves(model, times, params, y_prev, lengths=None, tol_abs=1e-13, tol_rel=0.0,
+                max_iter=100, nthreads=0):
+    """Every backward-Euler step solved on its own from the given previous states:
+    out[b][k] solves step k from y_prev[b][k-1] (Sec. 2.2, the Newton of forward()).
+    Returns (out [B][N+1][n], status [B])."""
+    times, params, y_prev = _f64(times), _f64(params), _f64(y_prev)
+    B, Np1, n = y_prev.shape
+    lens = None if lengths is None else np.ascontiguousarray(lengths, dtype=np.int32)
+    out = np.empty_like(y_prev)
+    status = np.zeros(B, dtype=np.int32)
+    rc = _load().tvo_step_solves(ctypes.byref(model.c()), B, Np1 - 1, _dptr(times), _iptr(lens),
+                                 _dptr(params), _dptr(y_prev), float(tol_abs), float(tol_rel),
+                                 int(max_iter), int(nthreads), _dptr(out), _iptr(status))
+    if rc < 0:
+        raise ValueError("tvo_step_solves rejected its arguments")
+    return out, status
 
 
 def adjoint(model, times, params, y, grad_out, lengths=None, nthreads=0):

@@ -525,6 +525,54 @@ int tvo_max_threads(void) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* One backward-Euler step by Newton (Sec. 2.2): solve                        */
+/*   G(y) = y - y_prev - dt h(y, t; p) = 0,   J = dG/dy = I - dt j(y),          */
+/* from the previous-step guess y = y_prev, y <- y - J^{-1} G with a dense LU.  */
+/* Stops when ||G||_inf <= tol_abs or <= tol_rel ||G_0||_inf, or after         */
+/* max_iter updates.  w holds 2n + n^2 doubles.  Returns the status and the    */
+/* number of updates in *iters.                                                 */
+/* ------------------------------------------------------------------------ */
+static int be_step(const tvo_model* m, const double* p, const double* yprev, double dt, double tk,
+                   double tol_abs, double tol_rel, int max_iter, double* yk, int* iters,
+                   double* w) {
+  const int n = m->n;
+  double* G = w;
+  double* hv = G + n;
+  double* J = hv + n;
+  memcpy(yk, yprev, sizeof(double) * n); /* 0y_{k} = y_{k-1} */
+  double norm0 = 0.0;
+  int it = 0, st = TVO_OK;
+  for (;;) {
+    /* G = y_k - y_{k-1} - dt h(y_k, t_k; p) */
+    tvo_rhs(m, p, yk, tk, hv);
+    for (int i = 0; i < n; ++i) G[i] = yk[i] - yprev[i] - dt * hv[i];
+    double nr = inf_norm(n, G);
+    if (it == 0) norm0 = nr;
+    if (!isfinite(nr)) {
+      st = TVO_NONFINITE;
+      break;
+    }
+    if (nr <= tol_abs || nr <= tol_rel * norm0) break;
+    if (it >= max_iter) {
+      st = TVO_NOT_CONVERGED;
+      break;
+    }
+    /* J = I - dt j(y_k); y_k -= J^{-1} G */
+    tvo_jac(m, p, yk, tk, J);
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) J[r * n + c] = (r == c ? 1.0 : 0.0) - dt * J[r * n + c];
+    if (lu_solve(n, J, G)) {
+      st = TVO_SINGULAR;
+      break;
+    }
+    for (int i = 0; i < n; ++i) yk[i] -= G[i];
+    ++it;
+  }
+  *iters = it;
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Forward: Sec. 2.2 backward Euler + Newton, previous-step starting guess.   */
 /* ------------------------------------------------------------------------ */
 int tvo_forward(const tvo_model* m, int B, int N, const double* y0, const double* times,
@@ -542,48 +590,16 @@ int tvo_forward(const tvo_model* m, int B, int N, const double* y0, const double
     const double* p = m->per_series ? params + (size_t)b * P : params;
     const double* tb = times + (size_t)b * (N + 1);
     double* yb = y + (size_t)b * (N + 1) * n;
-    double* G = (double*)malloc(sizeof(double) * (3 * n + 2 * n * n));
-    double* hv = G + n;
-    double* yk = hv + n;
-    double* J = yk + n;
+    double* w = (double*)malloc(sizeof(double) * (2 * n + n * n));
     int st = TVO_OK;
     memcpy(yb, y0 + (size_t)b * n, sizeof(double) * n);
     for (int k = 1; k <= N; ++k) {
-      const double* yprev = yb + (size_t)(k - 1) * n;
-      double dt = step_dt(tb, lengths, b, k);
-      double tk = tb[k];
-      memcpy(yk, yprev, sizeof(double) * n); /* 0y_{k} = y_{k-1} */
-      double norm0 = 0.0;
       int it = 0;
-      for (;;) {
-        /* G = y_k - y_{k-1} - dt h(y_k, t_k; p) */
-        tvo_rhs(m, p, yk, tk, hv);
-        for (int i = 0; i < n; ++i) G[i] = yk[i] - yprev[i] - dt * hv[i];
-        double nr = inf_norm(n, G);
-        if (it == 0) norm0 = nr;
-        if (!isfinite(nr)) {
-          st = TVO_NONFINITE;
-          break;
-        }
-        if (nr <= tol_abs || nr <= tol_rel * norm0) break;
-        if (it >= max_iter) {
-          if (st == TVO_OK) st = TVO_NOT_CONVERGED;
-          break;
-        }
-        /* J = I - dt j(y_k); y_k -= J^{-1} G */
-        tvo_jac(m, p, yk, tk, J);
-        for (int r = 0; r < n; ++r)
-          for (int c = 0; c < n; ++c) J[r * n + c] = (r == c ? 1.0 : 0.0) - dt * J[r * n + c];
-        if (lu_solve(n, J, G)) {
-          st = TVO_SINGULAR;
-          break;
-        }
-        for (int i = 0; i < n; ++i) yk[i] -= G[i];
-        ++it;
-      }
+      int sk = be_step(m, p, yb + (size_t)(k - 1) * n, step_dt(tb, lengths, b, k), tb[k], tol_abs,
+                       tol_rel, max_iter, yb + (size_t)k * n, &it, w);
+      if (sk > st) st = sk;
       if (iters) iters[(size_t)b * N + (k - 1)] = it;
-      memcpy(yb + (size_t)k * n, yk, sizeof(double) * n);
-      if (st == TVO_NONFINITE || st == TVO_SINGULAR) {
+      if (sk == TVO_NONFINITE || sk == TVO_SINGULAR) {
         /* leave the rest of the trajectory as NaN: nothing after this is defined */
         for (int q = k + 1; q <= N; ++q)
           for (int i = 0; i < n; ++i) yb[(size_t)q * n + i] = NAN;
@@ -594,7 +610,45 @@ int tvo_forward(const tvo_model* m, int B, int N, const double* y0, const double
     }
     if (status) status[b] = st;
     if (st > worst) worst = st;
-    free(G);
+    free(w);
+  }
+  return worst;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Independent step solves (Sec. 2.2): for every series and step k = 1..N,    */
+/* the backward-Euler step from the GIVEN state y_prev[b][k-1], by the same    */
+/* Newton as tvo_forward.  out[b][0] = y_prev[b][0].  Checks any trajectory    */
+/* step by step without propagating its earlier differences.                   */
+/* ------------------------------------------------------------------------ */
+int tvo_step_solves(const tvo_model* m, int B, int N, const double* times, const int* lengths,
+                    const double* params, const double* y_prev, double tol_abs, double tol_rel,
+                    int max_iter, int nthreads, double* out, int* status) {
+  int P = tvo_param_count(m);
+  if (P < 0 || B < 0 || N < 0 || max_iter < 0) return TVO_BADARG;
+  int n = m->n;
+  int worst = TVO_OK;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(max : worst)
+#endif
+  for (int b = 0; b < B; ++b) {
+    const double* p = m->per_series ? params + (size_t)b * P : params;
+    const double* tb = times + (size_t)b * (N + 1);
+    const double* yb = y_prev + (size_t)b * (N + 1) * n;
+    double* ob = out + (size_t)b * (N + 1) * n;
+    double* w = (double*)malloc(sizeof(double) * (2 * n + n * n));
+    int st = TVO_OK;
+    memcpy(ob, yb, sizeof(double) * n);
+    for (int k = 1; k <= N; ++k) {
+      int it = 0;
+      int sk = be_step(m, p, yb + (size_t)(k - 1) * n, step_dt(tb, lengths, b, k), tb[k], tol_abs,
+                       tol_rel, max_iter, ob + (size_t)k * n, &it, w);
+      if (sk > st) st = sk;
+    }
+    if (status) status[b] = st;
+    if (st > worst) worst = st;
+    free(w);
   }
   return worst;
 }

@@ -100,6 +100,15 @@ int tvo_forward(const tvo_model* m, int B, int N, const double* y0, const double
                 const int* lengths, const double* params, double tol_abs, double tol_rel,
                 int max_iter, int nthreads, double* y, int* iters, int* status);
 
+/* Independent backward-Euler step solves: out[b][k] is the step k solution
+ * from the given y_prev[b][k-1] (the same Newton and stopping rule as
+ * tvo_forward), out[b][0] = y_prev[b][0].  status [B] (or NULL) receives the
+ * worst step status of the series.  Returns TVO_OK, TVO_BADARG or the worst
+ * status. */
+int tvo_step_solves(const tvo_model* m, int B, int N, const double* times, const int* lengths,
+                    const double* params, const double* y_prev, double tol_abs, double tol_rel,
+                    int max_iter, int nthreads, double* out, int* status);
+
 /* Discrete adjoint of tvo_forward's equations at the trajectory y.  Writes
  * dparams (zeroed first) and dy0 (may be NULL). */
 int tvo_adjoint(const tvo_model* m, int B, int N, const double* times, const int* lengths,

@@ -6,6 +6,11 @@ Each test names what it pins:
   * gradients of nonlinear models             -> central finite differences
   * model h, dh/dy, dh/dp                     -> torch library ops / autograd
   * nonlinear step root                       -> scipy.optimize.fsolve per step
+  * independent step solves                   -> closed-form linear step, the forward
+                                                 trajectory itself
+  * forward-error estimate                    -> closed-form propagation on a
+                                                 non-symmetric linear system; the
+                                                 observed tol vs tol/1000 difference
   * padding (dt = 0) and series independence  -> invariants
 """
 import numpy as np
@@ -172,6 +177,117 @@ def test_be_steps_against_scipy_fsolve(oracle_lib, which):
             scale = max(np.abs(x).max(), 1.0)
             assert np.abs(y[b, k] - x).max() <= 1e-9 * scale, (b, k)
             yp = x
+
+
+# --------------------------------------------------------------------------
+# Independent step solves: out_k solves step k from the GIVEN y_{k-1}.
+# --------------------------------------------------------------------------
+def _nonsym_linear(seed, n=4, lam_decades=(0.0, 3.0)):
+    """A = -V diag(lam) V^-1 with V a seeded well-conditioned non-orthogonal matrix,
+    so A != A^T (a transposed operand changes every result below)."""
+    g = np.random.default_rng(seed)
+    V = np.eye(n) + 0.4 * g.standard_normal((n, n))
+    lam = 10.0 ** g.uniform(lam_decades[0], lam_decades[1], n)
+    Vi = np.linalg.inv(V)
+    return -(V * lam[None, :]) @ Vi, V, Vi, lam
+
+
+def test_step_solves_linear_closed_form(oracle_lib):
+    """Linear h = A y: the BE step from any state x is (I - dt A)^-1 x =
+    V diag(1 / (1 + dt lam)) V^-1 x, here from states that are NOT a BE trajectory
+    (random draws) and on per-series non-uniform grids."""
+    A, V, Vi, lam = _nonsym_linear(101)
+    B, N = 3, 40
+    g = np.random.default_rng(102)
+    yprev = g.standard_normal((B, N + 1, 4))
+    times = workloads.random_times(103, B, N, t_end=0.05)
+    m = Model("linear", 4)
+    out, st = oracle_lib.step_solves(m, times, A.reshape(-1), yprev)
+    assert not st.any()
+    assert np.array_equal(out[:, 0], yprev[:, 0])
+    dt = np.diff(times, axis=1)  # [B][N]
+    z = np.einsum("ij,bkj->bki", Vi, yprev[:, :-1])  # V^-1 y_{k-1}
+    exact = np.einsum("ij,bkj->bki", V, z / (1.0 + dt[..., None] * lam[None, None, :]))
+    assert _relerr(out[:, 1:], exact) < 1e-12
+
+
+@pytest.mark.parametrize("which", ["vdp", "mds"])
+def test_step_solves_reproduce_forward(oracle_lib, which):
+    """Fed the oracle's own trajectory, every independent step solve starts where the
+    step-by-step integration started and runs the same Newton, so it reproduces the
+    trajectory exactly (an index slip between y_{k-1}, t_k and dt_k would not);
+    the time-dependent mass-damper-spring model checks t_k."""
+    if which == "vdp":
+        w = workloads.vdp(B=6, N=700, seed=104)
+    else:
+        w = workloads.mds(B=4, N=300, n_unit=2, jitter=0.2)
+    m = Model.from_spec(w["spec"])
+    tol = 1e-12 if which == "vdp" else 1e-18
+    y, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], tol_abs=tol, max_iter=60)
+    assert not st.any()
+    out, st2 = oracle_lib.step_solves(m, w["times"], w["params"], y, tol_abs=tol, max_iter=60)
+    assert not st2.any()
+    assert np.array_equal(out, y)
+    # shifting the states by one step breaks it
+    shifted = y.copy()
+    shifted[:, 1:] = y[:, :-1]
+    out2, _ = oracle_lib.step_solves(m, w["times"], w["params"], shifted, tol_abs=tol)
+    assert not np.array_equal(out2, y)
+
+
+# --------------------------------------------------------------------------
+# Forward-error estimate (random residuals propagated through the linearised
+# BE recursion d_k = A_k^-1 (d_{k-1} + r_k)).
+# --------------------------------------------------------------------------
+def test_forward_error_estimate_linear_closed_form(oracle_lib):
+    """On a linear system with uniform steps A_k = I - dt A for every k, so the
+    propagated perturbation has the closed form d_k = sum_{m<=k} (I - dt A)^-(k-m+1) r_m,
+    evaluated here as one lower-triangular Toeplitz product per eigenvalue of A
+    (V^-1 r in, V out), from the same random draws as the estimate."""
+    A, V, Vi, lam = _nonsym_linear(105, lam_decades=(0.0, 2.0))
+    B, N, n, tol, trials, seed = 3, 60, 4, 1e-9, 3, 7
+    times = workloads.uniform_times(B, N, 0.3)
+    dt = times[0, 1]
+    g = np.random.default_rng(106)
+    y = g.standard_normal((B, N + 1, n))  # only its scale enters
+    m = Model("linear", 4)
+    est = oracle_lib.forward_error_estimate(m, times, A.reshape(-1), y, tol, trials=trials,
+                                            seed=seed)
+    rg = np.random.default_rng(seed)
+    k = np.arange(N)
+    expo = k[:, None] - k[None, :] + 1  # k - m + 1 for m <= k
+    lower = expo >= 1
+    want = np.zeros(B)
+    for _ in range(trials):
+        r = rg.uniform(-tol, tol, (B, N, n))
+        s = np.einsum("ij,bmj->bmi", Vi, r)
+        z = np.zeros((B, N, n), dtype=complex if np.iscomplexobj(lam) else float)
+        for i in range(n):
+            T = np.where(lower, (1.0 / (1.0 + dt * lam[i])) ** np.maximum(expo, 1), 0.0)
+            z[:, :, i] = s[:, :, i] @ T.T
+        d = np.einsum("ij,bkj->bki", V, z).real
+        want = np.maximum(want, np.abs(d).max(axis=(1, 2)) / np.abs(y).max(axis=(1, 2)))
+    assert _relerr(est, want) < 1e-10
+
+
+def test_forward_error_estimate_brackets_observed(oracle_lib):
+    """The estimate sets the van der Pol trajectory gates at 10x its value.  Against
+    the difference actually observed between two oracle runs stopped at tol and at
+    tol/1000, it must bound that difference within the factor 10 on every series,
+    and not exceed it by more than 1000x where it is not negligible."""
+    w = workloads.vdp(B=16, N=2000)
+    m = Model.from_spec(w["spec"])
+    for tol in (1e-8, 1e-10):
+        y1, _, s1 = oracle_lib.forward(m, w["y0"], w["times"], w["params"], tol_abs=tol,
+                                       max_iter=100)
+        y2, _, s2 = oracle_lib.forward(m, w["y0"], w["times"], w["params"], tol_abs=tol / 1000,
+                                       max_iter=100)
+        assert not s1.any() and not s2.any()
+        obs = np.abs(y1 - y2).max(axis=(1, 2)) / np.abs(y2).max(axis=(1, 2))
+        est = oracle_lib.forward_error_estimate(m, w["times"], w["params"], y2, tol)
+        assert np.all(obs <= 10.0 * est), (tol, obs / est)
+        big = est >= 1e-3 * est.max()
+        assert np.all(obs[big] >= est[big] / 1000.0), (tol, obs[big] / est[big])
 
 
 # --------------------------------------------------------------------------
