@@ -5,14 +5,17 @@ The explicit recursion has one solution per series; Newton on the chunk system
 is stopped at a tight tolerance (1e-12), so the GPU trajectory is that solution
 up to residuals of that size, which the recursion may amplify (van der Pol's
 growing phase).  Gates per series: max(1e-10 relative with FP64 blocks, 1e-5 with
-FP32 blocks, 10 x the propagated forward-error estimate).
-Both adjoints run on the oracle's trajectory and are compared directly.
+FP32 blocks, 10 x the propagated forward-error estimate); and every step against
+the explicit step from the GPU's own previous state at 1e-10 (parity_helpers), a
+check no conditioning enters.  Both adjoints run on the oracle's trajectory and
+are compared directly.
 """
 import numpy as np
 import pytest
 
 import workloads
 from oracle import Model as OModel
+from parity_helpers import STEP_GATE, fe_step_errors
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -101,6 +104,7 @@ def test_forward_euler_forward_and_adjoint(tvi, oracle_lib, which, precision, ch
     err = relerr_series(y, ref)
     bad = np.nonzero(err > np.maximum(GATE[precision], 10.0 * est))[0]
     assert bad.size == 0, (bad, err[bad], est[bad])
+    assert fe_step_errors(oracle_lib, m, w, y).max() <= STEP_GATE
     B, Np1, n = ref.shape
     g = workloads.random_grad_out(81, B, Np1 - 1, n)
     dp_ref, dy0_ref = oracle_lib.adjoint_euler(m, w["times"], w["params"], ref, g)
@@ -122,6 +126,7 @@ def test_forward_euler_padded_lengths(tvi, oracle_lib, precision):
     est = fe_error_estimate(oracle_lib, m, dict(w, times=_padded_times(w["times"], lens)), ref,
                             1e-12)
     assert np.all(relerr_series(y, ref) <= np.maximum(GATE[precision], 10.0 * est))
+    assert fe_step_errors(oracle_lib, m, w, y, lengths=lens).max() <= STEP_GATE
     g = workloads.random_grad_out(82, 4, 600, 2)
     for b, L in enumerate(lens):
         g[b, L + 1:] = 0.0

@@ -15,6 +15,7 @@ import pytest
 
 import workloads
 from oracle import Model as OModel
+from parity_helpers import STEP_GATE, be_step_bound, be_step_errors
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -96,12 +97,13 @@ def node16(oracle_lib):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_node16_full_size(tvi, node16, precision):
+def test_node16_full_size(tvi, oracle_lib, node16, precision):
     w, ref, g, dp_ref, dy0_ref, est = node16
     y, stats, status, rc = gpu_forward(tvi, w, 200, precision, 1e-12)
     assert rc == 0 and not status.any()
     err = relerr_series(y, ref)
     assert np.all(err <= np.maximum(GATE[precision], 10.0 * est)), (err.max(), est.max())
+    assert be_step_errors(oracle_lib, OModel.from_spec(w["spec"]), w, y).max() <= STEP_GATE
     dp, dy0 = gpu_adjoint(tvi, w, 200, precision, ref, g)
     assert relerr(dp, dp_ref) <= GATE[precision]
     assert relerr(dy0, dy0_ref) <= GATE[precision]
@@ -182,13 +184,14 @@ def test_bf16_blocks_are_the_jacobian(tvi, node16):
     assert relerr(dy016, dy0_ref) <= 5e-3
 
 
-def test_bf16_node16_full_size(tvi, node16):
+def test_bf16_node16_full_size(tvi, oracle_lib, node16):
     w, ref, g, dp_ref, dy0_ref, est = node16
     y32, s32, _, rc32 = gpu_forward(tvi, w, 200, "fp32", 1e-12)
     y, stats, status, rc = gpu_forward(tvi, w, 200, "bf16", 1e-12)
     assert rc == 0 and rc32 == 0 and not status.any()
     err = relerr_series(y, ref)
     assert np.all(err <= np.maximum(GATE["bf16"], 10.0 * est)), (err.max(), est.max())
+    assert be_step_errors(oracle_lib, OModel.from_spec(w["spec"]), w, y).max() <= STEP_GATE
     # inexact-Newton blocks cost few extra updates; a wrong Jacobian costs many
     assert stats[:, 0].sum() <= 1.3 * s32[:, 0].sum(), (stats[:, 0].sum(), s32[:, 0].sum())
     dp, dy0 = gpu_adjoint(tvi, w, 200, "bf16", ref, g)
@@ -274,6 +277,12 @@ def test_node32_full_size_sampled(tvi, oracle_lib):
     assert rc == 0 and not status.any()
     err = relerr_series(y[sample], ref)
     assert np.all(err <= np.maximum(GATE["bf16"], 10.0 * est)), (err, est)
+    # every real step of the sampled series against the oracle's solve of that step
+    # from the GPU's own previous state: residuals of tol 1e-8 leave at most
+    # be_step_bound there (one step's conditioning)
+    step = be_step_errors(oracle_lib, m, sub, y[sample], lengths=sub["lengths"])
+    assert np.all(step <= be_step_bound(oracle_lib, m, sub, y[sample], tol,
+                                        lengths=sub["lengths"])), step
     g = np.zeros_like(y)
     g[sample] = workloads.random_grad_out(72, len(sample), y.shape[1] - 1, 32)
     for b_, L in zip(sample, lens[sample]):

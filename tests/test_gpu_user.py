@@ -7,8 +7,10 @@ any size, a tanh MLP, the mass-damper-spring chain, Chaboche viscoplasticity,
 coupled neurons), so forward trajectories and adjoint gradients are compared
 with the oracle exactly as for the built-in models: 1e-10 relative with FP64
 blocks, 1e-5 with FP32 blocks, and for nonlinear models max(gate, 10 x the
-propagated forward-error estimate) per series.  Sizes run from n = 1 to 20,
-most of them ones the built-in engines do not have.
+propagated forward-error estimate) per series, together with the
+conditioning-free check of every step against the oracle's solve of that step
+from the GPU's own previous state at 1e-10 (parity_helpers).  Sizes run from
+n = 1 to 20, most of them ones the built-in engines do not have.
 """
 import ctypes
 
@@ -17,6 +19,7 @@ import pytest
 
 import workloads
 from oracle import Model as OModel
+from parity_helpers import STEP_GATE, be_step_errors, fe_step_errors
 from test_gpu_euler import fe_error_estimate
 from paper_2310_08649_gb300.user_sources import CHABOCHE, LINEAR, MDS, NEURON, VDP, \
     VDP_FP64_JAC, chaboche_param_count, mds_param_count, mlp_param_count, mlp_tanh, \
@@ -107,6 +110,7 @@ def test_user_vdp_matches_oracle(tvi, users, oracle_lib, precision, chunk, jac):
     err = relerr_series(y, ref)
     bad = np.nonzero(err > np.maximum(GATE[precision], 10.0 * est))[0]
     assert bad.size == 0, (bad, err[bad], est[bad])
+    assert be_step_errors(oracle_lib, m, w, y).max() <= STEP_GATE
     g = workloads.random_grad_out(91, 32, 3000, 2)
     dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g)
     dp, dy0 = adjoint(tvi, model, w, o, ref, g)
@@ -183,6 +187,7 @@ def test_user_forward_euler(tvi, users, oracle_lib, precision):
     # explicit recursion: residuals of 1e-12 grow with the recursion's conditioning
     est = fe_error_estimate(oracle_lib, m, w, ref, 1e-12)
     assert np.all(relerr_series(y, ref) <= np.maximum(GATE[precision], 10.0 * est))
+    assert fe_step_errors(oracle_lib, m, w, y).max() <= STEP_GATE
     g = workloads.random_grad_out(94, 8, 1500, 2)
     dp_ref, dy0_ref = oracle_lib.adjoint_euler(m, w["times"], w["params"], ref, g)
     dp, dy0 = adjoint(tvi, model, w, o, ref, g)
@@ -302,6 +307,7 @@ def test_user_chaboche_matches_oracle(tvi, users, oracle_lib, precision, u, chun
     err = relerr_series(y, ref)
     bad = np.nonzero(err > np.maximum(GATE[precision], 10.0 * est))[0]
     assert bad.size == 0, (bad, err[bad], est[bad])
+    assert be_step_errors(oracle_lib, m, w, y).max() <= STEP_GATE
     g = workloads.random_grad_out(190 + u, 12, 2000, 2 + u)
     dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g)
     dp, dy0 = adjoint(tvi, model, w, o, ref, g)
@@ -331,6 +337,7 @@ def test_user_neuron_matches_oracle(tvi, users, oracle_lib, precision, u, chunk)
     err = relerr_series(y, ref)
     bad = np.nonzero(err > np.maximum(GATE[precision], 10.0 * est))[0]
     assert bad.size == 0, (bad, err[bad], est[bad])
+    assert be_step_errors(oracle_lib, m, w, y).max() <= STEP_GATE
     g = workloads.random_grad_out(240 + u, 16, 2000, 4 * u)
     dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g)
     dp, dy0 = adjoint(tvi, model, w, o, ref, g)
@@ -361,6 +368,7 @@ def test_user_large_forward_euler(tvi, users, oracle_lib, precision, which, chun
     est = fe_error_estimate(oracle_lib, m, w, ref, 1e-12)
     err = relerr_series(y, ref)
     assert np.all(err <= np.maximum(GATE[precision], 10.0 * est)), (err.max(), est.max())
+    assert fe_step_errors(oracle_lib, m, w, y).max() <= STEP_GATE
     n = w["spec"]["n"]
     g = workloads.random_grad_out(252, 12, 2000, n)
     dp_ref, dy0_ref = oracle_lib.adjoint_euler(m, w["times"], w["params"], ref, g)

@@ -15,7 +15,8 @@ plus generator-specific extras.
 
 Default sizes are the paper-shaped workloads:
   linear_stiff  n=4 stiff linear system, 16 series, 1000 uniform steps on [0, 1]
-  vdp           van der Pol n=2, 128 series, 10,000 log-spaced steps per series
+  vdp           van der Pol n=2, 128 series, 10,000 log-spaced steps per series over
+                [0, min(3 mu, 500 / mu)]
   mlp_ode       neural ODE n=16, MLP 16-64-64-16 tanh, 64 series, 2000 steps on [0, 10]
   mlp_large     neural ODE n=32, MLP 32-128-128-32 SiLU, 512 series, 20,000 padded
                 steps with per-series lengths uniform in [2000, 20000]
@@ -67,18 +68,22 @@ def linear_stiff(seed=SEED_LINEAR, B=16, N=1000, n=4, t_end=1.0, lam_decades=(0.
             "lengths": None, "Q": Q, "lam": lam}
 
 
-def vdp(seed=SEED_VDP, B=128, N=10000, t_max=3.0, mu_dt_max=0.69, mu_decades=(1.0, 3.0)):
+def vdp(seed=SEED_VDP, B=128, N=10000, span_mu=3.0, t_max=None, mu_dt_max=0.69,
+        mu_decades=(1.0, 3.0)):
     """van der Pol, mu log-uniform in [10, 1000] per series, y0 uniform in [-2, 2]^2,
-    N log-spaced steps (6 decades).  The largest log step is about
-    t_end 6 ln(10) / (N - 1), so series b ends at
-        t_end = min(t_max, mu_dt_max (N - 1) / (6 ln(10) mu_b))
-    (= min(3, 500 / mu_b) at N = 10,000): mu dt <= mu_dt_max at every step and the
-    grid resolves the fast time scale 1/mu everywhere.  Times differ per series."""
+    N log-spaced steps (6 decades) over [0, span_mu * mu].  The largest log step
+    is about t_end 6 ln(10) / (N - 1), so series b ends at
+        t_end = min(span_mu mu_b, mu_dt_max (N - 1) / (6 ln(10) mu_b))
+    (= min(3 mu_b, 500 / mu_b) at N = 10,000): mu dt <= mu_dt_max at every step and
+    the grid resolves the fast time scale 1/mu everywhere.  t_max, when given, caps
+    t_end further.  Times differ per series."""
     g = _rng(seed)
     mu = 10.0 ** g.uniform(mu_decades[0], mu_decades[1], B)
     y0 = g.uniform(-2.0, 2.0, (B, 2))
     resolve = 500.0 * (N - 1) / 9999.0 * (mu_dt_max / 0.69)
-    t_end = np.minimum(t_max, resolve / mu)
+    t_end = np.minimum(span_mu * mu, resolve / mu)
+    if t_max is not None:
+        t_end = np.minimum(t_end, t_max)
     times = log_times(B, N, 1.0) * t_end[:, None]
     return {"spec": {"kind": "vdp", "n": 2, "hidden": (0, 0), "per_series": True},
             "y0": y0, "times": times, "params": mu.reshape(B, 1).copy(), "lengths": None}
