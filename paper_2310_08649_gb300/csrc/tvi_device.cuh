@@ -235,13 +235,28 @@ __device__ __forceinline__ void sync_first(int nthreads) {
     asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
+// Max of a 32-bit unsigned value over the warp (one redux.sync instruction).
+__device__ __forceinline__ unsigned warp_max_u32(unsigned v) {
+  unsigned r;
+  asm volatile("redux.sync.max.u32 %0, %1, 0xffffffff;" : "=r"(r) : "r"(v));
+  return r;
+}
+
+// Exact 64-bit max over the warp: the largest high word, then the largest low
+// word among the lanes that hold it.
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+  const unsigned hi = static_cast<unsigned>(v >> 32), lo = static_cast<unsigned>(v);
+  const unsigned mh = warp_max_u32(hi);
+  const unsigned ml = warp_max_u32(hi == mh ? lo : 0u);
+  return (static_cast<unsigned long long>(mh) << 32) | ml;
+}
+
 // Max over the `nwa` warps that call it (the block's first nwa warps).  The
 // caller guarantees a barrier between two consecutive calls (s_red is reused).
 __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v,
                                                             unsigned long long* s_red, int lane,
                                                             int warp, int nwa) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(kFull, v, o));
+  v = warp_max_u64(v);
   if (nwa == 1) return v;  // one warp: no barrier needed
   if (lane == 0) s_red[warp] = v;
   sync_first(32 * nwa);
@@ -250,20 +265,35 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
   return r;
 }
 
+// The last of a thread's first `rpa` rows (1 <= rpa <= RPT), without a dynamic
+// register index.
+template <int RPT, int NS>
+__device__ __forceinline__ void last_row(const double (&v)[RPT][NS], int rpa, double (&out)[NS]) {
+#pragma unroll
+  for (int s = 0; s < NS; ++s) out[s] = v[RPT - 1][s];
+#pragma unroll
+  for (int r = 0; r < RPT - 1; ++r)
+    if (r == rpa - 1)
+#pragma unroll
+      for (int s = 0; s < NS; ++s) out[s] = v[r][s];
+}
+
 // ---------------------------------------------------------------------------
 // Solve the chain d_j = M_j d_{j-1} + v_j over the block's rows, d_{-1} = 0.
-// Called by the block's first `nwa` warps only; thread t holds rows
-// t*RPT .. t*RPT+RPT-1 in f[], and rows past the chunk end must hold the
-// identity map.  On return x[r] = d of each own row.  Synchronisation: two
-// barriers over those warps when nwa > 1.
+// Called by the block's first `nwa` warps only; thread t holds its rows in
+// f[0 .. rpa-1] (rpa <= RPT, the same in every thread), and rows past the
+// chunk end must hold the identity map.  On return x[r] = d of each own row
+// r < rpa.  Synchronisation: two barriers over those warps when nwa > 1.
 // ---------------------------------------------------------------------------
 template <int NS, typename T, int RPT>
 __device__ __forceinline__ void solve_chain(const Aff<NS, T> (&f)[RPT], T (&x)[RPT][NS],
-                                            Aff<NS, T>* s_wtot, int lane, int warp, int nwa) {
+                                            Aff<NS, T>* s_wtot, int lane, int warp, int nwa,
+                                            int rpa = RPT) {
   // (1) serial composition of the thread's own rows
   Aff<NS, T> seg = f[0];
 #pragma unroll
-  for (int r = 1; r < RPT; ++r) seg = compose(f[r], seg);
+  for (int r = 1; r < RPT; ++r)
+    if (r < rpa) seg = compose(f[r], seg);
   // (2) cyclic reduction over the lanes of the warp
 #pragma unroll
   for (int s = 1; s < 32; s <<= 1) {
@@ -316,6 +346,7 @@ __device__ __forceinline__ void solve_chain(const Aff<NS, T> (&f)[RPT], T (&x)[R
   // (4) fix-up: substitute forward through the own rows
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
+    if (r >= rpa) break;  // the same in every thread
     T xn[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) {

@@ -25,16 +25,17 @@ __device__ __forceinline__ double model_time(const double* tb, int k) {
 template <class Model, int RPT>
 __device__ __forceinline__ unsigned long long residual_norm_block(
     const Model& mdl, const double (&yi)[Model::NS], const double (&dyv)[RPT][Model::NS],
-    const double (&dt)[RPT], const bool (&act)[RPT], const double* tb, int k0,
+    const double (&dt)[RPT], const bool (&act)[RPT], int rpa, const double* tb, int k0,
     double (*s_wlast)[Model::NS], unsigned long long* s_red, int lane, int warp) {
   constexpr int NS = Model::NS;
   const int nwarps = static_cast<int>(blockDim.x >> 5);
-  double prev[NS];
+  double prev[NS], mine[NS];
+  last_row<RPT, NS>(dyv, rpa, mine);
 #pragma unroll
-  for (int s = 0; s < NS; ++s) prev[s] = __shfl_up_sync(kFull, dyv[RPT - 1][s], 1);
+  for (int s = 0; s < NS; ++s) prev[s] = __shfl_up_sync(kFull, mine[s], 1);
   if (lane == 31) {
 #pragma unroll
-    for (int s = 0; s < NS; ++s) s_wlast[warp][s] = dyv[RPT - 1][s];
+    for (int s = 0; s < NS; ++s) s_wlast[warp][s] = mine[s];
   }
   __syncthreads();
   if (lane == 0) {
@@ -44,6 +45,7 @@ __device__ __forceinline__ unsigned long long residual_norm_block(
   unsigned long long mx = 0ull;
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
+    if (r >= rpa) break;  // block-uniform
     double y[NS], h[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) y[s] = yi[s] + dyv[r][s];
@@ -104,8 +106,13 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
   int i = 0, c_cur = a.chunk;
   while (i < N) {
     const int L = min(c_cur, N - i);
+    // rows per thread of this attempt: one while the attempt fits the block's
+    // threads, else RPT.  A warp's FP64 instructions issue one per 64 cycles
+    // whatever its active lanes, so a short attempt spread one row per thread
+    // runs half the FP64 instructions per warp (and more warps in parallel).
+    const int rpa = (L + static_cast<int>(blockDim.x) - 1) / static_cast<int>(blockDim.x);
     // warps holding at least one step of this attempt; the rest skip all work
-    const int nwa = ((L + RPT - 1) / RPT + 31) / 32;
+    const int nwa = ((L + rpa - 1) / rpa + 31) / 32;
     const bool wact = warp < nwa;
     const bool can_halve = a.retry_halving && c_cur > 1;
     // ---- per-thread rows of this chunk attempt ----
@@ -118,9 +125,9 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
     for (int s = 0; s < NS; ++s) yiT[s] = narrow<T>(yi[s]);
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-      const int j = tid * RPT + r;
+      const int j = tid * rpa + r;
       const int k = i + 1 + j;
-      act[r] = j < L;
+      act[r] = r < rpa && j < L;
       dt[r] = (act[r] && k <= len) ? (tb[k] - tb[k - 1]) : 0.0;
       dtT[r] = narrow<T>(dt[r]);
 #pragma unroll
@@ -146,7 +153,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
         if (tid == 0) feat[NS] = mdl.param_feature();
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
-          if (act[r]) feat[NS + 1 + tid * RPT + r] = log10f(fmaxf(static_cast<float>(dt[r]), 1e-30f));
+          if (act[r]) feat[NS + 1 + tid * rpa + r] = log10f(fmaxf(static_cast<float>(dt[r]), 1e-30f));
         __syncthreads();
         pred_infer_block(a.pred, pd, feat, h1, h2, outv);
         // the network proposes per-step slopes s_j; the guess is their running
@@ -155,7 +162,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
         for (int r = 0; r < RPT; ++r)
           if (act[r])
 #pragma unroll
-            for (int s = 0; s < NS; ++s) outv[(tid * RPT + r) * NS + s] *= static_cast<float>(dt[r]);
+            for (int s = 0; s < NS; ++s) outv[(tid * rpa + r) * NS + s] *= static_cast<float>(dt[r]);
         __syncthreads();
         if (warp == 0) {
           constexpr int kPer = (kPredMaxChunk + 31) / 32;
@@ -197,18 +204,18 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
         for (int r = 0; r < RPT; ++r)
 #pragma unroll
           for (int s = 0; s < NS; ++s)
-            dyp[r][s] = act[r] ? static_cast<double>(outv[(tid * RPT + r) * NS + s]) : 0.0;
+            dyp[r][s] = act[r] ? static_cast<double>(outv[(tid * rpa + r) * NS + s]) : 0.0;
         double dz[RPT][NS];
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
 #pragma unroll
           for (int s = 0; s < NS; ++s) dz[r][s] = 0.0;
         const unsigned long long n_zero =
-            residual_norm_block<Model, RPT>(mdl, yi, dz, dt, act, tb, i + 1 + tid * RPT, s_wlast,
-                                            s_red, lane, warp);
+            residual_norm_block<Model, RPT>(mdl, yi, dz, dt, act, rpa, tb, i + 1 + tid * rpa,
+                                            s_wlast, s_red, lane, warp);
         const unsigned long long n_pred =
-            residual_norm_block<Model, RPT>(mdl, yi, dyp, dt, act, tb, i + 1 + tid * RPT, s_wlast,
-                                            s_red, lane, warp);
+            residual_norm_block<Model, RPT>(mdl, yi, dyp, dt, act, rpa, tb, i + 1 + tid * rpa,
+                                            s_wlast, s_red, lane, warp);
         if (n_pred < n_zero) {  // both finite bit patterns compare as values
 #pragma unroll
           for (int r = 0; r < RPT; ++r)
@@ -229,19 +236,24 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
       }
     }
 
-    double norm0 = 0.0;
     int it = 0, outcome = kConv;
+    // Convergence and divergence are decided on FP64 bit patterns (ordered like
+    // the values for non-negative doubles) against thresholds formed once per
+    // attempt from its first residual, so no FP64 instruction sits in a pass's
+    // control flow.
+    unsigned long long thr_bits = 0ull, div_bits = 0ull;
     // Only the nwa warps holding steps run the Newton loop; they synchronise on
     // a named barrier among themselves, the others wait at the barrier after it.
     if (wact) {
     for (;;) {
-      // dy_{j-1} of the first own row: last row of the previous thread
-      double prev[NS];
+      // y_{j-1} of the first own row: last row of the previous thread
+      double prev[NS], mine[NS];
+      last_row<RPT, NS>(yv, rpa, mine);
 #pragma unroll
-      for (int s = 0; s < NS; ++s) prev[s] = __shfl_up_sync(kFull, yv[RPT - 1][s], 1);
+      for (int s = 0; s < NS; ++s) prev[s] = __shfl_up_sync(kFull, mine[s], 1);
       if (lane == 31) {
 #pragma unroll
-        for (int s = 0; s < NS; ++s) s_wlast[warp][s] = yv[RPT - 1][s];
+        for (int s = 0; s < NS; ++s) s_wlast[warp][s] = mine[s];
       }
       sync_first(32 * nwa);
       if (lane == 0) {  // the row before row 0 is the chunk start y_i
@@ -251,9 +263,14 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
       // ---- residual, FP64 ----
       double R[RPT][NS];
       unsigned long long mx = 0ull;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) R[r][s] = 0.0;
       if (wact) {
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
+          if (r >= rpa) break;  // block-uniform: no FP64 work for rows this attempt lacks
           // backward Euler evaluates h at y_j, forward Euler at y_{j-1} (Sec. 2.2)
           double yp[NS], yh[NS], h[NS];
 #pragma unroll
@@ -261,7 +278,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
             yp[s] = (r == 0) ? prev[s] : yv[r - 1][s];
             yh[s] = fwd_euler ? yp[s] : yv[r][s];
           }
-          const int k = i + 1 + tid * RPT + r;
+          const int k = i + 1 + tid * rpa + r;
           mdl.rhs(yh, act[r] ? model_time<Model>(tb, fwd_euler ? k - 1 : k) : 0.0, h);
 #pragma unroll
           for (int s = 0; s < NS; ++s) {
@@ -271,33 +288,35 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
         }
       }
       const unsigned long long nb = block_max_u64(mx, s_red, lane, warp, nwa);
-      const double nr = __longlong_as_double(static_cast<long long>(nb));
-      if (it == 0) norm0 = nr;
-      if (nb < kNonFiniteBits && (nr <= a.tol_abs || nr <= a.tol_rel * norm0)) {
+      if (it == 0) {  // this attempt's thresholds, from its first residual
+        const double nr0 = __longlong_as_double(static_cast<long long>(nb));
+        thr_bits = abs_bits(fmax(a.tol_abs, a.tol_rel * nr0));
+        div_bits = abs_bits(10.0 * nr0);
+      }
+      if (nb <= thr_bits) {  // finite and within tol_abs or tol_rel ||R_0||
         outcome = kConv;
         break;
       }
       // When a smaller chunk can still be tried, an attempt whose residual is
       // still above 10x its starting value after 4 updates is abandoned early
       // (a heuristic for speed only: the retry solves the same equations).
-      const int fail = nb >= kNonFiniteBits                          ? kNonFinite
-                       : it >= a.max_iter                            ? kMaxIter
-                       : (can_halve && it >= 4 && nr > 10.0 * norm0) ? kDiverged
-                                                                     : kConv;
+      const int fail = nb >= kNonFiniteBits                      ? kNonFinite
+                       : it >= a.max_iter                        ? kMaxIter
+                       : (can_halve && it >= 4 && nb > div_bits) ? kDiverged
+                                                                 : kConv;
       if (fail != kConv) {
         outcome = fail;
         if (can_halve) {
           // Rows whose backward-Euler residual is already within the tolerance form
           // a solution of their steps (row j involves only y_{j-1} and y_j), so the
           // attempt's longest such prefix is kept: first row index over tolerance.
-          const unsigned long long thr = abs_bits(fmax(a.tol_abs, a.tol_rel * norm0));
           unsigned long long v = 0ull;  // ~j of the first row over tolerance, max-reduced
 #pragma unroll
           for (int r = 0; r < RPT; ++r) {
             bool over = false;
 #pragma unroll
-            for (int s = 0; s < NS; ++s) over = over || abs_bits(R[r][s]) > thr;
-            if (act[r] && over) v = umax64(v, ~static_cast<unsigned long long>(tid * RPT + r));
+            for (int s = 0; s < NS; ++s) over = over || abs_bits(R[r][s]) > thr_bits;
+            if (act[r] && over) v = umax64(v, ~static_cast<unsigned long long>(tid * rpa + r));
           }
           sync_first(32 * nwa);  // s_red reuse
           const unsigned long long m = block_max_u64(v, s_red, lane, warp, nwa);
@@ -324,7 +343,7 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
                 else yt[s] = yv[r][s];
               }
             }
-            const int k = i + 1 + tid * RPT + r;
+            const int k = i + 1 + tid * rpa + r;
             mdl.step_matrix(yt, model_time<Model>(tb, fwd_euler ? k - 1 : k), dtT[r],
                             A);  // A = I - dt j
             T Rt[NS];
@@ -353,14 +372,14 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
           }
         }
       }
-      solve_chain<NS, T, RPT>(f, d, s_wtot, lane, warp, nwa);
+      solve_chain<NS, T, RPT>(f, d, s_wtot, lane, warp, nwa, rpa);
       // ---- Newton update, FP64 accumulate ----
       if (wact) {
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
 #pragma unroll
           for (int s = 0; s < NS; ++s)
-            if (act[r]) {
+            if (r < rpa && act[r]) {
               yv[r][s] -= widen<T>(d[r][s]);
               if constexpr (kMixed) yT[r][s] -= d[r][s];
             }
@@ -383,13 +402,13 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
       if (K >= kMinPrefix) {
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
-          const int j = tid * RPT + r;
+          const int j = tid * rpa + r;
           if (act[r] && j < K) {
             double* out = yb + static_cast<size_t>(i + 1 + j) * NS;
 #pragma unroll
             for (int s = 0; s < NS; ++s) out[s] = yv[r][s];
           }
-          if (j == K - 1) {
+          if (act[r] && j == K - 1) {
 #pragma unroll
             for (int s = 0; s < NS; ++s) s_carry[s] = yv[r][s];
           }
@@ -417,13 +436,13 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
     // ---- write the chunk's trajectory and carry y_{i+L} ----
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-      const int j = tid * RPT + r;
+      const int j = tid * rpa + r;
       if (act[r]) {
         double* out = yb + static_cast<size_t>(i + 1 + j) * NS;
 #pragma unroll
         for (int s = 0; s < NS; ++s) out[s] = yv[r][s];
       }
-      if (j == L - 1) {
+      if (act[r] && j == L - 1) {
 #pragma unroll
         for (int s = 0; s < NS; ++s) s_carry[s] = yv[r][s];
       }
