@@ -142,6 +142,14 @@ int tvi_param_count(const tvi_model* model);
  * any later call with the same or smaller sizes. */
 size_t tvi_workspace_bytes(const tvi_model* model, const tvi_options* opt, int B, int N);
 
+/* Steps one chunk attempt holds for this model and these options over N steps
+ * (Sec. 2.3, n_chunk as actually solved), or -1 for a bad model or options.  The
+ * small-state engine (linear, van der Pol, user models with n <= 4) keeps a
+ * chunk on one multiprocessor and solves at most 1024 steps together: a larger
+ * opt->chunk runs as 1024-step chunks, which solve the same equations to the
+ * same tolerance.  Every engine also stops at N. */
+int tvi_effective_chunk(const tvi_model* model, const tvi_options* opt, int N);
+
 /*
  * Forward integration, chunked backward (or forward, opt->scheme) Euler with
  * Newton (Alg. 1).
@@ -206,18 +214,22 @@ tvi_status tvi_adjoint(const tvi_model* model, const tvi_options* opt, int B, in
  *
  * Arguments and results are those of tvi_adjoint, minus the workspace.  The
  * per-series partial gradients of shared parameters live instead in a fixed
- * 4 MiB array inside the library's device image, which every GPU that loads the
- * library holds until the process exits; B * P > 524,288 with shared
+ * 4 MiB array inside the library's device image, which every GPU where it is
+ * used holds until the process exits; B * P > 524,288 with shared
  * parameters (per_series = 0) is rejected with TVI_EINVAL.  Per-series
  * parameters need no scratch.  The call allocates nothing: no cudaMalloc,
  * cudaFree or allocating library routine.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, once per device, with that device current); make that
- * first call before any stream capture.  All calls share the one array: calls
- * whose work overlaps on the GPU (other streams, other host threads) race on it
- * and must be serialised by the caller.  Every call overwrites the entries it
- * reads, so nothing from an earlier call leaks into a later result.
+ * With lazy module loading (the CUDA default) the 4 MiB is committed on the first
+ * call on each device rather than when the library loads: a caller whose
+ * allocator will reserve the whole device should make that first call before
+ * it does.  The first call in each CUDA context also looks up the array's
+ * device address (cudaGetSymbolAddress, with that context's device current);
+ * make it before any stream capture.  A context created after cudaDeviceReset
+ * gets its own lookup.  All calls share the one array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on it and must
+ * be serialised by the caller.  Every call overwrites the entries it reads, so
+ * nothing from an earlier call leaks into a later result.
  */
 tvi_status tvi_adjoint_noalloc(const tvi_model* model, const tvi_options* opt, int B, int N,
                                const double* times, const int* lengths, const double* params,

@@ -6,8 +6,8 @@ solved by parallel cyclic reduction, and the discrete adjoint for parameter
 gradients.  The computation lives in the CUDA library built from csrc/ (C ABI
 in include/tvi.h); this package is its thin Python binding.
 """
-from .api import Integrate, Model, Options, UserModel, adjoint, integrate, make_workspace, \
-    odeint, workspace_bytes
+from .api import Integrate, Model, Options, UserModel, adjoint, effective_chunk, integrate, \
+    make_workspace, odeint, workspace_bytes
 
-__all__ = ["Integrate", "Model", "Options", "UserModel", "adjoint", "integrate", "make_workspace",
-           "odeint", "workspace_bytes"]
+__all__ = ["Integrate", "Model", "Options", "UserModel", "adjoint", "effective_chunk",
+           "integrate", "make_workspace", "odeint", "workspace_bytes"]

@@ -19,7 +19,8 @@ STATUS = {0: "TVI_OK", -1: "TVI_EINVAL", -2: "TVI_EWORKSPACE", -3: "TVI_ECUDA",
 TVI_ENOTCONV, TVI_ENONFINITE = -4, -5
 
 # every symbol include/tvi.h declares
-EXPORTS = ("tvi_default_options", "tvi_param_count", "tvi_workspace_bytes", "tvi_integrate",
+EXPORTS = ("tvi_default_options", "tvi_param_count", "tvi_workspace_bytes",
+           "tvi_effective_chunk", "tvi_integrate",
            "tvi_adjoint", "tvi_adjoint_noalloc", "tvi_predictor_size", "tvi_predictor_forward",
            "tvi_predictor_workspace_bytes", "tvi_predictor_train_step", "tvi_user_model_create",
            "tvi_user_model_prepare", "tvi_user_model_destroy", "tvi_kernel_launches",
@@ -70,6 +71,8 @@ def load():
             lib.tvi_param_count.restype = ctypes.c_int
             lib.tvi_workspace_bytes.argtypes = [mp, op, ctypes.c_int, ctypes.c_int]
             lib.tvi_workspace_bytes.restype = sz
+            lib.tvi_effective_chunk.argtypes = [mp, op, ctypes.c_int]
+            lib.tvi_effective_chunk.restype = ctypes.c_int
             lib.tvi_integrate.argtypes = [mp, op, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp,
                                           vp, vp, vp, sz, vp]
             lib.tvi_integrate.restype = ctypes.c_int

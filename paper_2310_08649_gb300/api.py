@@ -147,6 +147,12 @@ def workspace_bytes(model, opts, B, N):
     return _lib.load().tvi_workspace_bytes(ctypes.byref(model.c()), ctypes.byref(opts.c()), B, N)
 
 
+def effective_chunk(model, opts, N):
+    """Steps one chunk attempt holds (tvi_effective_chunk): the requested chunk,
+    at most N, and at most 1024 on the small-state engine."""
+    return _lib.load().tvi_effective_chunk(ctypes.byref(model.c()), ctypes.byref(opts.c()), N)
+
+
 def make_workspace(model, opts, B, N, device):
     return torch.empty(max(workspace_bytes(model, opts, B, N), 256), dtype=torch.uint8,
                        device=device)

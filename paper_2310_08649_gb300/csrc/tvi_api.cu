@@ -214,6 +214,14 @@ size_t tvi_workspace_bytes(const tvi_model* model, const tvi_options* opt, int B
   return layout(B, P).total;
 }
 
+int tvi_effective_chunk(const tvi_model* model, const tvi_options* opt, int N) {
+  if (tvi_param_count(model) < 0 || !opt || opt->chunk < 1 || N < 0) return -1;
+  if (is_mlp(model) || is_large_user(model)) return mlp_chunk(opt, N);
+  int c = opt->chunk < tvi::kSmallMaxChunk ? opt->chunk : tvi::kSmallMaxChunk;
+  if (N >= 1 && c > N) c = N;
+  return c;
+}
+
 tvi_status tvi_integrate(const tvi_model* model, const tvi_options* opt, int B, int N,
                          const double* y0, const double* times, const int* lengths,
                          const double* params, double* y_out, int* stats, int* series_status,
@@ -418,12 +426,19 @@ const char* tvi_version(void) { return "tvi sm_103a"; }
 // parameters; this variant keeps that scratch in a fixed array that lives in
 // the library's device image instead.
 //
-// The array is loaded with the library's GPU code, so every GPU that loads the
-// library holds its kNoAllocScratchBytes until the process exits.  Host code
-// cannot use the array's name as a device address (on the host it names a
-// shadow variable), so the device address is looked up with
-// cudaGetSymbolAddress once per device, with that device current, on the first
-// call made on it; make that first call before any stream capture.
+// The array is part of the library's GPU code, so every GPU that runs that
+// code holds its kNoAllocScratchBytes until the process exits.  With lazy
+// module loading (the CUDA default since 12.2) the module, and with it the
+// 4 MiB, is committed on the first call that needs it on a device -- the
+// first call of this entry point there -- not when the library is loaded: a
+// caller whose allocator will reserve the whole device should make that first
+// call before it does.  Host code cannot use the array's name as a device
+// address (on the host it names a shadow variable), so the device address is
+// looked up with cudaGetSymbolAddress once per CUDA context, with its device
+// current, on the first call made in that context; make that first call
+// before any stream capture.  The cache is keyed by the context's unique id,
+// so a context created after cudaDeviceReset gets its own lookup instead of a
+// stale address.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -432,6 +447,34 @@ constexpr int kNoAllocMaxDevices = 64;
 
 std::mutex g_noalloc_mu;
 double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kNoAllocMaxDevices] = {};
+
+// Unique id of the calling thread's current context (cuCtxGetId, reached through
+// the runtime's driver entry points), or 0 when it cannot be read.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    // both functions exist with these signatures since CUDA 12.0
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    looked_up = true;
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+  return 0;
+}
 
 }  // namespace
 
@@ -439,7 +482,8 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles
 
 namespace {
 
-// Device address of g_noalloc_scratch on the current device (looked up once).
+// Device address of g_noalloc_scratch in the current context (looked up once per
+// context).
 tvi_status noalloc_scratch(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -448,13 +492,17 @@ tvi_status noalloc_scratch(double** out) {
     return fail(TVI_EUNSUPPORTED, "tvi_adjoint_noalloc: device %d beyond the supported %d", dev,
                 kNoAllocMaxDevices);
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  // no context may be current yet on a fresh thread (id 0): the lookup then binds
+  // the device's primary context, and its id is read after it
+  const unsigned long long ctx = current_context_id();
+  if (!g_noalloc_addr[dev] || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
                        "tvi_adjoint_noalloc: cudaGetSymbolAddress of the scratch array");
     g_noalloc_addr[dev] = static_cast<double*>(p);
+    g_noalloc_ctx[dev] = current_context_id();
   }
   *out = g_noalloc_addr[dev];
   return TVI_OK;

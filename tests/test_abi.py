@@ -48,6 +48,21 @@ def test_defaults_param_counts_and_workspace(lib):
     assert ws >= 256 + 16 * 16 * 8 and ws % 256 == 0
 
 
+def test_effective_chunk(lib):
+    """The small-state engine solves at most 1024 steps together; every engine stops at N."""
+    from paper_2310_08649_gb300 import Model, Options, effective_chunk
+    vdp = Model("vdp", 2, per_series=True)
+    assert effective_chunk(vdp, Options(chunk=4096), 10000) == 1024
+    assert effective_chunk(vdp, Options(chunk=1000), 10000) == 1000
+    assert effective_chunk(vdp, Options(chunk=100), 50) == 50
+    assert effective_chunk(vdp, Options(chunk=7), 0) == 7
+    mlp = Model("mlp_tanh", 16, (64, 64))
+    assert effective_chunk(mlp, Options(chunk=5000), 2000) == 2000
+    assert effective_chunk(mlp, Options(chunk=3000), 20000) == 3000
+    assert effective_chunk(Model("vdp", 3), Options(chunk=10), 10) == -1
+    assert effective_chunk(vdp, Options(chunk=0), 10) == -1
+
+
 def test_argument_errors_are_returned_without_touching_the_gpu(lib):
     """Validation happens before any CUDA call, so these run on a CPU-only host."""
     from paper_2310_08649_gb300 import Model, Options, _lib
