@@ -72,6 +72,7 @@ WORKLOADS = {
 
 
 PRED_TRAIN_SEEDS = range(3000, 3004)  # 4 x 128 series x 100 chunks = 51,200 samples
+TARGET_TOL = 1e-8                      # Newton tolerance of the target comparison
 PRED_EVAL_SEED = 4000                  # held out
 
 
@@ -98,6 +99,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-chunk1", action="store_true")
+    ap.add_argument("--no-target", action="store_true",
+                    help="skip the predictor / tol 1e-8 / chunk = 1 FP64 target legs")
     args = ap.parse_args()
     for k, v in WORKLOADS[args.workload].items():
         if getattr(args, k) is None:
@@ -159,11 +162,13 @@ def real_steps(w):
 
 
 def workload_config(args):
-    desc = {"vdp": "van der Pol n=2, mu log-uniform [10,1000], log-spaced steps",
+    span = ("log-spaced steps (6 decades) per series over [0, min(3 mu, "
+            f"{500.0 * (args.N - 1) / 9999.0:g}/mu)]")
+    desc = {"vdp": f"van der Pol n=2, mu log-uniform [10,1000], {span}",
             "vdp_pred": "van der Pol n=2 (held-out seed) with the learned Newton predictor "
-                        "(MLP 103-256-256-200)",
+                        f"(MLP 103-256-256-200), {span}",
             "vdp_user": "van der Pol n=2 as a user model (device source compiled at run time), "
-                        "mu log-uniform [10,1000], log-spaced steps",
+                        f"mu log-uniform [10,1000], {span}",
             "mds_user": f"mass-damper-spring chain, {args.n_unit} units (n={2 * args.n_unit}), "
                         "forcing f_a sin(2 pi t/T) with T linspace [0.01,1] over the series, as a "
                         "user model; uniform steps on [0,1]",
@@ -463,6 +468,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
+    base_inp = {"y0": y0, "times": times, "params": params, "grad": grad, "lengths": lengths}
+
     def make(opts):
         ws = tvi.make_workspace(model, opts, B, N, dev)
         y = torch.empty((B, N + 1, n), dtype=torch.float64, device=dev)
@@ -472,7 +479,8 @@ def run_ours(args):
         dy0 = torch.empty_like(y0)
         return ws, y, stats, st, dp, dy0
 
-    def timed_steps(opts, K, W):
+    def timed_steps(opts, K, W, inp=None):
+        inp = base_inp if inp is None else inp
         ws, y, stats, st, dp, dy0 = make(opts)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
                torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -480,10 +488,12 @@ def run_ours(args):
         def step(e=None):
             if e:
                 e[0].record(stream)
-            tvi.integrate(model, opts, y0, times, params, lengths, y, stats, st, ws, stream)
+            tvi.integrate(model, opts, inp["y0"], inp["times"], inp["params"], inp["lengths"], y,
+                          stats, st, ws, stream)
             if e:
                 e[1].record(stream)
-            tvi.adjoint(model, opts, times, params, y, grad, lengths, dp, dy0, ws, stream)
+            tvi.adjoint(model, opts, inp["times"], inp["params"], y, inp["grad"], inp["lengths"],
+                        dp, dy0, ws, stream)
             if e:
                 e[2].record(stream)
         for _ in range(W):
@@ -510,21 +520,25 @@ def run_ours(args):
         return {"fwd_ms": fwd, "adj_ms": adj, "total_ms": float(np.sum(fwd) + np.sum(adj)),
                 "stats": stats.cpu().numpy(), "t0": t0, "t1": t1, "launches": int(launches)}
 
-    pred_info, pred_opts = None, {}
-    if args.workload == "vdp_pred":
+    def train_predictor(tol):
+        """Learned Newton predictor trained on 51,200 solver chunks of training seeds
+        3000-3003 (chunk 100, FP32 blocks, tol); returns (options, info)."""
         from paper_2310_08649_gb300.predictor import Predictor, PredictorSpec, solver_dataset
         spec = PredictorSpec()
         t_train = time.perf_counter()
         px, pt = solver_dataset(lambda s: workloads.vdp(seed=s, B=args.B, N=args.N),
-                                PRED_TRAIN_SEEDS, spec, tol=args.tol)
+                                PRED_TRAIN_SEEDS, spec, tol=tol)
         predictor = Predictor(spec, seed=0)
         predictor.set_normalisation(px, pt)
         losses = predictor.fit(px, pt, epochs=200, batch=512, lr=1e-3, lr_end=1e-5, seed=1)
         torch.cuda.synchronize()
-        pred_opts = predictor.options()
-        pred_info = {"train_samples": int(px.shape[0]), "epochs": 200,
-                     "train_s": time.perf_counter() - t_train,
-                     "final_loss": losses[-1], "first_epoch_loss": losses[0]}
+        return predictor.options(), {"train_samples": int(px.shape[0]), "epochs": 200,
+                                     "train_s": time.perf_counter() - t_train,
+                                     "final_loss": losses[-1], "first_epoch_loss": losses[0]}
+
+    pred_info, pred_opts = None, {}
+    if args.workload == "vdp_pred":
+        pred_opts, pred_info = train_predictor(args.tol)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -563,8 +577,9 @@ def run_ours(args):
 
     side = torch.cuda.Stream(dev)
     start_ev, grad_ev = torch.cuda.Event(), torch.cuda.Event()
+    h_y = torch.empty(y.shape, dtype=torch.float64).pin_memory()
 
-    def e2e_step():
+    def e2e_step(with_y):
         # dL/dy is read only by the adjoint: it is uploaded on a second stream while the
         # forward pass runs; the adjoint waits for it, so every copy stays in the step
         start_ev.record(stream)
@@ -583,20 +598,26 @@ def run_ours(args):
                     dy0, ws, stream)
         h_dp.copy_(dp, non_blocking=True)
         h_dy0.copy_(dy0, non_blocking=True)
-    for _ in range(min(args.warmup, 3)):
-        e2e_step()
-    torch.cuda.synchronize()
-    K2 = max(1, min(args.steps, 50))
-    e_ms = 0.0
-    for k in range(K2):
-        flush.fill_(k & 0xff)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        e2e_step()
-        b.record(stream)
-        b.synchronize()
-        e_ms += a.elapsed_time(b)
-    e2e_value = units_per_step * K2 / (e_ms / 1e3)
+        if with_y:
+            h_y.copy_(y, non_blocking=True)
+
+    def e2e_time(with_y):
+        for _ in range(min(args.warmup, 3)):
+            e2e_step(with_y)
+        torch.cuda.synchronize()
+        K2 = max(1, min(args.steps, 50))
+        e_ms = 0.0
+        for k in range(K2):
+            flush.fill_(k & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e2e_step(with_y)
+            b.record(stream)
+            b.synchronize()
+            e_ms += a.elapsed_time(b)
+        return units_per_step * K2 / (e_ms / 1e3)
+    e2e_value_y = e2e_time(True)
+    e2e_value = e2e_time(False)
 
     # chunk = 1 sequential FP64 scheme: same library, tolerance and launch strategy
     chunk1 = None
@@ -604,9 +625,15 @@ def run_ours(args):
         o1 = tvi.Options(chunk=1, tol_abs=args.tol, precision="fp64", sync_status=False)
         r1 = timed_steps(o1, args.baseline_steps, 1)
         v1 = units_per_step * args.baseline_steps / (r1["total_ms"] / 1e3)
+        p1 = r1["stats"][:, 0] + r1["stats"][:, 1]
         chunk1 = {"value": v1, "ms_per_step": r1["total_ms"] / args.baseline_steps,
                   "fwd_ms": float(np.mean(r1["fwd_ms"])), "adj_ms": float(np.mean(r1["adj_ms"])),
-                  "chunk": 1, "blocks": "fp64", "ratio": value / v1}
+                  "chunk": 1, "blocks": "fp64", "ratio": value / v1,
+                  "passes_max": int(p1.max()),
+                  "us_per_pass": 1e3 * float(np.mean(r1["fwd_ms"])) / max(int(p1.max()), 1),
+                  "note": "the same fused kernel at chunk 1: one warp per series, one step "
+                          "per Newton pass; us_per_pass = forward time / passes of the "
+                          "slowest series (it sets the kernel's duration)"}
     # the configuration's chunk sweep, same tolerance and blocks (a few steps each)
     sweep = None
     if args.workload == "vdp" and not args.no_chunk1:
@@ -619,6 +646,50 @@ def run_ours(args):
             sweep[str(c)] = {"value": units_per_step * K / (rc_["total_ms"] / 1e3),
                              "fwd_ms": float(np.mean(rc_["fwd_ms"])),
                              "adj_ms": float(np.mean(rc_["adj_ms"]))}
+    # The target configuration: chunked integration with FP32 blocks and the learned
+    # predictor against chunk = 1 FP64, forward + adjoint, both at Newton tolerance
+    # 1e-8, on the held-out seed the predictor never saw; the dy = 0 guess at chunk
+    # 100 and 1000 is timed beside it.
+    target = None
+    if args.workload == "vdp" and not args.no_target:
+        tol_t = TARGET_TOL
+        wt = workloads.vdp(B=B, N=N, seed=PRED_EVAL_SEED + rank)
+        gt = workloads.random_grad_out(2002 + rank, B, N, n)
+        tin = {"y0": d(wt["y0"]), "times": d(wt["times"]), "params": d(wt["params"]),
+               "grad": d(gt), "lengths": None}
+        t_opts, t_info = train_predictor(tol_t)
+        legs = {}
+
+        def leg(name, K, **kw):
+            o = tvi.Options(tol_abs=tol_t, sync_status=False, adjoint_refine=args.refine, **kw)
+            r = timed_steps(o, K, 1, tin)
+            S = r["stats"]
+            passes = S[:, 0] + S[:, 1]
+            legs[name] = {"value": units_per_step * K / (r["total_ms"] / 1e3),
+                          "fwd_ms": float(np.mean(r["fwd_ms"])),
+                          "adj_ms": float(np.mean(r["adj_ms"])), "chunk": kw["chunk"],
+                          "blocks": kw["precision"],
+                          "newton_updates_per_chunk": float(S[:, 0].sum() / max(S[:, 1].sum(), 1)),
+                          "passes_max": int(passes.max()), "steps_timed": K}
+            if kw.get("predictor") is not None:
+                legs[name].update(guesses_used=int(S[:, 4].sum()), fallbacks=int(S[:, 5].sum()))
+        K_t = max(3, min(args.steps, 20))
+        leg("predictor_c100_fp32", K_t, chunk=100, precision="fp32", **t_opts)
+        leg("zero_guess_c100_fp32", K_t, chunk=100, precision="fp32")
+        leg("zero_guess_c1000_fp32", K_t, chunk=1000, precision="fp32")
+        leg("chunk1_fp64", 2, chunk=1, precision="fp64")
+        c1 = legs["chunk1_fp64"]
+        # the kernel's duration is its slowest series': one pass = one residual evaluation
+        c1["us_per_pass"] = 1e3 * c1["fwd_ms"] / max(c1["passes_max"], 1)
+        for v in legs.values():
+            v["ratio_vs_chunk1_fp64"] = v["value"] / c1["value"]
+        target = {"tol_abs": tol_t, "ratio_needed": 20.0,
+                  "workload": "the van der Pol configuration above on held-out seed "
+                              f"{PRED_EVAL_SEED} (the predictor trains on seeds 3000-3003)",
+                  "ratio": legs["predictor_c100_fp32"]["ratio_vs_chunk1_fp64"],
+                  "best_chunked": max((k for k in legs if k != "chunk1_fp64"),
+                                      key=lambda k: legs[k]["value"]),
+                  "legs": legs, "predictor": t_info}
     clocks.stop()
     clk = clocks.summary(res["t0"], res["t1"])
 
@@ -626,6 +697,58 @@ def run_ours(args):
     refine = opts.adjoint_refine if args.precision != "fp64" else 0
     stats_np = res["stats"]
     roof = roofline(args, w, stats_np, fwd_ms, adj_ms, refine)
+
+    def step_and_gradient_checks(w, g, S, yg, ref, lens_s):
+        """Errors that no trajectory conditioning enters, on the oracle's S series:
+        (1) every step of this run's trajectory against the oracle's solve of that
+        step from the run's own previous state; (2) this library's adjoint run on the
+        ORACLE's trajectory (dL/dy zero outside the sample) against the oracle's
+        adjoint there, i.e. both adjoints solving the same linear system."""
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+        om = oracle.Model.from_spec(w["spec"])
+        out = {}
+        one = np.empty_like(yg)
+
+        def solve(b):
+            p = w["params"][b:b + 1] if om.per_series else w["params"]
+            lb = None if lens_s is None else lens_s[b:b + 1]
+            tb = 1e-13 * max(1.0, float(np.abs(yg[b]).max()))
+            one[b:b + 1], st = oracle.step_solves(om, w["times"][b:b + 1], p, yg[b:b + 1],
+                                                  lengths=lb, tol_abs=tb, max_iter=100, nthreads=1)
+            return int(st[0])
+        with ThreadPoolExecutor(max_workers=max(1, oracle.max_threads())) as ex:
+            st_all = list(ex.map(solve, range(S)))
+        out["y_step_max_rel"] = float(np.max(np.abs(yg - one).max(axis=(1, 2)) /
+                                             np.maximum(np.abs(one).max(axis=(1, 2)), 1e-300)))
+        out["y_step_note"] = ("every step against the oracle's solve of that step from this "
+                              "run's own previous state (one step's conditioning only)")
+        if any(st_all):
+            out["y_step_status"] = st_all
+        # both adjoints on the oracle trajectory of the sample
+        y_mix = y.clone()
+        y_mix[:S] = torch.as_tensor(ref["y"], device=dev)
+        g_mix = torch.zeros_like(y_mix)
+        g_mix[:S] = torch.as_tensor(g[:S], device=dev)
+        dp_o, dy0_o = torch.empty_like(params), torch.empty_like(y0)
+        ws_o = tvi.make_workspace(model, opts, B, N, dev)
+        tvi.adjoint(model, opts, times, params, y_mix, g_mix, lengths, dp_o, dy0_o, ws_o, stream)
+        torch.cuda.synchronize()
+        dp_o, dy0_o = dp_o.cpu().numpy(), dy0_o.cpu().numpy()
+        rel = lambda a, b: float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))  # noqa
+        if om.per_series:
+            out["dparams_on_oracle_y_max_rel"] = float(np.max(
+                np.abs(dp_o[:S] - ref["dp"]).max(axis=1) /
+                np.maximum(np.abs(ref["dp"]).max(axis=1), 1e-300)))
+        else:
+            out["dparams_on_oracle_y_max_rel"] = rel(dp_o, ref["dp"])
+        out["dy0_on_oracle_y_max_rel"] = float(np.max(
+            np.abs(dy0_o[:S] - ref["dy0"]).max(axis=1) /
+            np.maximum(np.abs(ref["dy0"]).max(axis=1), 1e-300)))
+        out["gradient_note"] = ("*_on_oracle_y: this library's adjoint at the oracle's "
+                                "trajectory against the oracle's adjoint there (the same "
+                                "linear system), loss on the sampled series only")
+        return out
 
     cpu, accuracy = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -650,6 +773,7 @@ def run_ours(args):
                             "Newton at tol, so the forward difference includes the problem's "
                             "conditioning, and the gradients differ through the trajectories"
                             + ("" if lens_s is None else "; padded series"))
+        accuracy.update(step_and_gradient_checks(w, g, S, yg, ref, lens_s))
 
     if rank == 0:
         upd, nchk = stats_np[:, 0].astype(np.float64), stats_np[:, 1].astype(np.float64)
@@ -669,13 +793,18 @@ def run_ours(args):
                                  "retries_total": int(stats_np[:, 2].sum()),
                                  "retries_max": int(stats_np[:, 2].max()),
                                  "max_updates_one_chunk": int(stats_np[:, 3].max())},
-                "chunk1_fp64": chunk1, "chunk_sweep": sweep, "roofline": roof,
+                "chunk1_fp64": chunk1, "chunk_sweep": sweep, "target": target, "roofline": roof,
                 "cpu_baseline": cpu,
                 "accuracy_vs_oracle": accuracy,
                 "e2e": {"value": e2e_value, "unit": "series*steps/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h,
                         "note": "pinned host buffers; dL/dy upload overlapped with the forward "
-                                "pass on a second stream"},
+                                "pass on a second stream; the step's result (dL/dparams, "
+                                "dL/dy0) is read back, the trajectory y_out stays on the device",
+                        "with_trajectory_d2h": {
+                            "value": e2e_value_y, "d2h_bytes_per_step": d2h + y.numel() * 8,
+                            "note": "the same step with y_out also copied to pinned host "
+                                    "memory inside the timed region"}},
                 "gpu_launches": res["launches"],
                 "gpu_launches_source": "tvi_kernel_launches() delta over the timed steps",
                 "clocks": clk}
