@@ -75,6 +75,15 @@ __device__ __forceinline__ Aff<NS, T> shfl_up_aff(const Aff<NS, T>& f, int s) {
   return o;
 }
 
+// 1/x for the block algebra: the division in FP64, a fast reciprocal (at most 2
+// ulp from the rounded quotient) in FP32, where the blocks only steer Newton
+// updates whose FP64 residual decides convergence.
+template <typename T>
+__device__ __forceinline__ T recip(T x) {
+  if constexpr (sizeof(T) == sizeof(double)) return T(1) / x;
+  else return __fdividef(1.0f, x);
+}
+
 // ---------------------------------------------------------------------------
 // Block inverse: Gauss-Jordan with partial pivoting, fully in registers (row
 // swaps are predicated selects, so no local memory).  NS = 2 uses the closed
@@ -86,7 +95,7 @@ __device__ __forceinline__ void block_inverse(const T (&A)[NS][NS], T (&X)[NS][N
     X[0][0] = T(1) / A[0][0];
   } else if constexpr (NS == 2) {
     T det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
-    T r = T(1) / det;
+    T r = recip<T>(det);
     X[0][0] = A[1][1] * r;
     X[0][1] = -A[0][1] * r;
     X[1][0] = -A[1][0] * r;
@@ -127,7 +136,7 @@ __device__ __forceinline__ void block_inverse(const T (&A)[NS][NS], T (&X)[NS][N
           }
         }
       }
-      T inv = T(1) / W[k][k];
+      T inv = recip<T>(W[k][k]);
 #pragma unroll
       for (int j = 0; j < NS; ++j) {
         W[k][j] *= inv;
@@ -282,21 +291,22 @@ __device__ __forceinline__ void last_row(const double (&v)[RPT][NS], int rpa, do
 // Solve the chain d_j = M_j d_{j-1} + v_j over the block's rows, d_{-1} = 0.
 // Called by the block's first `nwa` warps only; thread t holds its rows in
 // f[0 .. rpa-1] (rpa <= RPT, the same in every thread), and rows past the
-// chunk end must hold the identity map.  On return x[r] = d of each own row
-// r < rpa.  Synchronisation: two barriers over those warps when nwa > 1.
+// chunk end must hold the identity map.  Lanes from `lanes` on (in every warp)
+// must hold identity maps only.  On return x[r] = d of each own row r < rpa.
+// Synchronisation: two barriers over those warps when nwa > 1.
 // ---------------------------------------------------------------------------
 template <int NS, typename T, int RPT>
 __device__ __forceinline__ void solve_chain(const Aff<NS, T> (&f)[RPT], T (&x)[RPT][NS],
                                             Aff<NS, T>* s_wtot, int lane, int warp, int nwa,
-                                            int rpa = RPT) {
+                                            int rpa = RPT, int lanes = 32) {
   // (1) serial composition of the thread's own rows
   Aff<NS, T> seg = f[0];
 #pragma unroll
   for (int r = 1; r < RPT; ++r)
     if (r < rpa) seg = compose(f[r], seg);
-  // (2) cyclic reduction over the lanes of the warp
-#pragma unroll
-  for (int s = 1; s < 32; s <<= 1) {
+  // (2) cyclic reduction over the lanes of the warp; `lanes` (block-uniform) is
+  // how many lanes of a warp hold rows, so a short chunk takes fewer levels
+  for (int s = 1; s < lanes; s <<= 1) {
     Aff<NS, T> o = shfl_up_aff(seg, s);
     if (lane >= s) seg = compose(seg, o);
   }

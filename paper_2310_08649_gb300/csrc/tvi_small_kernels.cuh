@@ -372,7 +372,8 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
           }
         }
       }
-      solve_chain<NS, T, RPT>(f, d, s_wtot, lane, warp, nwa, rpa);
+      solve_chain<NS, T, RPT>(f, d, s_wtot, lane, warp, nwa, rpa,
+                              nwa > 1 ? 32 : (L + rpa - 1) / rpa);
       // ---- Newton update, FP64 accumulate ----
       if (wact) {
 #pragma unroll
