@@ -41,7 +41,11 @@ typedef enum {
   TVI_ECUDA = -3,         /* a CUDA runtime call failed (text in tvi_last_error) */
   TVI_ENOTCONV = -4,      /* some series hit the Newton iteration limit on a one-step chunk */
   TVI_ENONFINITE = -5,    /* some series produced a NaN/Inf residual on a one-step chunk */
-  TVI_ETIMEOUT = -6,      /* a bounded device wait gave up (tensor-core path); results invalid */
+  TVI_ETIMEOUT = -6,      /* a bounded device wait gave up (tensor-core path); results invalid.
+                             Test hook: a non-negative integer in the environment variable
+                             TVI_TEST_TC_FIRST_WAIT_POLLS bounds the first data wait of each
+                             tensor-core block at that many polls (0: gives up at once), read
+                             at every launch; unset, the full limit applies */
   TVI_EUNSUPPORTED = -7   /* model/precision/size combination not built */
 } tvi_status;
 
@@ -106,14 +110,18 @@ typedef struct {
   double tol_rel;     /* ... or ||R||_inf <= tol_rel ||R_0||_inf (norm over the whole chunk) */
   int max_iter;       /* Newton update limit per chunk attempt */
   int precision;      /* tvi_precision */
-  int retry_halving;  /* 1 (linear and van der Pol models): a chunk whose Newton fails
+  int retry_halving;  /* 1: a chunk whose Newton fails is re-solved by halves.  Small-state
+                         engine (linear, van der Pol, user models with n <= 4): a failure
                          (limit, non-finite, or residual still > 10x its start after 4
-                         updates) keeps its longest leading run of >= 8 steps whose
-                         residuals are within the tolerance (those steps are solved), and
-                         the rest is re-solved with half the steps, recursively down to
+                         updates) keeps the attempt's longest leading run of >= 8 steps
+                         whose residuals are within the tolerance (those steps are solved),
+                         and the rest is re-solved with half the steps, recursively down to
                          one step; after two successes in a row the chunk doubles back up
-                         to `chunk`.  Every kept step satisfies the same equation to the
-                         same tolerance.  The MLP models do not halve. */
+                         to `chunk`.  Large-state engines (MLP and user models with n > 4,
+                         all series in lockstep): the series whose attempt hit the limit or
+                         a non-finite residual re-solve the same steps as two halves,
+                         recursively down to one step, while the others go on.  Every kept
+                         step satisfies the same equation to the same tolerance. */
   int adjoint_refine; /* FP64-residual refinement sweeps of each adjoint chunk solve
                          (used when precision != FP64) */
   int rows_per_thread;/* solver tiling: steps held by one thread (0 = automatic) */
@@ -283,8 +291,8 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
  * n <= 4 the fused small-state solver, so they run inlined in the same
  * one-block-per-series kernels as the built-in linear and van der Pol models;
  * for 5 <= n <= 32 the large-state kernels (a thread per (series, step) for the
- * residual, a warp per step for the Jacobian block and its inverse) around the
- * chunk solve of the MLP engine.  `source` defines, at global scope, with
+ * residual, up to a warp per step for the Jacobian block and its inverse) around
+ * the chunk solve of the MLP engine.  `source` defines, at global scope, with
  * TVI_N (= n) and TVI_P (= P) #defined before it:
  *
  *   __device__ void tvi_rhs(const double* y, double t, const double* p, double* h);
@@ -307,11 +315,12 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
  * The library trusts them: J must be the Jacobian of h for Newton to converge
  * quadratically, and g its parameter product for the gradients to be those of
  * the discrete loss.  Sizes 1 <= n <= 32; 1 <= P <= 32 for n <= 4, 1 <= P <= 64
- * above (more than 32 are read from memory, not held in registers); FP64 or FP32 blocks
- * (BF16: TVI_EUNSUPPORTED); per-series or shared parameters; no Newton
- * predictor; both schemes.  n <= 4 also has retry_halving and
- * tvi_adjoint_noalloc; n > 4 needs the workspace of tvi_workspace_bytes, does
- * not halve, and rejects tvi_adjoint_noalloc (TVI_EUNSUPPORTED).  Calls on one model from several host threads are safe.  The paper has no counterpart to
+ * above (more than 32 are read from memory, not held in registers); FP64 or FP32
+ * blocks (BF16: TVI_EUNSUPPORTED); per-series or shared parameters; no Newton
+ * predictor; both schemes; retry_halving.  n <= 4 also has tvi_adjoint_noalloc;
+ * n > 4 needs the workspace of tvi_workspace_bytes and rejects
+ * tvi_adjoint_noalloc (TVI_EUNSUPPORTED).  Calls on one model from several host
+ * threads are safe.  The paper has no counterpart to
  * run-time compilation: it is how an ABI of plain pointers accepts functions.
  */
 

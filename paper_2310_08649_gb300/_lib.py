@@ -16,7 +16,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 SCHEMES = {"backward": 0, "forward": 1}
 STATUS = {0: "TVI_OK", -1: "TVI_EINVAL", -2: "TVI_EWORKSPACE", -3: "TVI_ECUDA",
           -4: "TVI_ENOTCONV", -5: "TVI_ENONFINITE", -6: "TVI_ETIMEOUT", -7: "TVI_EUNSUPPORTED"}
-TVI_ENOTCONV, TVI_ENONFINITE = -4, -5
+TVI_ENOTCONV, TVI_ENONFINITE, TVI_ETIMEOUT = -4, -5, -6
 
 # every symbol include/tvi.h declares
 EXPORTS = ("tvi_default_options", "tvi_param_count", "tvi_workspace_bytes",

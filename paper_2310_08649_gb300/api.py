@@ -167,7 +167,9 @@ def integrate(model, opts, y0, times, params, lengths=None, y_out=None, stats=No
               series_status=None, workspace=None, stream=None, raise_on_status=True):
     """Chunked backward-Euler integration (tvi_integrate).
 
-    Returns (y [B][N+1][n], stats [B][6] int32, series_status [B] int32, rc)."""
+    Returns (y [B][N+1][n], stats [B][6] int32, series_status [B] int32, rc).  With
+    raise_on_status=False the per-series failure codes (TVI_ENOTCONV, TVI_ENONFINITE,
+    TVI_ETIMEOUT) are returned in rc instead of raised."""
     lib = _lib.load()
     B, n = y0.shape
     N = times.shape[1] - 1
@@ -189,7 +191,8 @@ def integrate(model, opts, y0, times, params, lengths=None, y_out=None, stats=No
                            _ptr(times), _ptr(lengths), _ptr(params), _ptr(y_out), _ptr(stats),
                            _ptr(series_status), _ptr(workspace), workspace.numel(),
                            _stream(stream))
-    if rc != 0 and (raise_on_status or rc not in (_lib.TVI_ENOTCONV, _lib.TVI_ENONFINITE)):
+    status_codes = (_lib.TVI_ENOTCONV, _lib.TVI_ENONFINITE, _lib.TVI_ETIMEOUT)
+    if rc != 0 and (raise_on_status or rc not in status_codes):
         raise _lib.TviError(rc, _lib.last_error())
     return y_out, stats, series_status, rc
 

@@ -21,6 +21,12 @@ enum { kSchemeBackward = 0, kSchemeForward = 1 };
 // Largest chunk the fused small-state kernels hold on chip; a larger requested
 // chunk is solved as chunks of this size (same equations, same result).
 constexpr int kSmallMaxChunk = 1024;
+// Host-driven Newton loops (large-state engines): the host reads the number of
+// series still iterating once per this many passes instead of after each one.
+constexpr int kHostCheckEvery = 4;
+// Deepest recursion of chunk halving on those engines (a chunk of up to 2^31
+// steps halves to one step within it).
+constexpr int kHalvingDepth = 32;
 
 // Thread bound of the fused kernels by steps per thread: more steps per thread
 // need more registers, so fewer threads (the block always holds 1024 steps).
@@ -160,6 +166,13 @@ cudaError_t mlp_launch_chain(int precision, const ChainArgs& ch, cudaStream_t s)
 cudaError_t mlp_launch_check(int B, int it, int max_iter, double tol_abs, double tol_rel,
                              unsigned long long* norm, double* norm0, int* active, int* status,
                              int* iters, int* remaining, cudaStream_t s);
+// chunk halving: an attempt's start for the series of `mask` (all when null), and
+// after it the failed ones into `fail` (their status restored, one retry counted)
+cudaError_t mlp_launch_chunk_begin(int B, int rowlen, int c, const int* mask, double* dy,
+                                   int* active, unsigned long long* norm, int* iters,
+                                   const int* status, int* status0, cudaStream_t s);
+cudaError_t mlp_launch_chunk_fail(int B, const int* mask, int* status, const int* status0,
+                                  int* fail, int* nfail, int* stats, cudaStream_t s);
 
 // Large-state user models (tvi_large.cu): n in 5..32, the run-time compiled
 // kernels of tvi_large_kernels.cuh around the pieces above.

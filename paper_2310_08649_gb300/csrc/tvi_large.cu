@@ -12,6 +12,8 @@
 // State vectors are padded to n4 = 4 ceil(n / 4) (the chain's vector width).
 #include <cuda_runtime.h>
 
+#include <functional>
+
 #include "tvi_device.cuh"
 #include "tvi_internal.h"
 
@@ -26,6 +28,7 @@ size_t al(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 struct LWs {
   int *worst, *remaining, *err, *active, *status, *iters;
+  int *status0, *nfail, *fail;  // chunk halving: status before an attempt, failures, masks
   double *yi, *carry, *norm0, *dy, *R, *acc;
   unsigned long long* norm;
   void* M;
@@ -49,6 +52,9 @@ LWs carve(char* base, int n, int P, int B, int c, int precision) {
   w.active = reinterpret_cast<int*>(take(sizeof(int) * B));
   w.status = reinterpret_cast<int*>(take(sizeof(int) * B));
   w.iters = reinterpret_cast<int*>(take(sizeof(int) * B));
+  w.status0 = reinterpret_cast<int*>(take(sizeof(int) * B));
+  w.nfail = reinterpret_cast<int*>(take(sizeof(int)));
+  w.fail = reinterpret_cast<int*>(take(sizeof(int) * B * kHalvingDepth));
   w.norm = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * B));
   w.norm0 = reinterpret_cast<double*>(take(sizeof(double) * B));
   w.yi = reinterpret_cast<double*>(take(sizeof(double) * B * n4));
@@ -73,24 +79,15 @@ __global__ void large_start_kernel(int B, int n, int n4, int Np1, const double* 
   if (i < B) status[i] = 0;
 }
 
-__global__ void large_chunk_init_kernel(int B, int n4, int c, double* dy, int* active,
-                                        unsigned long long* norm, int* iters) {
-  const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < static_cast<size_t>(B) * c * n4) dy[i] = 0.0;  // Sec. 2.3 guess dy = 0
-  if (i < static_cast<size_t>(B)) {
-    active[i] = 1;
-    norm[i] = 0ull;
-    iters[i] = 0;
-  }
-}
-
 // y_{i0+1..i0+L} = y_i + dy; carry y_{i0+L}; one block per series.  Padded
 // steps (k > length) keep the last real state exactly (reading C-14), whatever
 // rounding Newton left in their identity rows.
 __global__ void large_store_kernel(int n, int n4, int L, int c, int N, int i0, const int* lengths,
                                    const double* dy, double* yi, double* y_out, const int* iters,
-                                   int* stats) {
+                                   int* stats, const int* mask, const int* fail) {
   const int b = blockIdx.x;
+  // only the attempt's series (mask), and not those re-solving it by halves
+  if ((mask && !mask[b]) || (fail && fail[b])) return;
   const int len = lengths ? min(max(lengths[b], 0), N) : N;
   const int jl = min(L, max(len - i0, 0)) - 1;  // last real row of the chunk, -1 if none
   const double* dyb = dy + static_cast<size_t>(b) * c * n4;
@@ -206,12 +203,14 @@ cudaError_t large_forward(const LargeKernels& k, int n, int P, int precision, co
       B, n, n4, N + 1, a.y0, a.y_out, w.yi, w.status);
   TVI_TRY(cudaGetLastError());
   if (a.stats) TVI_TRY(cudaMemsetAsync(a.stats, 0, sizeof(int) * kStats * B, s));
-  for (int i0 = 0; i0 < N; i0 += c) {
-    const int L = (N - i0 < c) ? N - i0 : c;
-    note_launch();
-    large_chunk_init_kernel<<<blocks_for(static_cast<size_t>(B) * c * n4, 256), 256, 0, s>>>(
-        B, n4, c, w.dy, w.active, w.norm, w.iters);
-    TVI_TRY(cudaGetLastError());
+  // One attempt over steps i0 + 1 .. i0 + L for the series in `mask` (all when
+  // null); with retry_halving the series whose attempt failed re-solve the same
+  // steps as two halves, recursively down to one step (as in the MLP engine).
+  std::function<cudaError_t(int, int, const int*, int)> solve =
+      [&](int i0, int L, const int* mask, int depth) -> cudaError_t {
+    const bool halve = a.retry_halving && L > 1 && depth < kHalvingDepth;
+    TVI_TRY(mlp_launch_chunk_begin(B, n4, c, mask, w.dy, w.active, w.norm, w.iters, w.status,
+                                   w.status0, s));
     LargeArgs la{};
     la.B = B; la.N = N; la.i0 = i0; la.L = L; la.c = c; la.n4 = n4;
     la.per_series = a.per_series; la.reverse = 0; la.fwd_euler = a.scheme == kSchemeForward;
@@ -223,10 +222,15 @@ cudaError_t large_forward(const LargeKernels& k, int n, int P, int precision, co
       TVI_TRY(cudaMemsetAsync(w.remaining, 0, sizeof(int), s));
       TVI_TRY(mlp_launch_check(B, it, a.max_iter, a.tol_abs, a.tol_rel, w.norm, w.norm0, w.active,
                                w.status, w.iters, w.remaining, s));
-      int remaining = 0;
-      TVI_TRY(cudaMemcpyAsync(&remaining, w.remaining, sizeof(int), cudaMemcpyDeviceToHost, s));
-      TVI_TRY(cudaStreamSynchronize(s));
-      if (remaining == 0) break;
+      // the host reads how many series still iterate only every kHostCheckEvery
+      // passes (and at the iteration limit, where the check stops every series);
+      // passes enqueued after the last series stopped find none active and return
+      if ((it + 1) % kHostCheckEvery == 0 || it >= a.max_iter) {
+        int remaining = 0;
+        TVI_TRY(cudaMemcpyAsync(&remaining, w.remaining, sizeof(int), cudaMemcpyDeviceToHost, s));
+        TVI_TRY(cudaStreamSynchronize(s));
+        if (remaining == 0) break;
+      }
       TVI_TRY(launch_user(k.block, block_grid(L, B, n4), la, s));
       ChainArgs ch{};
       ch.B = B; ch.n = n4; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 0; ch.M = w.M;
@@ -234,11 +238,25 @@ cudaError_t large_forward(const LargeKernels& k, int n, int P, int precision, co
       ch.post_add = la.fwd_euler;  // forward Euler: d_j = (I + dt J) d_{j-1} + R_j
       TVI_TRY(mlp_launch_chain(precision, ch, s));
     }
+    int* fail = halve ? w.fail + static_cast<size_t>(depth) * B : nullptr;
+    int nfail = 0;
+    if (halve) {
+      TVI_TRY(mlp_launch_chunk_fail(B, mask, w.status, w.status0, fail, w.nfail, a.stats, s));
+      TVI_TRY(cudaMemcpyAsync(&nfail, w.nfail, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TVI_TRY(cudaStreamSynchronize(s));
+    }
     note_launch();
     large_store_kernel<<<B, 128, 0, s>>>(n, n4, L, c, N, i0, a.lengths, w.dy, w.yi, a.y_out,
-                                         w.iters, a.stats);
+                                         w.iters, a.stats, mask, fail);
     TVI_TRY(cudaGetLastError());
-  }
+    if (nfail > 0) {
+      const int L1 = (L + 1) / 2;
+      TVI_TRY(solve(i0, L1, fail, depth + 1));
+      TVI_TRY(solve(i0 + L1, L - L1, fail, depth + 1));
+    }
+    return cudaSuccess;
+  };
+  for (int i0 = 0; i0 < N; i0 += c) TVI_TRY(solve(i0, (N - i0 < c) ? N - i0 : c, nullptr, 0));
   note_launch();
   large_worst_kernel<<<blocks_for(B, 128), 128, 0, s>>>(B, w.status, w.err, a.series_status,
                                                         w.worst);

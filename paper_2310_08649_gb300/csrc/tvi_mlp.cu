@@ -26,6 +26,8 @@
 // With FP64 blocks every MLP pass is FP64; with FP32 / BF16 blocks the
 // adjoint's MLP passes run in FP32 (64x the FP64 rate on this part), which
 // bounds the gradient's relative error near 1e-7 instead of 1e-15.
+#include <cstdlib>
+#include <functional>
 #include <cuda_runtime.h>
 
 #include "tvi_device.cuh"
@@ -365,6 +367,7 @@ struct BlocksArgs {
   const double* dv;   // [B][c][h1+h2+n]
   const int* active;  // [B] or null
   void* M;            // [B][c][n][n] in T
+  int first_wait_polls;  // tensor-core kernel: poll limit of each block's first data wait
 };
 
 // weight i of the flat parameter vector in the block precision
@@ -701,7 +704,8 @@ __global__ void __launch_bounds__(kTcThreads) mlp_blocks_tc_kernel(BlocksArgs a,
     if (tid < TP)
       s_dt[tid] = tid < np ? narrow<float>(step_dt(tb, len, step_of(a.reverse, a.i0, a.L, j0 + tid)))
                            : 0.0f;
-    if (tc::mbar_wait_bounded(&s_dvbar[buf], (dvphase >> buf) & 1u, kTcWaitLimit))
+    if (tc::mbar_wait_bounded(&s_dvbar[buf], (dvphase >> buf) & 1u,
+                              tile == first ? a.first_wait_polls : kTcWaitLimit))
       outst &= ~(1u << buf);
     else
       s_stop = 1;
@@ -1297,14 +1301,35 @@ __global__ void mlp_start_kernel(int B, int n, int Np1, const double* y0, double
   if (i < B) status[i] = 0;
 }
 
-__global__ void mlp_chunk_init_kernel(int B, int n, int c, double* dy, int* active,
-                                      unsigned long long* norm, int* iters) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < B * c * n) dy[i] = 0.0;  // Sec. 2.3 guess dy = 0
-  if (i < B) {
-    active[i] = 1;
+// Start of a chunk attempt for the series in `mask` (every series when null):
+// dy = 0 (the Sec. 2.3 guess), the series active, its status remembered so that
+// a failure of this attempt can be told apart from an earlier one.
+__global__ void chunk_begin_kernel(int B, int rowlen, int c, const int* mask, double* dy,
+                                   int* active, unsigned long long* norm, int* iters,
+                                   const int* status, int* status0) {
+  const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < static_cast<size_t>(B) * c * rowlen) dy[i] = 0.0;
+  if (i < static_cast<size_t>(B)) {
+    active[i] = mask ? mask[i] : 1;
     norm[i] = 0ull;
     iters[i] = 0;
+    status0[i] = status[i];
+  }
+}
+
+// After an attempt that may be halved: the series of `mask` whose attempt failed
+// (status set by it) go into `fail`, get their earlier status back (the halves
+// re-solve the same steps) and count one retry; *nfail counts them.
+__global__ void chunk_fail_kernel(int B, const int* mask, int* status, const int* status0,
+                                  int* fail, int* nfail, int* stats) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const bool failed = (!mask || mask[b]) && status[b] != status0[b];
+  fail[b] = failed ? 1 : 0;
+  if (failed) {
+    status[b] = status0[b];
+    atomicAdd(nfail, 1);
+    if (stats) stats[b * kStats + 2] += 1;
   }
 }
 
@@ -1313,8 +1338,10 @@ __global__ void mlp_chunk_init_kernel(int B, int n, int c, double* dy, int* acti
 // whatever rounding Newton left in their identity rows.
 __global__ void mlp_store_kernel(int n, int L, int c, int N, int i0, const int* lengths,
                                  const double* dy, double* yi, double* y_out, const int* iters,
-                                 int* stats) {
+                                 int* stats, const int* mask, const int* fail) {
   const int b = blockIdx.x;
+  // only the attempt's series (mask), and not those re-solving it by halves
+  if ((mask && !mask[b]) || (fail && fail[b])) return;
   const int len = lengths ? min(max(lengths[b], 0), N) : N;
   const int jl = min(L, max(len - i0, 0)) - 1;  // last real row of the chunk, -1 if none
   const double* dyb = dy + static_cast<size_t>(b) * c * n;
@@ -1375,6 +1402,7 @@ struct Ws {
   void* M;
   unsigned long long* norm;
   int *active, *status, *iters, *remaining, *worst, *tcerr;
+  int *status0, *nfail, *fail;  // chunk halving: status before an attempt, failures, masks
   size_t total;
 };
 
@@ -1399,6 +1427,9 @@ Ws carve(char* base, int B, int c, const MlpDims& d, int precision, bool adjoint
   w.active = reinterpret_cast<int*>(take(sizeof(int) * B));
   w.status = reinterpret_cast<int*>(take(sizeof(int) * B));
   w.iters = reinterpret_cast<int*>(take(sizeof(int) * B));
+  w.status0 = reinterpret_cast<int*>(take(sizeof(int) * B));
+  w.nfail = reinterpret_cast<int*>(take(sizeof(int)));
+  w.fail = reinterpret_cast<int*>(take(sizeof(int) * B * kHalvingDepth));
   w.dy = reinterpret_cast<double*>(take(sizeof(double) * bc * d.n));
   w.R = reinterpret_cast<double*>(take(sizeof(double) * bc * d.n));
   w.dv = reinterpret_cast<double*>(take(sizeof(double) * bc * (d.h1 + d.h2 + d.n)));
@@ -1509,7 +1540,23 @@ cudaError_t launch_blocks(const BlocksArgs& bk, int precision, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_blocks_tc(const BlocksArgs& bk, int* err, cudaStream_t s) {
+// Poll limit of the first derivative-copy wait of each tensor-core block: the
+// full limit, unless the environment variable TVI_TEST_TC_FIRST_WAIT_POLLS sets
+// another (a test hook: 0 makes that wait give up at once, so the timeout path --
+// error flag, drain of the copies in flight, tensor memory freed -- runs without
+// any fault).
+int tc_first_wait_polls() {
+  const char* v = std::getenv("TVI_TEST_TC_FIRST_WAIT_POLLS");
+  if (!v || !*v) return kTcWaitLimit;
+  char* end = nullptr;
+  const long x = std::strtol(v, &end, 10);
+  if (end == v || x < 0 || x > kTcWaitLimit) return kTcWaitLimit;
+  return static_cast<int>(x);
+}
+
+cudaError_t launch_blocks_tc(const BlocksArgs& bk_in, int* err, cudaStream_t s) {
+  BlocksArgs bk = bk_in;
+  bk.first_wait_polls = tc_first_wait_polls();
   const TcLayout Lo = tc_layout(bk.d);
   const size_t sm = Lo.total < kTcMinSmem ? kTcMinSmem : Lo.total;
   cudaError_t e = bk.d.n == 16 ? set_smem(mlp_blocks_tc_kernel<16>, sm)
@@ -1812,6 +1859,24 @@ cudaError_t mlp_launch_check(int B, int it, int max_iter, double tol_abs, double
   return cudaGetLastError();
 }
 
+cudaError_t mlp_launch_chunk_begin(int B, int rowlen, int c, const int* mask, double* dy,
+                                   int* active, unsigned long long* norm, int* iters,
+                                   const int* status, int* status0, cudaStream_t s) {
+  note_launch();
+  chunk_begin_kernel<<<(static_cast<unsigned>(B) * c * rowlen + 255) / 256, 256, 0, s>>>(
+      B, rowlen, c, mask, dy, active, norm, iters, status, status0);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_launch_chunk_fail(int B, const int* mask, int* status, const int* status0,
+                                  int* fail, int* nfail, int* stats, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(nfail, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  chunk_fail_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, mask, status, status0, fail, nfail, stats);
+  return cudaGetLastError();
+}
+
 bool mlp_supported(int n, int h1, int h2) {
   const bool n_ok = n == 4 || n == 8 || n == 16 || n == 32;  // index math uses shifts
   return n_ok && h1 >= 4 && h1 <= 128 && h1 % 4 == 0 && h2 >= 4 && h2 <= 128 && h2 % 4 == 0;
@@ -1844,12 +1909,16 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
   mlp_start_kernel<<<(B * n + 255) / 256, 256, 0, s>>>(B, n, N + 1, a.y0, a.y_out, w.yi, w.status);
   TVI_TRY(cudaGetLastError());
   if (a.stats) TVI_TRY(cudaMemsetAsync(a.stats, 0, sizeof(int) * kStats * B, s));
-  for (int i0 = 0; i0 < N; i0 += c) {
-    const int L = (N - i0 < c) ? N - i0 : c;
-    note_launch();
-    mlp_chunk_init_kernel<<<(B * c * n + 255) / 256, 256, 0, s>>>(B, n, c, w.dy, w.active, w.norm,
-                                                                   w.iters);
-    TVI_TRY(cudaGetLastError());
+  // One attempt over steps i0 + 1 .. i0 + L for the series in `mask` (all when
+  // null).  With retry_halving, the series whose attempt failed (iteration limit
+  // or non-finite residual) re-solve the same steps as two halves, recursively
+  // down to one step (the same equations to the same tolerance: only where
+  // Newton starts changes); a one-step failure sets the series' status.
+  std::function<cudaError_t(int, int, const int*, int)> solve =
+      [&](int i0, int L, const int* mask, int depth) -> cudaError_t {
+    const bool halve = a.retry_halving && L > 1 && depth < kHalvingDepth;
+    TVI_TRY(mlp_launch_chunk_begin(B, n, c, mask, w.dy, w.active, w.norm, w.iters, w.status,
+                                   w.status0, s));
     for (int it = 0;; ++it) {
       ResidualArgs r{};
       r.d = d; r.B = B; r.N = N; r.i0 = i0; r.L = L; r.c = c; r.reverse = 0;
@@ -1862,10 +1931,15 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
       note_launch();
       mlp_check_kernel<<<(B + 127) / 128, 128, 0, s>>>(ck);
       TVI_TRY(cudaGetLastError());
-      int remaining = 0;
-      TVI_TRY(cudaMemcpyAsync(&remaining, w.remaining, sizeof(int), cudaMemcpyDeviceToHost, s));
-      TVI_TRY(cudaStreamSynchronize(s));
-      if (remaining == 0) break;
+      // the host reads how many series still iterate only every kHostCheckEvery
+      // passes (and at the iteration limit, where the check stops every series);
+      // passes enqueued after the last series stopped find none active and return
+      if ((it + 1) % kHostCheckEvery == 0 || it >= a.max_iter) {
+        int remaining = 0;
+        TVI_TRY(cudaMemcpyAsync(&remaining, w.remaining, sizeof(int), cudaMemcpyDeviceToHost, s));
+        TVI_TRY(cudaStreamSynchronize(s));
+        if (remaining == 0) break;
+      }
       BlocksArgs bk{};
       bk.d = d; bk.B = B; bk.N = N; bk.i0 = i0; bk.L = L; bk.c = c; bk.reverse = 0;
       bk.times = a.times; bk.lengths = a.lengths; bk.Wf = w.Wf; bk.Wd = a.params; bk.dv = w.dv;
@@ -1876,11 +1950,25 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
       TVI_TRY(launch_blocks_any(bk, precision, w.tcerr, s));
       TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s));
     }
+    int* fail = halve ? w.fail + static_cast<size_t>(depth) * B : nullptr;
+    int nfail = 0;
+    if (halve) {
+      TVI_TRY(mlp_launch_chunk_fail(B, mask, w.status, w.status0, fail, w.nfail, a.stats, s));
+      TVI_TRY(cudaMemcpyAsync(&nfail, w.nfail, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TVI_TRY(cudaStreamSynchronize(s));
+    }
     note_launch();
     mlp_store_kernel<<<B, 128, 0, s>>>(n, L, c, N, i0, a.lengths, w.dy, w.yi, a.y_out, w.iters,
-                                       a.stats);
+                                       a.stats, mask, fail);
     TVI_TRY(cudaGetLastError());
-  }
+    if (nfail > 0) {
+      const int L1 = (L + 1) / 2;
+      TVI_TRY(solve(i0, L1, fail, depth + 1));
+      TVI_TRY(solve(i0 + L1, L - L1, fail, depth + 1));
+    }
+    return cudaSuccess;
+  };
+  for (int i0 = 0; i0 < N; i0 += c) TVI_TRY(solve(i0, (N - i0 < c) ? N - i0 : c, nullptr, 0));
   note_launch();
   mlp_worst_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, w.status, w.tcerr, a.series_status, w.worst);
   TVI_TRY(cudaGetLastError());

@@ -146,6 +146,57 @@ def test_mlp_status_and_rejections(tvi):
                       dev(bad["times"]), dev(bad["params"]))
 
 
+def test_mlp_chunk_halving(tvi, oracle_lib):
+    """A stiff network (weights x3, 240 steps on [0, 5]) whose 240-step chunk Newton
+    cannot solve within 12 updates: without halving the series report the
+    iteration limit; with it the failed series re-solve the chunk by halves until
+    Newton converges, and the trajectory is the oracle's (same equations, same
+    tolerance), every step checked on its own."""
+    import paper_2310_08649_gb300._lib as L
+    w = workloads.mlp_ode(B=3, N=240, n=4, hidden=(8, 12), t_end=5.0, seed=61)
+    w["params"] = w["params"] * 3.0
+    m = OModel.from_spec(w["spec"])
+    ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], tol_abs=1e-12,
+                                    max_iter=60)
+    assert not st.any()
+    tm = tvi.Model.from_spec(w["spec"])
+    args = (dev(w["y0"]), dev(w["times"]), dev(w["params"]))
+    o = tvi.Options(chunk=240, tol_abs=1e-12, precision="fp64", max_iter=12, retry_halving=False)
+    _, _, status, rc = tvi.integrate(tm, o, *args, raise_on_status=False)
+    assert rc == L.TVI_ENOTCONV and status.cpu().numpy().all()
+    o = tvi.Options(chunk=240, tol_abs=1e-12, precision="fp64", max_iter=12)
+    y, stats, status, rc = tvi.integrate(tm, o, *args, raise_on_status=False)
+    torch.cuda.synchronize()
+    y, stats = y.cpu().numpy(), stats.cpu().numpy()
+    assert rc == 0 and not status.cpu().numpy().any()
+    assert stats[:, 2].min() >= 1  # every series halved at least once
+    est = oracle_lib.forward_error_estimate(m, w["times"], w["params"], ref, 1e-12)
+    assert np.all(relerr_series(y, ref) <= np.maximum(GATE["fp64"], 10.0 * est))
+    assert be_step_errors(oracle_lib, m, w, y).max() <= STEP_GATE
+
+
+def test_tc_wait_timeout_reports_status(tvi, monkeypatch):
+    """The tensor-core block kernel bounds every mbarrier wait.  With the test hook
+    TVI_TEST_TC_FIRST_WAIT_POLLS = 0 the first data wait of every block gives up at
+    once (the bulk copy it waits for is still in flight, and is drained before the
+    block frees its tensor memory and exits): the forward pass returns TVI_ETIMEOUT
+    with status 3 for every series, the adjoint NaN gradients, and the context
+    stays usable -- the same calls without the hook succeed afterwards."""
+    import paper_2310_08649_gb300._lib as L
+    w = workloads.mlp_ode(B=4, N=60, n=16, hidden=(64, 64), seed=67)
+    g = workloads.random_grad_out(68, 4, 60, 16)
+    monkeypatch.setenv("TVI_TEST_TC_FIRST_WAIT_POLLS", "0")
+    y, _, status, rc = gpu_forward(tvi, w, 20, "bf16", 1e-10)
+    assert rc == L.TVI_ETIMEOUT == -6 and np.all(status == 3), (rc, status)
+    dp, dy0 = gpu_adjoint(tvi, w, 20, "bf16", np.zeros((4, 61, 16)), g)
+    assert np.all(np.isnan(dp)) and np.all(np.isnan(dy0))
+    monkeypatch.delenv("TVI_TEST_TC_FIRST_WAIT_POLLS")
+    y, _, status, rc = gpu_forward(tvi, w, 20, "bf16", 1e-10)
+    assert rc == 0 and not status.any()
+    dp, dy0 = gpu_adjoint(tvi, w, 20, "bf16", y, g)
+    assert np.all(np.isfinite(dp)) and np.all(np.isfinite(dy0))
+
+
 # ---------------------------------------------------------------------------
 # BF16 block products on the tensor cores (n >= 16)
 # ---------------------------------------------------------------------------

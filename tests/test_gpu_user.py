@@ -378,6 +378,34 @@ def test_user_large_forward_euler(tvi, users, oracle_lib, precision, which, chun
     assert relerr(dy0, dy0_ref) <= GATE[precision]
 
 
+def test_user_large_chunk_halving(tvi, oracle_lib):
+    """A stiff run-time compiled model on the large-state route (tanh MLP, n = 5,
+    weights x5, 240 steps on [0, 12]) whose 240-step chunk needs more than 8 Newton
+    updates: without halving the series report the iteration limit; with it they
+    re-solve the chunk by halves and match the oracle, every step checked on its
+    own."""
+    import paper_2310_08649_gb300._lib as L
+    w = workloads.mlp_ode(B=3, N=240, n=5, hidden=(3, 3), t_end=12.0, seed=62)
+    w["params"] = w["params"] * 5.0
+    m = OModel.from_spec(w["spec"])
+    ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], tol_abs=1e-12,
+                                    max_iter=60)
+    assert not st.any()
+    user = tvi.UserModel(5, mlp_param_count(5, 3, 3), mlp_tanh(3, 3))
+    model = user.model(per_series=False)
+    o = tvi.Options(chunk=240, tol_abs=1e-12, precision="fp64", max_iter=8, retry_halving=False)
+    _, _, status, rc = forward(tvi, model, w, o)
+    assert rc == L.TVI_ENOTCONV and status.all()
+    o = tvi.Options(chunk=240, tol_abs=1e-12, precision="fp64", max_iter=8)
+    y, stats, status, rc = forward(tvi, model, w, o)
+    assert rc == 0 and not status.any()
+    assert stats[:, 2].min() >= 1  # every series halved at least once
+    est = oracle_lib.forward_error_estimate(m, w["times"], w["params"], ref, 1e-12)
+    assert np.all(relerr_series(y, ref) <= np.maximum(GATE["fp64"], 10.0 * est))
+    assert be_step_errors(oracle_lib, m, w, y).max() <= STEP_GATE
+    user.close()
+
+
 def test_user_padded_lengths_and_noalloc(tvi, users, oracle_lib):
     import paper_2310_08649_gb300._lib as L
     w = workloads.vdp(B=4, N=700, seed=66)
