@@ -61,8 +61,8 @@ WORKLOADS = {
     "chaboche_user": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 50, "N": 2000,
                       "refine": 2},
     # coupled neurons of the paper's timing study (--n-unit neurons, 50 series, 2000
-    # steps on [0, 10]) as a user model; two neurons (n = 8) by default, up to four
-    # (n = 16, 61 parameters) within the 64-parameter bound of the large-state route
+    # steps on [0, 10]) as a user model; two neurons (n = 8) by default, up to the
+    # study's ten (n = 40, 151 parameters)
     "neuron_user": {"chunk": 1000, "precision": "fp32", "tol": 1e-10, "B": 50, "N": 2000,
                     "refine": 2},
     "node16": {"chunk": 200, "precision": "bf16", "tol": 1e-8, "B": 64, "N": 2000, "refine": 2},

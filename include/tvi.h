@@ -290,7 +290,7 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
  * compiled at run time (NVRTC, sm_103a) together with kernel templates: for
  * n <= 4 the fused small-state solver, so they run inlined in the same
  * one-block-per-series kernels as the built-in linear and van der Pol models;
- * for 5 <= n <= 32 the large-state kernels (a thread per (series, step) for the
+ * for 5 <= n <= 40 the large-state kernels (a thread per (series, step) for the
  * residual, up to a warp per step for the Jacobian block and its inverse) around
  * the chunk solve of the MLP engine.  `source` defines, at global scope, with
  * TVI_N (= n) and TVI_P (= P) #defined before it:
@@ -314,7 +314,7 @@ tvi_status tvi_predictor_train_step(float* packed, float* adam_m, float* adam_v,
  * built-in models); a plain FP64 tvi_jac is evaluated in FP64 and rounded.
  * The library trusts them: J must be the Jacobian of h for Newton to converge
  * quadratically, and g its parameter product for the gradients to be those of
- * the discrete loss.  Sizes 1 <= n <= 32; 1 <= P <= 32 for n <= 4, 1 <= P <= 64
+ * the discrete loss.  Sizes 1 <= n <= 40; 1 <= P <= 32 for n <= 4, 1 <= P <= 160
  * above (more than 32 are read from memory, not held in registers); FP64 or FP32
  * blocks (BF16: TVI_EUNSUPPORTED); per-series or shared parameters; no Newton
  * predictor; both schemes; retry_halving.  n <= 4 also has tvi_adjoint_noalloc;

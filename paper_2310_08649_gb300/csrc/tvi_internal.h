@@ -127,9 +127,9 @@ cudaError_t small_sum_partials(const AdjArgs& a, int P, cudaStream_t s);
 // (the compiler log for kJitCompile) in *err.
 enum { kJitOk = 0, kJitNoNvrtc = 1, kJitCompile = 2, kJitCuda = 3 };
 constexpr int kUserSmallMaxN = 4;  // fused one-block-per-series kernels up to here
-constexpr int kUserMaxN = 32;      // large-state kernels above
+constexpr int kUserMaxN = 40;       // large-state kernels above (blocks of up to 40 x 40)
 constexpr int kUserMaxP = 32;       // parameters of fused-kernel models (held in registers)
-constexpr int kUserMaxPLarge = 64;  // parameters of large-state models (read from memory
+constexpr int kUserMaxPLarge = 160; // parameters of large-state models (read from memory
                                     // above 32)
 bool user_valid(const tvi_user_model* m);
 int user_n(const tvi_user_model* m);

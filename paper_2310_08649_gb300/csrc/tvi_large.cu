@@ -1,4 +1,4 @@
-// tvi_large.cu -- host side of user models with 4 < n <= 32 (the large-state
+// tvi_large.cu -- host side of user models with 4 < n <= 40 (the large-state
 // route): workspace, the model-independent kernels, and the Newton and adjoint
 // loops around the run-time compiled kernels of tvi_large_kernels.cuh.
 //
@@ -169,7 +169,8 @@ cudaError_t launch_user(const void* kernel, dim3 grid, const LargeArgs& a, cudaS
 }
 
 // the block kernel: four warps per block, each forming 32 / SEG blocks (SEG the
-// lanes of one block: 8, 16 or 32 for n4 up to 8, 16, 32)
+// lanes of one block: 8, 16 or 32 for n4 up to 8, 16, 32; above, one block per warp
+// with two rows a lane)
 dim3 block_grid(int L, int B, int n4) {
   const int per_warp = n4 <= 8 ? 4 : (n4 <= 16 ? 2 : 1);
   const int per_block = 4 * per_warp;

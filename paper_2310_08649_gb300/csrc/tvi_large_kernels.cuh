@@ -1,5 +1,5 @@
 // tvi_large_kernels.cuh -- the model-dependent kernels of user models with
-// 4 < n <= 32, compiled at run time together with the user's functions.
+// 4 < n <= 40, compiled at run time together with the user's functions.
 //
 // Above n = 4 a step's n x n block no longer fits one thread's registers, so
 // these models take the large-state route of the MLP engine: every (series,
@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(kLargeThreads) large_residual_kernel(LargeArgs
   if ((threadIdx.x & 31) == 0 && mx) atomicMax(a.norm + b, mx);
 }
 
-// lanes that form one block: a power of two >= N4 (a warp holds 32 / SEG blocks)
+// lanes that form one block: a power of two >= N4 up to a warp (a warp holds
+// 32 / SEG blocks); wider blocks give each lane RPL = ceil(N4 / 32) rows
 template <int N4>
 constexpr int block_lanes() {
   return N4 <= 8 ? 8 : (N4 <= 16 ? 16 : 32);
@@ -111,7 +112,11 @@ __global__ void __launch_bounds__(128) large_block_kernel(LargeArgs a) {
   constexpr int SEG = block_lanes<N4>();
   constexpr int G = 32 / SEG;   // blocks per warp
   constexpr int LD = N4 + 1;    // padded row stride of the staging buffer
-  __shared__ T s_buf[4][G][N4 * LD];
+  // blocks wider than a warp stage J in their own output slot (global memory)
+  // and store the result from registers: a shared buffer per warp would exceed
+  // the static shared memory of four warps
+  constexpr bool kWide = N4 > 32;
+  __shared__ T s_buf[4][G][kWide ? 1 : N4 * LD];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / SEG, lg = lane - grp * SEG;
   const int b = blockIdx.y;
@@ -121,7 +126,8 @@ __global__ void __launch_bounds__(128) large_block_kernel(LargeArgs a) {
   const int j = jw + grp;
   const bool live = j < a.L;
   const int jc = live ? j : jw;  // a valid row for the index arithmetic
-  T* buf = s_buf[warp][grp];
+  T* slot = static_cast<T*>(a.J) + (static_cast<size_t>(b) * a.c + jc) * N4 * N4;
+  T* buf = kWide ? slot : s_buf[warp][grp];
   const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
   const int k = step_index(a.reverse, a.i0, a.L, jc);
   // forward Euler couples a_k to a_{k+1} through step k+1 in the adjoint
@@ -148,7 +154,32 @@ __global__ void __launch_bounds__(128) large_block_kernel(LargeArgs a) {
     mdl.template jacobian<T>(y, prev ? tb[k - 1] : tb[k], buf);  // J, NS x NS row-major
   }
   __syncwarp();
-  T* slot = static_cast<T*>(a.J) + (static_cast<size_t>(b) * a.c + j) * N4 * N4;
+  if (a.fwd_euler && kWide) {
+    // lane lg holds rows rr = lg + 32 u of B = I + dt J; every lane reads J before
+    // any lane overwrites the slot
+    T Bv[(N4 + 31) / 32][N4];
+#pragma unroll
+    for (int u = 0; u < (N4 + 31) / 32; ++u) {
+      const int rr = lg + 32 * u;
+#pragma unroll
+      for (int q = 0; q < N4; ++q) {
+        const T Jv = (rr < NS && q < NS) ? buf[rr * NS + q] : T(0);
+        Bv[u][q] = fma(dt, Jv, rr == q ? T(1) : T(0));
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < (N4 + 31) / 32; ++u) {
+      const int rr = lg + 32 * u;
+      if (rr < N4)
+#pragma unroll
+        for (int q = 0; q < N4; ++q) {
+          if (a.reverse) slot[rr * N4 + q] = Bv[u][q];
+          else slot[q * N4 + rr] = Bv[u][q];
+        }
+    }
+    return;
+  }
   if (a.fwd_euler) {
     // no inverse: the block is B = I + dt J (forward, stored transposed as the chain
     // reads it) or B^T (adjoint), slot[r][q] = B[q][r] or B[r][q]
@@ -162,22 +193,38 @@ __global__ void __launch_bounds__(128) large_block_kernel(LargeArgs a) {
     }
     return;
   }
-  T row[2 * N4];
+  // lane lg keeps rows lg + SEG * u (u < RPL) of [A | I]
+  constexpr int RPL = (N4 + SEG - 1) / SEG;
+  T row[RPL][2 * N4];
+  bool used[RPL];
+  int myk[RPL];
 #pragma unroll
-  for (int q = 0; q < N4; ++q) {
-    const T Jv = (live && lg < NS && q < NS) ? buf[lg * NS + q] : T(0);
-    row[q] = lg < N4 ? fma(-dt, Jv, lg == q ? T(1) : T(0)) : T(0);
-    row[N4 + q] = lg == q ? T(1) : T(0);
+  for (int u = 0; u < RPL; ++u) {
+    const int rr = lg + SEG * u;
+#pragma unroll
+    for (int q = 0; q < N4; ++q) {
+      const T Jv = (live && rr < NS && q < NS) ? buf[rr * NS + q] : T(0);
+      row[u][q] = rr < N4 ? fma(-dt, Jv, rr == q ? T(1) : T(0)) : T(0);
+      row[u][N4 + q] = rr == q ? T(1) : T(0);
+    }
+    used[u] = rr >= N4;  // lanes without a row never pivot
+    myk[u] = 0;
   }
   __syncwarp();  // buf is reused for the result
-  bool used = lg >= N4;  // lanes without a row never pivot
-  int myk = 0;
 #pragma unroll
   for (int kk = 0; kk < N4; ++kk) {
-    const T x = fabs(row[kk]);
     // NaN rows sort high (and stay NaN): every lane of the group agrees on the pivot
-    T v = used ? T(-1) : (x == x ? x : static_cast<T>(__int_as_float(0x7f800000)));
-    int p = lg;
+    T v = T(-1);
+    int p = N4;
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) {
+      const T x = fabs(row[u][kk]);
+      const T xv = used[u] ? T(-1) : (x == x ? x : static_cast<T>(__int_as_float(0x7f800000)));
+      if (xv > v) {
+        v = xv;
+        p = lg + SEG * u;
+      }
+    }
 #pragma unroll
     for (int o = SEG / 2; o > 0; o >>= 1) {
       const T ov = __shfl_xor_sync(kFull, v, o, SEG);
@@ -187,20 +234,51 @@ __global__ void __launch_bounds__(128) large_block_kernel(LargeArgs a) {
         p = op;
       }
     }
-    if (lg == p) {
-      used = true;
-      myk = kk;
+    const int pl = p % SEG, pu = p / SEG;  // owner lane and its row slot
+#pragma unroll
+    for (int u = 0; u < RPL; ++u)
+      if (lg == pl && u == pu) {
+        used[u] = true;
+        myk[u] = kk;
+      }
+    // the pivot row, broadcast entry by entry from its owner
+    T prow[2 * N4];
+#pragma unroll
+    for (int q = 0; q < 2 * N4; ++q) {
+      T src = row[0][q];
+#pragma unroll
+      for (int u = 1; u < RPL; ++u) src = (pu == u) ? row[u][q] : src;
+      prow[q] = __shfl_sync(kFull, src, pl, SEG);
     }
-    const T inv = T(1) / __shfl_sync(kFull, row[kk], p, SEG);
-    const T f = lg == p ? T(1) - inv : row[kk] * inv;
+    const T inv = T(1) / prow[kk];
 #pragma unroll
-    for (int q = 0; q < 2 * N4; ++q)
-      row[q] = fma(-f, __shfl_sync(kFull, row[q], p, SEG), row[q]);
-  }
-  if (lg < N4) {
+    for (int u = 0; u < RPL; ++u) {
+      const bool piv = lg == pl && u == pu;
+      const T f = piv ? T(1) - inv : row[u][kk] * inv;
 #pragma unroll
-    for (int q = 0; q < N4; ++q) buf[myk * LD + q] = row[N4 + q];  // A^-1[myk][q]
+      for (int q = 0; q < 2 * N4; ++q) row[u][q] = fma(-f, prow[q], row[u][q]);
+    }
   }
+  if constexpr (kWide) {
+    // rows myk of A^-1 straight from registers: forward slot[q][myk] (transposed),
+    // reverse slot[myk][q]
+#pragma unroll
+    for (int u = 0; u < RPL; ++u)
+      if (lg + SEG * u < N4) {
+#pragma unroll
+        for (int q = 0; q < N4; ++q) {
+          if (a.reverse) slot[myk[u] * N4 + q] = row[u][N4 + q];
+          else slot[q * N4 + myk[u]] = row[u][N4 + q];
+        }
+      }
+    return;
+  }
+#pragma unroll
+  for (int u = 0; u < RPL; ++u)
+    if (lg + SEG * u < N4) {
+#pragma unroll
+      for (int q = 0; q < N4; ++q) buf[myk[u] * LD + q] = row[u][N4 + q];  // A^-1[myk][q]
+    }
   __syncwarp();
   if (live) {
     for (int i = lg; i < N4 * N4; i += SEG) {
@@ -281,10 +359,10 @@ __global__ void __launch_bounds__(kLargeThreads) large_param_kernel(LargeArgs a)
     if (lane == 0) s_part[warp][q] = v;
   }
   __syncthreads();
-  if (tid < NP) {
+  for (int q = tid; q < NP; q += kLargeThreads) {  // NP may exceed the block's threads
     double v = 0.0;
-    for (int w = 0; w < kLargeThreads / 32; ++w) v += s_part[w][tid];
-    a.acc[static_cast<size_t>(b) * NP + tid] += v;
+    for (int w = 0; w < kLargeThreads / 32; ++w) v += s_part[w][q];
+    a.acc[static_cast<size_t>(b) * NP + q] += v;
   }
 }
 

@@ -957,22 +957,26 @@ constexpr int chain_depth() {
 // arrays checked by the C ABI).  The width N is a template parameter so the
 // mat-vec unrolls: the block's column loads do not depend on d_{j-1} and are
 // issued before it, leaving one shared-memory round trip and N/4 dependent
-// FMAs on the step-to-step path.
+// FMAs on the step-to-step path.  Lane l owns components l and, for N > 32,
+// l + 32 (KC components per lane).
 template <typename T, int N, int W>
 __global__ void __launch_bounds__(32 * W) mlp_chain_kernel(ChainArgs a) {
+  constexpr int KC = (N + 31) / 32;
   constexpr int D = chain_depth<T, N, W>();
   constexpr int H = D / 2;
   constexpr uint32_t mbytes = static_cast<uint32_t>(sizeof(T) * N * N);
   constexpr uint32_t vbytes = static_cast<uint32_t>(sizeof(double) * N);
   constexpr size_t slot_bytes = chain_slot_bytes<T, N>();
   extern __shared__ __align__(16) unsigned char chain_smem[];
-  __shared__ T s_u[W][32];
+  __shared__ T s_u[W][32 * KC];
   __shared__ __align__(8) uint64_t s_bar[W][2];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int b = blockIdx.x * W + wib;
   // warp-uniform exit: the kernel synchronises only within a warp
   if (b >= a.B || (a.active && !a.active[b])) return;
-  const bool own = lane < N;
+  bool own[KC];
+#pragma unroll
+  for (int kc = 0; kc < KC; ++kc) own[kc] = lane + 32 * kc < N;
   unsigned char* ring = chain_smem + static_cast<size_t>(wib) * D * slot_bytes;
   uint64_t* bars = s_bar[wib];
   const unsigned char* Mb = static_cast<const unsigned char*>(a.M) +
@@ -1011,7 +1015,10 @@ __global__ void __launch_bounds__(32 * W) mlp_chain_kernel(ChainArgs a) {
   };
   issue_half(0);
   issue_half(H);
-  T dprev = (a.x_init && own) ? static_cast<T>(a.x_init[b * N + lane]) : T(0);
+  T dprev[KC];
+#pragma unroll
+  for (int kc = 0; kc < KC; ++kc)
+    dprev[kc] = (a.x_init && own[kc]) ? static_cast<T>(a.x_init[b * N + lane + 32 * kc]) : T(0);
 #pragma unroll 1
   for (int j = 0; j < a.L; ++j) {
     if (j % H == 0) {
@@ -1028,31 +1035,43 @@ __global__ void __launch_bounds__(32 * W) mlp_chain_kernel(ChainArgs a) {
     const unsigned char* slot = ring + static_cast<size_t>(j % D) * slot_bytes;
     const T* Mt = reinterpret_cast<const T*>(slot);  // Mt[q * N + r] = M_j[r][q]
     const double* rr = reinterpret_cast<const double*>(slot + mbytes);
-    // independent of d_{j-1}: row `lane` of M_j, the rhs and the x entry
-    T m[N];
+    // independent of d_{j-1}: rows `lane` (+ 32) of M_j, the rhs and the x entries
+    T m[KC][N], rc[KC];
+    double x_cur[KC];
 #pragma unroll
-    for (int q = 0; q < N; ++q) m[q] = own ? Mt[q * N + lane] : T(0);
-    const T rc = own ? static_cast<T>(rr[lane]) : T(0);
-    const double x_cur = (own && a.mode != 1) ? rr[N + lane] : 0.0;
-    // component `lane` of d_{j-1} + rhs_j (of d_{j-1} alone with post_add)
-    su[lane] = a.post_add ? dprev : dprev + rc;
+    for (int kc = 0; kc < KC; ++kc) {
+      const int r = lane + 32 * kc;
+#pragma unroll
+      for (int q = 0; q < N; ++q) m[kc][q] = own[kc] ? Mt[q * N + r] : T(0);
+      rc[kc] = own[kc] ? static_cast<T>(rr[r]) : T(0);
+      x_cur[kc] = (own[kc] && a.mode != 1) ? rr[N + r] : 0.0;
+      // component r of d_{j-1} + rhs_j (of d_{j-1} alone with post_add)
+      if (own[kc]) su[r] = a.post_add ? dprev[kc] : dprev[kc] + rc[kc];
+    }
     __syncwarp();
-    T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
+    T acc[KC];
 #pragma unroll
-    for (int q = 0; q < N; q += 4) {
-      acc0 = fma(m[q], su[q], acc0);
-      acc1 = fma(m[q + 1], su[q + 1], acc1);
-      acc2 = fma(m[q + 2], su[q + 2], acc2);
-      acc3 = fma(m[q + 3], su[q + 3], acc3);
+    for (int kc = 0; kc < KC; ++kc) {
+      T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
+#pragma unroll
+      for (int q = 0; q < N; q += 4) {
+        acc0 = fma(m[kc][q], su[q], acc0);
+        acc1 = fma(m[kc][q + 1], su[q + 1], acc1);
+        acc2 = fma(m[kc][q + 2], su[q + 2], acc2);
+        acc3 = fma(m[kc][q + 3], su[q + 3], acc3);
+      }
+      acc[kc] = (acc0 + acc1) + (acc2 + acc3) + (a.post_add ? rc[kc] : T(0));
     }
     __syncwarp();  // su and (at a half's end) its slots are free again
     if (j % H == H - 1) issue_half(j + 1 - H + D);
-    const T acc = (acc0 + acc1) + (acc2 + acc3) + (a.post_add ? rc : T(0));
-    dprev = own ? acc : T(0);
-    if (own) {
-      const double dd = static_cast<double>(acc);
-      xb[static_cast<size_t>(j) * N + lane] =
-          (a.mode == 0) ? x_cur - dd : (a.mode == 1 ? dd : x_cur + dd);
+#pragma unroll
+    for (int kc = 0; kc < KC; ++kc) {
+      dprev[kc] = own[kc] ? acc[kc] : T(0);
+      if (own[kc]) {
+        const double dd = static_cast<double>(acc[kc]);
+        xb[static_cast<size_t>(j) * N + lane + 32 * kc] =
+            (a.mode == 0) ? x_cur[kc] - dd : (a.mode == 1 ? dd : x_cur[kc] + dd);
+      }
     }
   }
   // after a timeout: give the halves still in flight a second bounded wait
@@ -1809,6 +1828,8 @@ cudaError_t launch_chain_w(const ChainArgs& ch, cudaStream_t s) {
     case 24: return launch_chain_n<T, 24, W>(ch, s);
     case 28: return launch_chain_n<T, 28, W>(ch, s);
     case 32: return launch_chain_n<T, 32, W>(ch, s);
+    case 36: return launch_chain_n<T, 36, W>(ch, s);
+    case 40: return launch_chain_n<T, 40, W>(ch, s);
     default: return cudaErrorInvalidValue;
   }
 }
