@@ -62,7 +62,7 @@ def test_missing_function_is_rejected(lib):
     assert rc == EINVAL and "tvi_vjp_p" in _lib.last_error()
 
 
-@pytest.mark.parametrize("n,P", [(0, 1), (33, 1), (2, 0), (2, 33), (5, 65), (-1, -1)])
+@pytest.mark.parametrize("n,P", [(0, 1), (41, 1), (2, 0), (2, 33), (5, 161), (-1, -1)])
 def test_bad_sizes(lib, n, P):
     rc, h = create(lib, n, P, VDP)
     assert rc == EINVAL and h.value is None
