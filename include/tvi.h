@@ -134,7 +134,8 @@ typedef struct {
                               used for chunk attempts of exactly this length */
   int predictor_hidden;    /* hidden width of the predictor MLP (even, <= 256) */
   int scheme;              /* tvi_scheme: TVI_BACKWARD_EULER (default) or
-                              TVI_FORWARD_EULER (linear, van der Pol and user models) */
+                              TVI_FORWARD_EULER (every model with FP64 or FP32 blocks;
+                              not with BF16 blocks or a predictor) */
 } tvi_options;
 
 /* Fill *opt with defaults: chunk 1, tol_abs 1e-8, tol_rel 0, max_iter 50, FP64,

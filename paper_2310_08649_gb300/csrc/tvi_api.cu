@@ -114,10 +114,11 @@ tvi_status check_model(const tvi_model* m) {
 
 // BF16 block products run on the tensor cores of the MLP path only
 tvi_status check_precision(const tvi_model* m, const tvi_options* o) {
-  if (o->scheme == TVI_FORWARD_EULER && (is_mlp(m) || o->predictor))
+  if (o->scheme == TVI_FORWARD_EULER &&
+      ((is_mlp(m) && o->precision == tvi::kPrecBf16) || o->predictor))
     return fail(TVI_EUNSUPPORTED,
-                "forward Euler is built for the linear, van der Pol and user models, without a "
-                "predictor");
+                "forward Euler runs with FP64 or FP32 blocks (no tensor-core blocks) and "
+                "without a predictor");
   if (m->kind == TVI_MODEL_USER && o->precision == tvi::kPrecBf16)
     return fail(TVI_EUNSUPPORTED, "user models run with FP64 or FP32 blocks");
   if (o->precision != tvi::kPrecBf16) return TVI_OK;

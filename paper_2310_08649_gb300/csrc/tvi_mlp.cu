@@ -217,6 +217,7 @@ struct ResidualArgs {
   MlpDims d;
   int B, N, i0, L, c;
   int reverse;               // 1: adjoint -- y from the trajectory at step i0 + L - j, no R
+  int fe;                    // forward Euler (forward pass): h and its derivatives at y_{j-1}
   const double* times;
   const int* lengths;
   const double* params;      // FP64 parameters (T = double)
@@ -258,6 +259,8 @@ __global__ void __launch_bounds__(kTileThreads) mlp_residual_kernel(ResidualArgs
       const int j = j0 + p;
       if (a.reverse)
         v = a.ytraj[(static_cast<size_t>(b) * (a.N + 1) + step_of(1, a.i0, a.L, j)) * d.n + c];
+      else if (a.fe)  // R_j = dy_j - dy_{j-1} - dt_j h(y_{j-1})
+        v = a.yi[b * d.n + c] + (j > 0 ? dyb[(j - 1) * d.n + c] : 0.0);
       else
         v = a.yi[b * d.n + c] + dyb[j * d.n + c];
     }
@@ -368,6 +371,7 @@ struct BlocksArgs {
   const int* active;  // [B] or null
   void* M;            // [B][c][n][n] in T
   int first_wait_polls;  // tensor-core kernel: poll limit of each block's first data wait
+  int fe;             // forward Euler: B = I + dt J (no inverse); reverse rows take dt_{k+1}
 };
 
 // weight i of the flat parameter vector in the block precision
@@ -449,8 +453,11 @@ __global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, 
   const int tid = threadIdx.x;
   const int len = a.lengths ? min(max(a.lengths[b], 0), a.N) : a.N;
   const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
+  // forward Euler's adjoint couples a_k to a_{k+1} through step k + 1
+  const int kshift = (a.fe && a.reverse) ? 1 : 0;
   for (int p = tid; p < TP; p += kTileThreads)
-    sdt[p] = static_cast<T>(p < np ? step_dt(tb, len, step_of(a.reverse, a.i0, a.L, j0 + p)) : 0.0);
+    sdt[p] = static_cast<T>(
+        p < np ? step_dt(tb, len, step_of(a.reverse, a.i0, a.L, j0 + p) + kshift) : 0.0);
   const int ln = __ffs(n) - 1;    // n and NT are powers of two
   const int lnt = __ffs(NT) - 1;
   for (int e = tid; e < h1 * NT; e += kTileThreads) {
@@ -518,7 +525,8 @@ __global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, 
         for (int i = 0; i < 4; ++i) {
           const int r = r0 + i;
           const T J = narrow<T>(dvt[p * dvs + h1 + h2 + r]) * acc[i][k2];
-          Ap[r * 2 * n + c] = ((r == c) ? T(1) : T(0)) - sdt[p] * J;
+          // backward Euler A = I - dt J (inverted below); forward Euler B = I + dt J
+          Ap[r * 2 * n + c] = ((r == c) ? T(1) : T(0)) + (a.fe ? sdt[p] : -sdt[p]) * J;
           Ap[r * 2 * n + n + c] = (r == c) ? T(1) : T(0);
         }
       }
@@ -526,6 +534,17 @@ __global__ void __launch_bounds__(kTileThreads) mlp_blocks_kernel(BlocksArgs a, 
   }
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
+  if (a.fe) {
+    // no inverse: B stored as the chain reads it (Mo[col][r] = B[r][col]; the
+    // adjoint's B^T untransposed, Mo[col][r] = B[col][r])
+    for (int e = tid; e < np * n * n; e += kTileThreads) {
+      const int p = e / (n * n), rc = e - p * n * n, col = rc / n, r = rc - col * n;
+      const T* Ap = sA + p * n * 2 * n;
+      static_cast<T*>(a.M)[(static_cast<size_t>(b) * a.c + j0 + p) * n * n + rc] =
+          a.reverse ? Ap[col * 2 * n + r] : Ap[r * 2 * n + col];
+    }
+    return;
+  }
   for (int p = warp; p < np; p += kTileThreads / 32)
     gj_invert_store<T>(sA + p * n * 2 * n, n, lane,
                        static_cast<T*>(a.M) + (static_cast<size_t>(b) * a.c + j0 + p) * n * n,
@@ -1107,6 +1126,9 @@ struct VjpArgs {
   const double* dv;        // [B][c][h1+h2+n] activation derivatives
   double* res;             // [B][c][n] or null
   double* del;             // [B*c][h1+h2+n] or null
+  int fe;                  // forward Euler: the products take a_{k+1} (row j-1, or the
+                           // carry) and dt_{k+1}: r_j = g_k + a_{j-1} - a_j + dt_{k+1} J^T
+                           // a_{j-1}, del = dt_{k+1} (delta's of a_{j-1}) at y_k
 };
 
 template <int KIND, int TP, typename T>
@@ -1140,9 +1162,13 @@ __global__ void __launch_bounds__(kTileThreads) mlp_vjp_kernel(VjpArgs a) {
     else sz3[(q - h1 - h2) * TP + pp] = v;
   }
   __syncthreads();
-  // delta3 = a * h'(z3)
-  for (int r = g; r < n; r += G)
-    sz3[r * TP + p] = live ? narrow<T>(avb[j * n + r]) * sz3[r * TP + p] : T(0);
+  // delta3 = a * h'(z3): a_j, or a_{j-1} (the carry for row 0) for forward Euler
+  for (int r = g; r < n; r += G) {
+    double av = 0.0;
+    if (live) av = !a.fe ? avb[j * n + r] : (j > 0 ? avb[(j - 1) * n + r] : a.carry[b * n + r]);
+    sz3[r * TP + p] = live ? narrow<T>(av) * sz3[r * TP + p] : T(0);
+  }
+  const int kshift = a.fe ? 1 : 0;  // forward Euler: dt_{k+1}
   __syncthreads();
   if constexpr (sizeof(T) == sizeof(float)) {
     // register-tiled products; then outputs with one thread per element
@@ -1161,7 +1187,8 @@ __global__ void __launch_bounds__(kTileThreads) mlp_vjp_kernel(VjpArgs a) {
         const double prev = (jj > 0) ? avb[(jj - 1) * n + c] : a.carry[b * n + c];
         const double gk = a.g[(static_cast<size_t>(b) * (a.N + 1) + kk) * n + c];
         a.res[(static_cast<size_t>(b) * a.c + jj) * n + c] =
-            fma(step_dt(tb, len, kk), widen(sjt[c * TP + pp]), gk + prev - avb[jj * n + c]);
+            fma(step_dt(tb, len, kk + kshift), widen(sjt[c * TP + pp]),
+                gk + prev - avb[jj * n + c]);
       }
     }
     if (a.del) {
@@ -1173,7 +1200,7 @@ __global__ void __launch_bounds__(kTileThreads) mlp_vjp_kernel(VjpArgs a) {
         const float v = q < h1 ? sd1[q * TP + pp]
                                : (q < h1 + h2 ? sd2[(q - h1) * TP + pp] : sz3[(q - h1 - h2) * TP + pp]);
         a.del[(static_cast<size_t>(b) * a.c + jj) * dw + q] =
-            step_dt(tb, len, step_of(1, a.i0, a.L, jj)) * widen(v);
+            step_dt(tb, len, step_of(1, a.i0, a.L, jj) + kshift) * widen(v);
       }
     }
     return;
@@ -1194,7 +1221,7 @@ __global__ void __launch_bounds__(kTileThreads) mlp_vjp_kernel(VjpArgs a) {
   __syncthreads();
   if (!live) return;
   const int k = step_of(1, a.i0, a.L, j);
-  const double dt = step_dt(tb, len, k);
+  const double dt = step_dt(tb, len, k + kshift);
   if (a.res) {
     // r_j = g_k + a_{j-1} - a_j + dt (W1^T delta1), assembled in FP64
     for (int c = g; c < n; c += G) {
@@ -1398,14 +1425,18 @@ __global__ void mlp_carry_kernel(int B, int n, int L, int c, const double* av, d
 }
 
 // gradients are NaN when a tensor-core wait gave up (results invalid)
-__global__ void mlp_adjoint_end_kernel(int B, int n, int Np1, const double* carry, const double* g,
-                                       double* dy0, const double* acc, double* dparams, int P,
+// dL/dy0 = a_1 + dL/dy_0 (backward Euler), or row 0 of `row0` [B][c][n] (forward
+// Euler: the y_0 pass's residual)
+__global__ void mlp_adjoint_end_kernel(int B, int n, int Np1, int c, const double* carry,
+                                       const double* g, const double* row0, double* dy0,
+                                       const double* acc, double* dparams, int P,
                                        const int* tcerr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool bad = *tcerr != 0;
   if (dy0 && i < B * n)
     dy0[i] = bad ? __longlong_as_double(0x7ff8000000000000LL)
-                 : carry[i] + g[static_cast<size_t>(i / n) * Np1 * n + (i % n)];
+           : row0 ? row0[static_cast<size_t>(i / n) * c * n + (i % n)]
+                  : carry[i] + g[static_cast<size_t>(i / n) * Np1 * n + (i % n)];
   if (i < P) dparams[i] = bad ? __longlong_as_double(0x7ff8000000000000LL) : acc[i];
 }
 
@@ -1921,6 +1952,7 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
                         void* workspace, cudaStream_t s, int* host_worst) {
   const MlpDims d = dims_of(n, h1, h2);
   const int B = a.B, N = a.N, c = a.chunk;
+  const int fe = a.scheme == kSchemeForward ? 1 : 0;
   Ws w = carve(static_cast<char*>(workspace), B, c, d, precision, false);
   TVI_TRY(cudaMemsetAsync(w.worst, 0, sizeof(int), s));
   TVI_TRY(cudaMemsetAsync(w.tcerr, 0, sizeof(int), s));
@@ -1942,7 +1974,7 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
                                    w.status0, s));
     for (int it = 0;; ++it) {
       ResidualArgs r{};
-      r.d = d; r.B = B; r.N = N; r.i0 = i0; r.L = L; r.c = c; r.reverse = 0;
+      r.d = d; r.B = B; r.N = N; r.i0 = i0; r.L = L; r.c = c; r.reverse = 0; r.fe = fe;
       r.times = a.times; r.lengths = a.lengths; r.params = a.params; r.yi = w.yi; r.dy = w.dy;
       r.R = w.R; r.dv = w.dv; r.norm = w.norm; r.active = w.active;
       TVI_TRY(launch_residual(kind, false, r, s));
@@ -1964,10 +1996,11 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
       BlocksArgs bk{};
       bk.d = d; bk.B = B; bk.N = N; bk.i0 = i0; bk.L = L; bk.c = c; bk.reverse = 0;
       bk.times = a.times; bk.lengths = a.lengths; bk.Wf = w.Wf; bk.Wd = a.params; bk.dv = w.dv;
-      bk.active = w.active; bk.M = w.M;
+      bk.active = w.active; bk.M = w.M; bk.fe = fe;
       ChainArgs ch{};
       ch.B = B; ch.n = n; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 0; ch.M = w.M;
       ch.rhs_buf = w.R; ch.active = w.active; ch.x = w.dy; ch.mode = 0; ch.err = w.tcerr;
+      ch.post_add = fe;  // forward Euler: d_j = (I + dt J) d_{j-1} + R_j
       TVI_TRY(launch_blocks_any(bk, precision, w.tcerr, s));
       TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s));
     }
@@ -2004,6 +2037,7 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
                         void* workspace, cudaStream_t s) {
   const MlpDims d = dims_of(n, h1, h2);
   const int B = a.B, N = a.N, c = a.chunk;
+  const int fe = a.scheme == kSchemeForward ? 1 : 0;
   Ws w = carve(static_cast<char*>(workspace), B, c, d, precision, true);
   TVI_TRY(cudaMemsetAsync(w.tcerr, 0, sizeof(int), s));
   note_launch();
@@ -2014,46 +2048,8 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
   // mixed precision: every MLP pass of the adjoint in FP32 (the refinement
   // residual is still assembled in FP64); FP64 blocks: FP64 throughout
   const bool mixed = precision != kPrecFp64;
-  const int nch = (N + c - 1) / c;
-  for (int ci = nch - 1; ci >= 0; --ci) {
-    const int i0 = ci * c;
-    const int L = (N - i0 < c) ? N - i0 : c;
-    // activation derivatives at the stored trajectory, rows in reverse step order
-    ResidualArgs r{};
-    r.d = d; r.B = B; r.N = N; r.i0 = i0; r.L = L; r.c = c; r.reverse = 1;
-    r.times = a.times; r.lengths = a.lengths; r.params = a.params; r.ytraj = a.y; r.dv = w.dv;
-    r.act = w.act; r.Wf = w.Wf;
-    TVI_TRY(launch_residual(kind, mixed, r, s));
-    BlocksArgs bk{};
-    bk.d = d; bk.B = B; bk.N = N; bk.i0 = i0; bk.L = L; bk.c = c; bk.reverse = 1;
-    bk.times = a.times; bk.lengths = a.lengths; bk.Wf = w.Wf; bk.Wd = a.params; bk.dv = w.dv;
-    bk.M = w.M;
-    // a_j = A^-T (a_{j-1} + g_k), a_{-1} = carry
-    ChainArgs ch{};
-    ch.B = B; ch.n = n; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 1; ch.M = w.M;
-    ch.rhs_traj = a.grad_out; ch.x_init = w.carry; ch.x = w.dy; ch.mode = 1; ch.err = w.tcerr;
-    TVI_TRY(launch_blocks_any(bk, precision, w.tcerr, s));
-    TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s));
-    VjpArgs v{};
-    v.d = d; v.B = B; v.N = N; v.i0 = i0; v.L = L; v.c = c; v.times = a.times;
-    v.lengths = a.lengths; v.params = a.params; v.Wf = w.Wf; v.g = a.grad_out;
-    v.carry = w.carry; v.av = w.dy;
-    v.dv = w.dv;  // backward passes only: the derivative pass above stored act' and h'
-    for (int it = 0; it < refine; ++it) {
-      v.res = w.R;
-      v.del = nullptr;
-      TVI_TRY(launch_vjp(kind, mixed, v, s));
-      ChainArgs cr = ch;
-      cr.rhs_traj = nullptr;
-      cr.rhs_buf = w.R;
-      cr.x_init = nullptr;
-      cr.mode = 2;  // a += correction
-      TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(cr, s) : launch_chain<float>(cr, s));
-    }
-    // parameter gradient factors at the final a, then the tiled sums
-    v.res = nullptr;
-    v.del = w.del;  // the activations were stored by the derivative pass
-    TVI_TRY(launch_vjp(kind, mixed, v, s));
+  // dL/dp += sum over the L rows of the activations x the factors in del
+  auto param_grad = [&](int L) -> cudaError_t {
     // pairs split into up to kMaxParamSplits ranges of >= 1024 so the tiles fill the GPU
     const int npairs = B * L;
     int nsplit = (npairs + 1023) / 1024;
@@ -2071,15 +2067,77 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
     }
     note_launch();
     mlp_param_reduce_kernel<<<(d.P + 255) / 256, 256, 0, s>>>(d.P, nsplit, w.part, w.acc);
-    TVI_TRY(cudaGetLastError());
+    return cudaGetLastError();
+  };
+  const int nch = (N + c - 1) / c;
+  for (int ci = nch - 1; ci >= 0; --ci) {
+    const int i0 = ci * c;
+    const int L = (N - i0 < c) ? N - i0 : c;
+    // activation derivatives at the stored trajectory, rows in reverse step order
+    ResidualArgs r{};
+    r.d = d; r.B = B; r.N = N; r.i0 = i0; r.L = L; r.c = c; r.reverse = 1;
+    r.times = a.times; r.lengths = a.lengths; r.params = a.params; r.ytraj = a.y; r.dv = w.dv;
+    r.act = w.act; r.Wf = w.Wf;
+    TVI_TRY(launch_residual(kind, mixed, r, s));
+    BlocksArgs bk{};
+    bk.d = d; bk.B = B; bk.N = N; bk.i0 = i0; bk.L = L; bk.c = c; bk.reverse = 1;
+    bk.times = a.times; bk.lengths = a.lengths; bk.Wf = w.Wf; bk.Wd = a.params; bk.dv = w.dv;
+    bk.M = w.M; bk.fe = fe;
+    // a_j = A^-T (a_{j-1} + g_k), a_{-1} = carry (forward Euler: a_j = B^T a_{j-1} + g_k)
+    ChainArgs ch{};
+    ch.B = B; ch.n = n; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 1; ch.M = w.M;
+    ch.rhs_traj = a.grad_out; ch.x_init = w.carry; ch.x = w.dy; ch.mode = 1; ch.err = w.tcerr;
+    ch.post_add = fe;
+    TVI_TRY(launch_blocks_any(bk, precision, w.tcerr, s));
+    TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s));
+    VjpArgs v{};
+    v.d = d; v.B = B; v.N = N; v.i0 = i0; v.L = L; v.c = c; v.times = a.times;
+    v.lengths = a.lengths; v.params = a.params; v.Wf = w.Wf; v.g = a.grad_out;
+    v.carry = w.carry; v.av = w.dy; v.fe = fe;
+    v.dv = w.dv;  // backward passes only: the derivative pass above stored act' and h'
+    for (int it = 0; it < refine; ++it) {
+      v.res = w.R;
+      v.del = nullptr;
+      TVI_TRY(launch_vjp(kind, mixed, v, s));
+      ChainArgs cr = ch;
+      cr.rhs_traj = nullptr;
+      cr.rhs_buf = w.R;
+      cr.x_init = nullptr;
+      cr.mode = 2;  // a += correction
+      TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(cr, s) : launch_chain<float>(cr, s));
+    }
+    // parameter gradient factors at the final a, then the tiled sums
+    v.res = nullptr;
+    v.del = w.del;  // the activations were stored by the derivative pass
+    TVI_TRY(launch_vjp(kind, mixed, v, s));
+    TVI_TRY(param_grad(L));
     note_launch();
     mlp_carry_kernel<<<(B * n + 255) / 256, 256, 0, s>>>(B, n, L, c, w.dy, w.carry);
     TVI_TRY(cudaGetLastError());
   }
+  if (fe && N > 0) {
+    // Forward Euler's step 1 evaluates h at y_0, so its terms sit outside every
+    // chunk: a one-row pass at y_0 with the VJP of a_1 (the carry) gives
+    // dt_1 (dh/dp)^T a_1 for the gradient and, with that row's own a set to 0,
+    // the residual g_0 + a_1 + dt_1 J(y_0)^T a_1 = dL/dy0 (App. A, explicit form).
+    ResidualArgs r{};
+    r.d = d; r.B = B; r.N = N; r.i0 = -1; r.L = 1; r.c = c; r.reverse = 1;
+    r.times = a.times; r.lengths = a.lengths; r.params = a.params; r.ytraj = a.y; r.dv = w.dv;
+    r.act = w.act; r.Wf = w.Wf;
+    TVI_TRY(launch_residual(kind, mixed, r, s));
+    TVI_TRY(cudaMemset2DAsync(w.dy, sizeof(double) * c * n, 0, sizeof(double) * n, B, s));
+    VjpArgs v{};
+    v.d = d; v.B = B; v.N = N; v.i0 = -1; v.L = 1; v.c = c; v.times = a.times;
+    v.lengths = a.lengths; v.params = a.params; v.Wf = w.Wf; v.g = a.grad_out;
+    v.carry = w.carry; v.av = w.dy; v.dv = w.dv; v.fe = 1; v.res = w.R; v.del = w.del;
+    TVI_TRY(launch_vjp(kind, mixed, v, s));
+    TVI_TRY(param_grad(1));
+  }
   const int cnt = (B * n > d.P) ? B * n : d.P;
   note_launch();
-  mlp_adjoint_end_kernel<<<(cnt + 255) / 256, 256, 0, s>>>(B, n, N + 1, w.carry, a.grad_out, a.dy0,
-                                                          w.acc, a.dparams, d.P, w.tcerr);
+  mlp_adjoint_end_kernel<<<(cnt + 255) / 256, 256, 0, s>>>(
+      B, n, N + 1, c, w.carry, a.grad_out, (fe && N > 0) ? w.R : nullptr, a.dy0, w.acc, a.dparams,
+      d.P, w.tcerr);
   return cudaGetLastError();
 }
 

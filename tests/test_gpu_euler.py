@@ -85,12 +85,18 @@ def fe_error_estimate(oracle_lib, m, w, y, tol, trials=4, seed=0):
 
 def workloads_fe():
     # linear: eigenvalues up to 100 at dt = 1/500 (1 - dt lam in (0, 1));
-    # van der Pol: mu in [10, 100] with spans short enough that mu dt <= 0.2
+    # van der Pol: mu in [10, 100] with spans short enough that mu dt <= 0.2;
+    # neural ODEs on the MLP engine: tanh n = 4 and n = 16 (the n = 16 blocks and
+    # the FP32 backward passes of the mixed-precision adjoint), SiLU n = 8
     return {"linear": workloads.linear_stiff(B=8, N=500, lam_decades=(0.0, 2.0)),
-            "vdp": workloads.vdp(B=16, N=2000, seed=51, mu_dt_max=0.2, mu_decades=(1.0, 2.0))}
+            "vdp": workloads.vdp(B=16, N=2000, seed=51, mu_dt_max=0.2, mu_decades=(1.0, 2.0)),
+            "mlp4": workloads.mlp_ode(B=4, N=300, n=4, hidden=(8, 12), t_end=3.0, seed=54),
+            "mlp16": workloads.mlp_ode(B=4, N=400, n=16, hidden=(64, 64), t_end=4.0, seed=55),
+            "silu8": workloads.mlp_ode(B=3, N=300, n=8, hidden=(16, 8), act="silu", t_end=3.0,
+                                       seed=56)}
 
 
-@pytest.mark.parametrize("which", ["linear", "vdp"])
+@pytest.mark.parametrize("which", ["linear", "vdp", "mlp4", "mlp16", "silu8"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("chunk", [1, 7, 64, 500])
 def test_forward_euler_forward_and_adjoint(tvi, oracle_lib, which, precision, chunk):
@@ -145,10 +151,40 @@ def _padded_times(times, lens):
 
 
 def test_forward_euler_rejections(tvi):
+    """Forward Euler runs without tensor-core (BF16) blocks."""
     import paper_2310_08649_gb300._lib as L
-    w = workloads.mlp_ode(B=2, N=20, n=4, hidden=(8, 8), seed=53)
+    w = workloads.mlp_ode(B=2, N=20, n=16, hidden=(64, 64), seed=53)
     m = tvi.Model.from_spec(w["spec"])
     with pytest.raises(L.TviError) as e:
-        tvi.integrate(m, tvi.Options(chunk=5, scheme="forward"), dev(w["y0"]), dev(w["times"]),
-                      dev(w["params"]))
+        tvi.integrate(m, tvi.Options(chunk=5, scheme="forward", precision="bf16"), dev(w["y0"]),
+                      dev(w["times"]), dev(w["params"]))
     assert e.value.code == -7
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_forward_euler_mlp_padded_lengths(tvi, oracle_lib, precision):
+    """Forward Euler on the MLP engine with per-series lengths padded into one launch
+    (dt = 0 past each length): padded steps keep the state, and trajectory and
+    gradients match the oracle's explicit recursion and its adjoint."""
+    w = workloads.mlp_ode(B=4, N=240, n=8, hidden=(16, 16), t_end=2.5, seed=57,
+                          lengths_range=(1, 240))
+    lens = w["lengths"]
+    lens[1] = 0
+    m = OModel.from_spec(w["spec"])
+    ref, st = oracle_lib.forward_euler(m, w["y0"], w["times"], w["params"], lengths=lens)
+    assert not st.any()
+    y, status, rc = forward(tvi, w, 50, precision, lengths=lens)
+    assert rc == 0 and not status.any()
+    for b, L in enumerate(lens):
+        assert np.all(y[b, L + 1:] == y[b, L])
+    est = fe_error_estimate(oracle_lib, m, dict(w, times=_padded_times(w["times"], lens)), ref,
+                            1e-12)
+    assert np.all(relerr_series(y, ref) <= np.maximum(GATE[precision], 10.0 * est))
+    assert fe_step_errors(oracle_lib, m, w, y, lengths=lens).max() <= STEP_GATE
+    g = workloads.random_grad_out(83, 4, 240, 8)
+    for b, L in enumerate(lens):
+        g[b, L + 1:] = 0.0
+    dp_ref, dy0_ref = oracle_lib.adjoint_euler(m, w["times"], w["params"], ref, g, lengths=lens)
+    dp, dy0 = adjoint(tvi, w, 50, precision, ref, g, lengths=lens)
+    assert relerr(dp, dp_ref) <= GATE[precision]
+    assert relerr(dy0, dy0_ref) <= GATE[precision]
