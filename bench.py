@@ -388,8 +388,10 @@ def roofline(args, w, stats, fwd_ms, adj_ms, refine):
     else:
         n, (h1, h2) = w["spec"]["n"], w["spec"]["hidden"]
         fma = n * h1 + h1 * h2 + h2 * n  # FMAs of one MLP evaluation (activations not counted)
-        # forward: one FP64 MLP evaluation per pair per Newton pass (the residual)
-        fwd_ops = float(np.sum((upd + nchk) * spc) * fma)
+        # forward: one FP64 MLP evaluation per pair per Newton pass after an update
+        # (the residual); an attempt's first pass starts from dy = 0, where every
+        # step evaluates the network at the chunk start: once per series
+        fwd_ops = float(np.sum(upd * spc + nchk) * fma)
         # adjoint: a derivative pass and refine + 1 backward passes per pair, in FP64
         # with FP64 blocks; in FP32 with FP32 / BF16 blocks (no FP64 roof)
         adj_ops = float(B * N * (refine + 2) * fma) if args.precision == "fp64" else 0.0

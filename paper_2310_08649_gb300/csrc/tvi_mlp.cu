@@ -311,6 +311,55 @@ __global__ void __launch_bounds__(kTileThreads) mlp_residual_kernel(ResidualArgs
   }
 }
 
+// First residual of a chunk attempt (forward pass).  The attempt starts from
+// dy = 0 (Sec. 2.3), so every step of the chunk evaluates the network at the
+// same point y_i + 0 (backward Euler at y_i + dy_j, forward Euler at
+// y_i + dy_{j-1}).  One block per series evaluates it once -- the FP64 code and
+// summation order of the per-pair tiles, so the values are the same -- and
+// writes R_j = dy_j - dy_{j-1} - dt_j h = -dt_j h and the activation
+// derivatives of every step of the chunk.  Grid: B.
+template <int KIND>
+__global__ void __launch_bounds__(kTileThreads) mlp_residual_start_kernel(ResidualArgs a) {
+  __shared__ double sy[32], sa1[128], sa2[128], sz3[32], sh[32], sdv[128 + 128 + 32];
+  const int b = blockIdx.x;
+  if (a.active && !a.active[b]) return;
+  const MlpDims d = a.d;
+  const int tid = threadIdx.x;
+  const MlpW<double> w = mlp_split(a.params, d);
+  const double* dyb = a.dy + static_cast<size_t>(b) * a.c * d.n;
+  for (int c = tid; c < d.n; c += kTileThreads) sy[c] = a.yi[b * d.n + c] + dyb[c];
+  __syncthreads();
+  const int dvs = d.h1 + d.h2 + d.n;
+  mlp_tile_forward<KIND, 1, double>(w, d, sy, sa1, sa2, sz3, 1, sdv, dvs);
+  for (int r = tid; r < d.n; r += kTileThreads) {
+    double h, dh;
+    act_out<KIND>(sz3[r], h, dh);
+    sdv[d.h1 + d.h2 + r] = dh;
+    sh[r] = h;
+  }
+  __syncthreads();
+  // the same derivatives for every step (dvs is even: h1, h2 are multiples of 4)
+  const int half = dvs / 2;
+  double2* dv2 = reinterpret_cast<double2*>(a.dv + static_cast<size_t>(b) * a.c * dvs);
+  for (int e = tid; e < a.L * half; e += kTileThreads) {
+    const int q = e % half;
+    dv2[e] = make_double2(sdv[2 * q], sdv[2 * q + 1]);
+  }
+  const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
+  const int len = a.lengths ? min(max(a.lengths[b], 0), a.N) : a.N;
+  double* Rb = a.R + static_cast<size_t>(b) * a.c * d.n;
+  unsigned long long mx = 0ull;
+  for (int e = tid; e < a.L * d.n; e += kTileThreads) {
+    const int j = e / d.n, r = e - j * d.n;
+    const double R = fma(-step_dt(tb, len, a.i0 + 1 + j), sh[r], 0.0);
+    Rb[e] = R;
+    mx = umax64(mx, abs_bits(R));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = umax64(mx, __shfl_xor_sync(kFull, mx, o));
+  if ((tid & 31) == 0 && mx) atomicMax(a.norm + b, mx);
+}
+
 struct CheckArgs {
   int B, it, max_iter;
   double tol_abs, tol_rel;
@@ -1546,6 +1595,16 @@ cudaError_t launch_residual_t(const ResidualArgs& r, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// first residual of a chunk attempt: the network once per series
+cudaError_t launch_residual_start(int kind, const ResidualArgs& r, cudaStream_t s) {
+  note_launch();
+  if (kind == kKindMlpTanh)
+    mlp_residual_start_kernel<kKindMlpTanh><<<r.B, kTileThreads, 0, s>>>(r);
+  else
+    mlp_residual_start_kernel<kKindMlpSilu><<<r.B, kTileThreads, 0, s>>>(r);
+  return cudaGetLastError();
+}
+
 // FP64 always for the Newton residual; the adjoint's derivative pass in FP32
 // when the blocks are FP32 / BF16
 cudaError_t launch_residual(int kind, bool fp32, const ResidualArgs& r, cudaStream_t s) {
@@ -1977,7 +2036,7 @@ cudaError_t mlp_forward(int kind, int n, int h1, int h2, int precision, const Fw
       r.d = d; r.B = B; r.N = N; r.i0 = i0; r.L = L; r.c = c; r.reverse = 0; r.fe = fe;
       r.times = a.times; r.lengths = a.lengths; r.params = a.params; r.yi = w.yi; r.dy = w.dy;
       r.R = w.R; r.dv = w.dv; r.norm = w.norm; r.active = w.active;
-      TVI_TRY(launch_residual(kind, false, r, s));
+      TVI_TRY(it == 0 ? launch_residual_start(kind, r, s) : launch_residual(kind, false, r, s));
       TVI_TRY(cudaMemsetAsync(w.remaining, 0, sizeof(int), s));
       CheckArgs ck{B, it, a.max_iter, a.tol_abs, a.tol_rel, w.norm, w.norm0, w.active, w.status,
                    w.iters, w.remaining};
