@@ -45,7 +45,10 @@ typedef enum {
                              Test hook: a non-negative integer in the environment variable
                              TVI_TEST_TC_FIRST_WAIT_POLLS bounds the first data wait of each
                              tensor-core block at that many polls (0: gives up at once), read
-                             at every launch; unset, the full limit applies */
+                             at every launch; unset, the full limit applies.  (A second test
+                             hook, TVI_TEST_PER_PAIR_FIRST_PASS=1, makes the neural-ODE
+                             forward evaluate an attempt's first residual per step instead
+                             of once per series; results are the same bit for bit.) */
   TVI_EUNSUPPORTED = -7   /* model/precision/size combination not built */
 } tvi_status;
 

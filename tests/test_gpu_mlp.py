@@ -175,6 +175,51 @@ def test_mlp_chunk_halving(tvi, oracle_lib):
     assert be_step_errors(oracle_lib, m, w, y).max() <= STEP_GATE
 
 
+FIRST_PASS_CASES = [
+    # (n, hidden, act, precision, scheme, chunk)
+    (4, (8, 12), "tanh", "fp64", "backward", 240),   # halves (stiff weights below)
+    (16, (64, 64), "tanh", "bf16", "backward", 37),
+    (16, (64, 64), "silu", "fp32", "forward", 50),
+    (32, (128, 128), "silu", "bf16", "backward", 64),
+    (32, (128, 128), "silu", "fp64", "forward", 64),
+]
+
+
+@pytest.mark.parametrize("case", FIRST_PASS_CASES)
+def test_first_pass_once_per_series_is_bit_identical(tvi, monkeypatch, case):
+    """Every chunk attempt starts from dy = 0, so its first residual evaluates the
+    network at the chunk start for every step; the forward pass evaluates it once per
+    series.  With the test hook TVI_TEST_PER_PAIR_FIRST_PASS=1 every step evaluates it
+    itself.  Trajectory, statistics and status must agree bit for bit (non-uniform
+    steps, padded lengths, ragged chunks; the first case also halves its chunks)."""
+    n, hidden, act, precision, scheme, chunk = case
+    B, N = 5, 240
+    w = workloads.mlp_ode(B=B, N=N, n=n, hidden=hidden, act=act, t_end=5.0 if n == 4 else 2.0,
+                          seed=71, lengths_range=(150, N))
+    if n == 4:
+        w["params"] = w["params"] * 3.0
+    rng = np.random.default_rng(72)
+    dt = rng.uniform(0.5, 1.5, (B, N)) * w["times"][:, 1:2]
+    w["times"] = np.concatenate([np.zeros((B, 1)), np.cumsum(dt, axis=1)], axis=1)
+    m = tvi.Model.from_spec(w["spec"])
+    o = tvi.Options(chunk=chunk, tol_abs=1e-11, precision=precision, max_iter=12 if n == 4 else 60,
+                    scheme=scheme)
+    args = (dev(w["y0"]), dev(w["times"]), dev(w["params"]), dev(w["lengths"], torch.int32))
+    runs = []
+    for hook in ("0", "1"):
+        monkeypatch.setenv("TVI_TEST_PER_PAIR_FIRST_PASS", hook)
+        y, stats, st, rc = tvi.integrate(m, o, *args, raise_on_status=False)
+        torch.cuda.synchronize()
+        runs.append((y.cpu().numpy(), stats.cpu().numpy(), st.cpu().numpy(), rc))
+    monkeypatch.delenv("TVI_TEST_PER_PAIR_FIRST_PASS")
+    (y0, s0, st0, rc0), (y1, s1, st1, rc1) = runs
+    assert rc0 == rc1 == 0 and not st0.any() and np.array_equal(st0, st1)
+    assert np.array_equal(s0, s1)
+    assert np.array_equal(y0.view(np.uint64), y1.view(np.uint64))
+    if n == 4:
+        assert s0[:, 2].max() >= 1  # chunks were halved
+
+
 def test_tc_wait_timeout_reports_status(tvi, monkeypatch):
     """The tensor-core block kernel bounds every mbarrier wait.  With the test hook
     TVI_TEST_TC_FIRST_WAIT_POLLS = 0 the first data wait of every block gives up at
