@@ -42,7 +42,7 @@ __device__ __forceinline__ int series_len(const LargeArgs& a, int b) {
 
 // dt of step k; padded steps (k > len) have dt = 0 (identity rows)
 __device__ __forceinline__ double step_dt_of(const double* tb, int len, int k) {
-  return k <= len ? tb[k] - tb[k - 1] : 0.0;
+  return (k >= 1 && k <= len) ? tb[k] - tb[k - 1] : 0.0;
 }
 
 template <class Model>

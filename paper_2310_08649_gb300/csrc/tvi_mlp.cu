@@ -94,8 +94,10 @@ __device__ __forceinline__ int step_of(int reverse, int i0, int L, int j) {
   return reverse ? i0 + L - j : i0 + 1 + j;
 }
 
+// dt of step k (1 <= k <= len); 0 for padded steps and for k = 0, the state
+// y_0 that the forward-Euler adjoint's one-row pass visits (no read of tb[-1])
 __device__ __forceinline__ double step_dt(const double* tb, int len, int k) {
-  return (k <= len) ? tb[k] - tb[k - 1] : 0.0;
+  return (k >= 1 && k <= len) ? tb[k] - tb[k - 1] : 0.0;
 }
 
 // ---------------------------------------------------------------------------
