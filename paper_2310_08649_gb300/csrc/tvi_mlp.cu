@@ -1561,11 +1561,18 @@ MlpDims dims_of(int n, int h1, int h2) {
 }
 
 constexpr size_t kMaxDynSmem = 227 * 1024;  // per-block shared memory limit
-constexpr int kResTP = 64;  // pairs per residual tile
+// pairs per residual tile: 64 for the FP32 derivative pass of the adjoint; 32
+// for the FP64 passes, whose time is the FP64 pipe's, so that smaller tiles
+// spread a chunk's pairs evenly over the SMs (n = 16, 64 x 200 pairs: 448 tiles
+// instead of 256 on 152 SMs) with half the shared memory per block
+template <typename T>
+constexpr int res_tp() {
+  return sizeof(T) == sizeof(double) ? 32 : 64;
+}
 constexpr int kVjpTP = 32;  // pairs per vector-Jacobian tile
 
-size_t residual_smem(const MlpDims& d) {
-  return sizeof(double) * (2 * d.n + d.h1 + d.h2) * kResTP;
+size_t residual_smem(const MlpDims& d, int tp) {
+  return sizeof(double) * (2 * d.n + d.h1 + d.h2) * tp;
 }
 size_t vjp_smem(const MlpDims& d) {
   return sizeof(double) * (d.n + d.h1 + d.h2) * kVjpTP;
@@ -1594,12 +1601,13 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 
 template <int KIND, typename T>
 cudaError_t launch_residual_t(const ResidualArgs& r, cudaStream_t s) {
-  const size_t sm = residual_smem(r.d);
-  cudaError_t e = set_smem(mlp_residual_kernel<KIND, kResTP, T>, sm);
+  constexpr int TP = res_tp<T>();
+  const size_t sm = residual_smem(r.d, TP);
+  cudaError_t e = set_smem(mlp_residual_kernel<KIND, TP, T>, sm);
   if (e != cudaSuccess) return e;
-  dim3 grid((r.L + kResTP - 1) / kResTP, r.B);
+  dim3 grid((r.L + TP - 1) / TP, r.B);
   note_launch();
-  mlp_residual_kernel<KIND, kResTP, T><<<grid, kTileThreads, sm, s>>>(r);
+  mlp_residual_kernel<KIND, TP, T><<<grid, kTileThreads, sm, s>>>(r);
   return cudaGetLastError();
 }
 
