@@ -1729,6 +1729,24 @@ cudaError_t launch_blocks_any(const BlocksArgs& bk, int precision, int* err, cud
 // memory (pass C reads them a second time, mostly from L2).  Shared memory per
 // warp: P (two buffers), the staged block M_j (rows padded to N + 1), q, d_in.
 // ---------------------------------------------------------------------------
+// four consecutive T (16-byte aligned) in shared memory
+__device__ __forceinline__ void ld4(const float* p, float (&u)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  u[0] = v.x; u[1] = v.y; u[2] = v.z; u[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&u)[4]) {
+  const double2 v0 = reinterpret_cast<const double2*>(p)[0];
+  const double2 v1 = reinterpret_cast<const double2*>(p)[1];
+  u[0] = v0.x; u[1] = v0.y; u[2] = v1.x; u[3] = v1.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&u)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(u[0], u[1], u[2], u[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&u)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(u[0], u[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(u[2], u[3]);
+}
+
 template <typename T, int N>
 constexpr size_t tile_warp_bytes() {
   return sizeof(T) * (2 * N * N + N * (N + 1) + 2 * N + 32);
@@ -1762,6 +1780,10 @@ __global__ void __launch_bounds__(32 * W) tile_chain_kernel(ChainArgs a) {
   // dependent arithmetic of the steps in between.
   constexpr int PF = N * sizeof(T) <= 32 ? 4 : 2;  // the deeper ring only where it fits
   constexpr int E = (N * N + 31) / 32;  // block entries a lane stages in pass A
+  constexpr int RT = N >= 12 ? 2 : 1;    // pass A register tile: RT rows x 4 columns
+  constexpr int NCQ = N / 4;
+  constexpr int kLanesA = (N / RT) * NCQ;  // <= 32
+  static_assert(N % 4 == 0 && kLanesA <= 32, "tile chain widths are multiples of 4 up to 16");
   // ---- pass A: (P, q) = composite of the tile's maps, starting from (I, 0) ----
   for (int e = lane; e < N * N; e += 32) P0[e] = (e / N == e % N) ? T(1) : T(0);
   if (lane < N) sq[lane] = T(0);
@@ -1804,12 +1826,29 @@ __global__ void __launch_bounds__(32 * W) tile_chain_kernel(ChainArgs a) {
           if (lane < N) su[lane] = a.post_add ? sq[lane] : sq[lane] + rj;
           load_a(j + PF, mreg[q], rreg[q]);
           __syncwarp();
-          for (int e = lane; e < N * N; e += 32) {
-            const int r = e / N, c = e - r * N;
-            T acc = T(0);
+          // P <- M_j P in register tiles: lane (rg, cq) forms rows RT rg .. RT rg + RT - 1
+          // and columns 4 cq .. 4 cq + 3 from 16-byte loads of P and broadcast loads
+          // of M_j's rows (k ascending, as a plain dot product)
+          if (lane < kLanesA) {
+            const int rg = lane / NCQ, cq = lane - rg * NCQ;
+            T acc[RT][4];
 #pragma unroll
-            for (int k = 0; k < N; ++k) acc = fma(sM[r * LDM + k], Pc[k * N + c], acc);
-            Pn[e] = acc;
+            for (int rr = 0; rr < RT; ++rr)
+#pragma unroll
+              for (int i = 0; i < 4; ++i) acc[rr][i] = T(0);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+              T b4[4];
+              ld4(Pc + k * N + 4 * cq, b4);
+#pragma unroll
+              for (int rr = 0; rr < RT; ++rr) {
+                const T av = sM[(RT * rg + rr) * LDM + k];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[rr][i] = fma(av, b4[i], acc[rr][i]);
+              }
+            }
+#pragma unroll
+            for (int rr = 0; rr < RT; ++rr) st4(Pn + (RT * rg + rr) * N + 4 * cq, acc[rr]);
           }
           if (lane < N) {
             T acc = a.post_add ? rj : T(0);
