@@ -817,6 +817,7 @@ def run_ours(args):
                 "dtype": {"fp32": "f32+f64", "bf16": "bf16+f32+f64"}.get(args.precision, "f64"),
                 "data": "synthetic",
                 "config": dict(workload_config(args),
+                               effective_chunk=tvi.effective_chunk(model, opts, args.N),
                                l2="flushed between timed steps (256 MB write)",
                                parallelism=f"series replicas x{world}"),
                 "newton_updates_per_chunk": float(upd.sum() / max(nchk.sum(), 1)),
