@@ -1186,6 +1186,7 @@ struct VjpArgs {
   int fe;                  // forward Euler: the products take a_{k+1} (row j-1, or the
                            // carry) and dt_{k+1}: r_j = g_k + a_{j-1} - a_j + dt_{k+1} J^T
                            // a_{j-1}, del = dt_{k+1} (delta's of a_{j-1}) at y_k
+  const int* active;       // [B] or null: series whose chunk is skipped write nothing
 };
 
 template <int KIND, int TP, typename T>
@@ -1194,6 +1195,7 @@ __global__ void __launch_bounds__(kTileThreads) mlp_vjp_kernel(VjpArgs a) {
   const MlpDims d = a.d;
   const int n = d.n, h1 = d.h1, h2 = d.h2;
   const int b = blockIdx.y;
+  if (a.active && !a.active[b]) return;  // block-uniform
   const int j0 = blockIdx.x * TP;
   const int np = min(TP, a.L - j0);
   T* sd1 = reinterpret_cast<T*>(smem);  // [h1][TP] act'(z1), then delta1
@@ -1314,6 +1316,7 @@ struct ParamArgs {
   const double* del;  // [B*c][h1+h2+n]
   double* part;       // [nsplit][P] partial sums, one per range of pairs (grid.y)
   int per;            // pairs per range (multiple of 64)
+  const int* active;  // [B] or null: pairs of series whose chunk is skipped add nothing
 };
 
 template <typename T>
@@ -1343,7 +1346,7 @@ __global__ void __launch_bounds__(256) mlp_param_grad_kernel(ParamArgs a) {
       const int pp = e / 32, q = e % 32;
       const int pi = p0 + pp;
       T xv = T(0), yv = T(0);
-      if (pi < npairs) {
+      if (pi < npairs && (!a.active || a.active[pi / a.L])) {
         const size_t row = static_cast<size_t>(pi / a.L) * a.c + (pi % a.L);
         if (r0 + q < rows[l]) xv = static_cast<T>(a.del[row * dw + doff[l] + r0 + q]);
         if (c0 + q < cols[l]) yv = static_cast<T>(a.act[row * aw + aoff[l] + c0 + q]);
@@ -1476,9 +1479,29 @@ __global__ void mlp_worst_kernel(int B, const int* status, const int* tcerr, int
 }
 
 // carry a_{i0+1} (row L-1) to the next (earlier) chunk
-__global__ void mlp_carry_kernel(int B, int n, int L, int c, const double* av, double* carry) {
+__global__ void mlp_carry_kernel(int B, int n, int L, int c, const double* av, double* carry,
+                                 const int* active) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < B * n) carry[i] = av[(static_cast<size_t>(i / n) * c + (L - 1)) * n + (i % n)];
+  if (i < B * n && (!active || active[i / n]))
+    carry[i] = av[(static_cast<size_t>(i / n) * c + (L - 1)) * n + (i % n)];
+}
+
+// Adjoint chunk of steps i0 + 1 .. i0 + L: a series takes part unless every step
+// lies past its length (dt = 0: identity blocks, no parameter terms) and dL/dy is
+// zero on all of them -- then a_k = a_{k+1} on every row and its carry passes
+// through unchanged, so skipping the chunk changes no result.  Grid: B.
+__global__ void mlp_adj_active_kernel(int n, int Np1, int i0, int L, const int* lengths,
+                                      const double* g, int* active) {
+  const int b = blockIdx.x;
+  const int len = min(max(lengths[b], 0), Np1 - 1);
+  bool any = i0 + 1 <= len;
+  if (!any) {
+    const double* gb = g + (static_cast<size_t>(b) * Np1 + i0 + 1) * n;
+    for (int e = threadIdx.x; e < L * n; e += blockDim.x)
+      if (gb[e] != 0.0) any = true;  // NaN counts as nonzero
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) active[b] = any ? 1 : 0;
 }
 
 // gradients are NaN when a tensor-core wait gave up (results invalid)
@@ -2174,14 +2197,14 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
   // residual is still assembled in FP64); FP64 blocks: FP64 throughout
   const bool mixed = precision != kPrecFp64;
   // dL/dp += sum over the L rows of the activations x the factors in del
-  auto param_grad = [&](int L) -> cudaError_t {
+  auto param_grad = [&](int L, const int* active) -> cudaError_t {
     // pairs split into up to kMaxParamSplits ranges of >= 1024 so the tiles fill the GPU
     const int npairs = B * L;
     int nsplit = (npairs + 1023) / 1024;
     nsplit = nsplit < 1 ? 1 : (nsplit > kMaxParamSplits ? kMaxParamSplits : nsplit);
     const int per = ((npairs + nsplit - 1) / nsplit + 63) / 64 * 64;
     nsplit = (npairs + per - 1) / per;
-    ParamArgs pa{d, B, L, c, w.act, w.del, w.part, per};
+    ParamArgs pa{d, B, L, c, w.act, w.del, w.part, per, active};
     const dim3 pgrid(param_grad_tiles(d), nsplit);
     if (precision == kPrecFp64) {
       note_launch();
@@ -2198,27 +2221,36 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
   for (int ci = nch - 1; ci >= 0; --ci) {
     const int i0 = ci * c;
     const int L = (N - i0 < c) ? N - i0 : c;
+    // with per-series lengths, the series whose chunk lies wholly past its length
+    // with zero dL/dy there skip it (their carry passes through)
+    int* act_mask = nullptr;
+    if (a.lengths) {
+      note_launch();
+      mlp_adj_active_kernel<<<B, 128, 0, s>>>(n, N + 1, i0, L, a.lengths, a.grad_out, w.active);
+      TVI_TRY(cudaGetLastError());
+      act_mask = w.active;
+    }
     // activation derivatives at the stored trajectory, rows in reverse step order
     ResidualArgs r{};
     r.d = d; r.B = B; r.N = N; r.i0 = i0; r.L = L; r.c = c; r.reverse = 1;
     r.times = a.times; r.lengths = a.lengths; r.params = a.params; r.ytraj = a.y; r.dv = w.dv;
-    r.act = w.act; r.Wf = w.Wf;
+    r.act = w.act; r.Wf = w.Wf; r.active = act_mask;
     TVI_TRY(launch_residual(kind, mixed, r, s));
     BlocksArgs bk{};
     bk.d = d; bk.B = B; bk.N = N; bk.i0 = i0; bk.L = L; bk.c = c; bk.reverse = 1;
     bk.times = a.times; bk.lengths = a.lengths; bk.Wf = w.Wf; bk.Wd = a.params; bk.dv = w.dv;
-    bk.M = w.M; bk.fe = fe;
+    bk.M = w.M; bk.fe = fe; bk.active = act_mask;
     // a_j = A^-T (a_{j-1} + g_k), a_{-1} = carry (forward Euler: a_j = B^T a_{j-1} + g_k)
     ChainArgs ch{};
     ch.B = B; ch.n = n; ch.L = L; ch.c = c; ch.N = N; ch.i0 = i0; ch.reverse = 1; ch.M = w.M;
     ch.rhs_traj = a.grad_out; ch.x_init = w.carry; ch.x = w.dy; ch.mode = 1; ch.err = w.tcerr;
-    ch.post_add = fe;
+    ch.post_add = fe; ch.active = act_mask;
     TVI_TRY(launch_blocks_any(bk, precision, w.tcerr, s));
     TVI_TRY(precision == kPrecFp64 ? launch_chain<double>(ch, s) : launch_chain<float>(ch, s));
     VjpArgs v{};
     v.d = d; v.B = B; v.N = N; v.i0 = i0; v.L = L; v.c = c; v.times = a.times;
     v.lengths = a.lengths; v.params = a.params; v.Wf = w.Wf; v.g = a.grad_out;
-    v.carry = w.carry; v.av = w.dy; v.fe = fe;
+    v.carry = w.carry; v.av = w.dy; v.fe = fe; v.active = act_mask;
     v.dv = w.dv;  // backward passes only: the derivative pass above stored act' and h'
     for (int it = 0; it < refine; ++it) {
       v.res = w.R;
@@ -2235,9 +2267,9 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
     v.res = nullptr;
     v.del = w.del;  // the activations were stored by the derivative pass
     TVI_TRY(launch_vjp(kind, mixed, v, s));
-    TVI_TRY(param_grad(L));
+    TVI_TRY(param_grad(L, act_mask));
     note_launch();
-    mlp_carry_kernel<<<(B * n + 255) / 256, 256, 0, s>>>(B, n, L, c, w.dy, w.carry);
+    mlp_carry_kernel<<<(B * n + 255) / 256, 256, 0, s>>>(B, n, L, c, w.dy, w.carry, act_mask);
     TVI_TRY(cudaGetLastError());
   }
   if (fe && N > 0) {
@@ -2256,7 +2288,7 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
     v.lengths = a.lengths; v.params = a.params; v.Wf = w.Wf; v.g = a.grad_out;
     v.carry = w.carry; v.av = w.dy; v.dv = w.dv; v.fe = 1; v.res = w.R; v.del = w.del;
     TVI_TRY(launch_vjp(kind, mixed, v, s));
-    TVI_TRY(param_grad(1));
+    TVI_TRY(param_grad(1, nullptr));
   }
   const int cnt = (B * n > d.P) ? B * n : d.P;
   note_launch();

@@ -133,6 +133,44 @@ def test_node32_silu_padded_lengths(tvi, oracle_lib):
         assert relerr(dy0, dy0_ref) <= GATE[precision]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adjoint_with_lengths_skips_padded_chunks_exactly(tvi, oracle_lib, precision):
+    """With per-series lengths, an adjoint chunk wholly past a series' length with zero
+    dL/dy there is skipped for that series (identity blocks, no parameter terms: its
+    carry passes through).  Short chunks and lengths from 30 to 200 make most chunks of
+    most series skippable.  Both the masked loss (skips taken) and a loss with nonzero
+    dL/dy past the lengths (no skip allowed) must match the oracle's adjoint."""
+    w = workloads.mlp_ode(B=6, N=200, n=4, hidden=(8, 12), t_end=4.0, seed=91,
+                          lengths_range=(30, 200))
+    lens = w["lengths"]
+    m = OModel.from_spec(w["spec"])
+    ref, _, st = oracle_lib.forward(m, w["y0"], w["times"], w["params"], lengths=lens,
+                                    tol_abs=1e-12)
+    assert not st.any()
+    g_full = workloads.random_grad_out(92, 6, 200, 4)
+    g_masked = g_full.copy()
+    for b, L in enumerate(lens):
+        g_masked[b, L + 1:] = 0.0
+    for g in (g_masked, g_full):
+        dp_ref, dy0_ref = oracle_lib.adjoint(m, w["times"], w["params"], ref, g, lengths=lens)
+        dp, dy0 = gpu_adjoint(tvi, w, 20, precision, ref, g, lengths=lens)
+        assert relerr(dp, dp_ref) <= GATE[precision]
+        assert relerr(dy0, dy0_ref) <= GATE[precision]
+    # forward Euler's adjoint couples a_k to step k + 1: the same skips
+    ref_fe, st = oracle_lib.forward_euler(m, w["y0"], w["times"], w["params"], lengths=lens)
+    assert not st.any()
+    tm = tvi.Model.from_spec(w["spec"])
+    o = tvi.Options(chunk=20, precision=precision, adjoint_refine=2, scheme="forward")
+    for g in (g_masked, g_full):
+        dp_ref, dy0_ref = oracle_lib.adjoint_euler(m, w["times"], w["params"], ref_fe, g,
+                                                   lengths=lens)
+        dp, dy0 = tvi.adjoint(tm, o, dev(w["times"]), dev(w["params"]), dev(ref_fe), dev(g),
+                              dev(lens, torch.int32))
+        torch.cuda.synchronize()
+        assert relerr(dp.cpu().numpy(), dp_ref) <= GATE[precision]
+        assert relerr(dy0.cpu().numpy(), dy0_ref) <= GATE[precision]
+
+
 def test_mlp_status_and_rejections(tvi):
     import paper_2310_08649_gb300._lib as L
     w = workloads.mlp_ode(B=3, N=50, n=4, hidden=(8, 8), seed=65)
