@@ -391,7 +391,15 @@ def roofline(args, w, stats, fwd_ms, adj_ms, refine):
         # forward: one FP64 MLP evaluation per pair per Newton pass after an update
         # (the residual); an attempt's first pass starts from dy = 0, where every
         # step evaluates the network at the chunk start: once per series
-        fwd_ops = float(np.sum(upd * spc + nchk) * fma)
+        # with per-series lengths only the steps within a length are evaluated: the
+        # chunks past it converge at their first pass, and whole tiles past it skip
+        # the network, so updates count the real steps of the chunks holding them
+        if w["lengths"] is not None:
+            lens = np.asarray(w["lengths"], dtype=np.float64)
+            real_chunks = np.maximum(np.ceil(lens / args.chunk), 1)
+            fwd_ops = float(np.sum(upd * (lens / real_chunks) + nchk) * fma)
+        else:
+            fwd_ops = float(np.sum(upd * spc + nchk) * fma)
         # adjoint: a derivative pass and refine + 1 backward passes per pair, in FP64
         # with FP64 blocks; in FP32 with FP32 / BF16 blocks (no FP64 roof)
         adj_ops = float(B * N * (refine + 2) * fma) if args.precision == "fp64" else 0.0

@@ -254,6 +254,27 @@ __global__ void __launch_bounds__(kTileThreads) mlp_residual_kernel(ResidualArgs
   const double* tb = a.times + static_cast<size_t>(b) * (a.N + 1);
   const int len = a.lengths ? min(max(a.lengths[b], 0), a.N) : a.N;
   const double* dyb = a.dy ? a.dy + static_cast<size_t>(b) * a.c * d.n : nullptr;
+  if (!a.reverse && a.i0 + 1 + j0 > len) {
+    // every step of the tile lies past the series' length: dt = 0, so R_j =
+    // dy_j - dy_{j-1} without the network (a finite h times dt = 0 adds nothing);
+    // the activation derivatives are written as zeros (the blocks of these steps
+    // are the identity whatever J is)
+    const int dvs = d.h1 + d.h2 + d.n;
+    double* dv_tile = a.dv + (static_cast<size_t>(b) * a.c + j0) * dvs;
+    for (int e = threadIdx.x; e < np * dvs; e += kTileThreads) dv_tile[e] = 0.0;
+    unsigned long long mx = 0ull;
+    for (int e = threadIdx.x; e < np * d.n; e += kTileThreads) {
+      const int j = j0 + e / d.n, r = e % d.n;
+      const double prev = (j > 0) ? dyb[(j - 1) * d.n + r] : 0.0;
+      const double R = dyb[j * d.n + r] - prev;
+      a.R[(static_cast<size_t>(b) * a.c + j) * d.n + r] = R;
+      mx = umax64(mx, abs_bits(R));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = umax64(mx, __shfl_xor_sync(kFull, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(a.norm + b, mx);
+    return;
+  }
   for (int e = threadIdx.x; e < d.n * TP; e += kTileThreads) {
     const int c = e / TP, p = e % TP;
     double v = 0.0;
@@ -1495,10 +1516,14 @@ __global__ void mlp_adj_active_kernel(int n, int Np1, int i0, int L, const int* 
   const int b = blockIdx.x;
   const int len = min(max(lengths[b], 0), Np1 - 1);
   bool any = i0 + 1 <= len;
-  if (!any) {
-    const double* gb = g + (static_cast<size_t>(b) * Np1 + i0 + 1) * n;
-    for (int e = threadIdx.x; e < L * n; e += blockDim.x)
-      if (gb[e] != 0.0) any = true;  // NaN counts as nonzero
+  if (!any) {  // n is a multiple of 4: rows are 16-byte aligned, read two values a load
+    const double2* gb = reinterpret_cast<const double2*>(g + (static_cast<size_t>(b) * Np1 + i0 + 1) * n);
+    const int m = L * n / 2;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < m; e += blockDim.x) {
+      const double2 v = gb[e];
+      if (v.x != 0.0 || v.y != 0.0) any = true;  // NaN counts as nonzero
+    }
   }
   any = __syncthreads_or(any);
   if (threadIdx.x == 0) active[b] = any ? 1 : 0;
@@ -2226,7 +2251,7 @@ cudaError_t mlp_adjoint(int kind, int n, int h1, int h2, int precision, const Ad
     int* act_mask = nullptr;
     if (a.lengths) {
       note_launch();
-      mlp_adj_active_kernel<<<B, 128, 0, s>>>(n, N + 1, i0, L, a.lengths, a.grad_out, w.active);
+      mlp_adj_active_kernel<<<B, 256, 0, s>>>(n, N + 1, i0, L, a.lengths, a.grad_out, w.active);
       TVI_TRY(cudaGetLastError());
       act_mask = w.active;
     }
