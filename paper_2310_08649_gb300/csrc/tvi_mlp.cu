@@ -104,11 +104,14 @@ __device__ __forceinline__ double step_dt(const double* tb, int len, int k) {
 // FP32 products of a tile of TP pairs: out(r, p) = sum_k A(r, k) X[k][p] for
 // r < R (a multiple of 4), with A(r, k) = Wg[r sr + k sk] read through the
 // read-only cache and X [K][TP] in shared memory.  Each thread owns 4 x 4
-// output tiles (16 FMAs per 4 weight loads and one 16-byte activation load);
-// the lanes of a warp share a row group, so the weight loads are broadcasts.
-// epi(r, p, value) receives every result.
+// output tiles; the lanes of a warp share a row group, so the weight loads are
+// broadcasts.  The weights of a k come in one 16-byte load when the four rows
+// are adjacent (kRowsAdjacent: sr = 1, the transposed products of the adjoint),
+// else those of four k at once per row when K is contiguous (sk = 1, K a
+// multiple of 4); k runs in ascending order either way.  epi(r, p, value)
+// receives every result.
 // ---------------------------------------------------------------------------
-template <int TP, typename Epi>
+template <int TP, bool kRowsAdjacent, typename Epi>
 __device__ __forceinline__ void tile_mm_f32(const float* __restrict__ Wg, int sr, int sk, int R,
                                             int K, const float* X, Epi epi) {
   constexpr int PG = TP / 4;
@@ -121,17 +124,37 @@ __device__ __forceinline__ void tile_mm_f32(const float* __restrict__ Wg, int sr
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
     const float* w0 = Wg + static_cast<size_t>(r0) * sr;
-    for (int k = 0; k < K; ++k) {
-      const float4 x = *reinterpret_cast<const float4*>(X + k * TP + p0);
-      float w[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) w[i] = __ldg(w0 + i * sr + k * sk);
+    auto step = [&](const float (&w)[4], const float4& x) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         acc[i][0] = fmaf(w[i], x.x, acc[i][0]);
         acc[i][1] = fmaf(w[i], x.y, acc[i][1]);
         acc[i][2] = fmaf(w[i], x.z, acc[i][2]);
         acc[i][3] = fmaf(w[i], x.w, acc[i][3]);
+      }
+    };
+    if constexpr (kRowsAdjacent) {  // sr = 1: A(r0 .. r0 + 3, k) adjacent
+#pragma unroll 2
+      for (int k = 0; k < K; ++k) {
+        const float4 x = *reinterpret_cast<const float4*>(X + k * TP + p0);
+        const float4 wv = __ldg(reinterpret_cast<const float4*>(w0 + static_cast<size_t>(k) * sk));
+        const float w[4] = {wv.x, wv.y, wv.z, wv.w};
+        step(w, x);
+      }
+    } else {  // sk = 1: A(r, k .. k + 3) adjacent
+      for (int k = 0; k < K; k += 4) {
+        float4 wr[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          wr[i] = __ldg(reinterpret_cast<const float4*>(w0 + static_cast<size_t>(i) * sr + k));
+        const float wk0[4] = {wr[0].x, wr[1].x, wr[2].x, wr[3].x};
+        const float wk1[4] = {wr[0].y, wr[1].y, wr[2].y, wr[3].y};
+        const float wk2[4] = {wr[0].z, wr[1].z, wr[2].z, wr[3].z};
+        const float wk3[4] = {wr[0].w, wr[1].w, wr[2].w, wr[3].w};
+        step(wk0, *reinterpret_cast<const float4*>(X + k * TP + p0));
+        step(wk1, *reinterpret_cast<const float4*>(X + (k + 1) * TP + p0));
+        step(wk2, *reinterpret_cast<const float4*>(X + (k + 2) * TP + p0));
+        step(wk3, *reinterpret_cast<const float4*>(X + (k + 3) * TP + p0));
       }
     }
 #pragma unroll
@@ -155,21 +178,21 @@ __device__ __forceinline__ void mlp_tile_forward(const MlpW<T>& w, const MlpDims
                                                  T* sa1, T* sa2, T* sz3, int np, double* dv_tile,
                                                  int dvs) {
   if constexpr (sizeof(T) == sizeof(float)) {
-    tile_mm_f32<TP>(w.W1, d.n, 1, d.h1, d.n, sy, [&](int r, int p, float z) {
+    tile_mm_f32<TP, false>(w.W1, d.n, 1, d.h1, d.n, sy, [&](int r, int p, float z) {
       float a, da;
       act_hidden<KIND>(z + __ldg(w.b1 + r), a, da);
       sa1[r * TP + p] = a;
       if (dv_tile && p < np) dv_tile[p * dvs + r] = widen(da);
     });
     __syncthreads();
-    tile_mm_f32<TP>(w.W2, d.h1, 1, d.h2, d.h1, sa1, [&](int r, int p, float z) {
+    tile_mm_f32<TP, false>(w.W2, d.h1, 1, d.h2, d.h1, sa1, [&](int r, int p, float z) {
       float a, da;
       act_hidden<KIND>(z + __ldg(w.b2 + r), a, da);
       sa2[r * TP + p] = a;
       if (dv_tile && p < np) dv_tile[p * dvs + d.h1 + r] = widen(da);
     });
     __syncthreads();
-    tile_mm_f32<TP>(w.W3, d.h2, 1, d.n, d.h2, sa2,
+    tile_mm_f32<TP, false>(w.W3, d.h2, 1, d.n, d.h2, sa2,
                     [&](int r, int p, float z) { sz3[r * TP + p] = z + __ldg(w.b3 + r); });
     __syncthreads();
     return;
@@ -1252,13 +1275,13 @@ __global__ void __launch_bounds__(kTileThreads) mlp_vjp_kernel(VjpArgs a) {
   __syncthreads();
   if constexpr (sizeof(T) == sizeof(float)) {
     // register-tiled products; then outputs with one thread per element
-    tile_mm_f32<TP>(w.W3, 1, h2, h2, n, sz3, [&](int c, int pp, float v) { sd2[c * TP + pp] *= v; });
+    tile_mm_f32<TP, true>(w.W3, 1, h2, h2, n, sz3, [&](int c, int pp, float v) { sd2[c * TP + pp] *= v; });
     __syncthreads();
-    tile_mm_f32<TP>(w.W2, 1, h1, h1, h2, sd2, [&](int c, int pp, float v) { sd1[c * TP + pp] *= v; });
+    tile_mm_f32<TP, true>(w.W2, 1, h1, h1, h2, sd2, [&](int c, int pp, float v) { sd1[c * TP + pp] *= v; });
     __syncthreads();
     if (a.res) {
       float* sjt = sz3 + n * TP;  // J^T a, [n][TP]
-      tile_mm_f32<TP>(w.W1, 1, n, n, h1, sd1, [&](int c, int pp, float v) { sjt[c * TP + pp] = v; });
+      tile_mm_f32<TP, true>(w.W1, 1, n, n, h1, sd1, [&](int c, int pp, float v) { sjt[c * TP + pp] = v; });
       __syncthreads();
       for (int e = threadIdx.x; e < n * TP; e += kTileThreads) {
         const int c = e / TP, pp = e - c * TP;
