@@ -1818,6 +1818,15 @@ __device__ __forceinline__ void st4(double* p, const double (&u)[4]) {
   reinterpret_cast<double2*>(p)[1] = make_double2(u[2], u[3]);
 }
 
+// rows of P <- M_j P a lane forms in pass A: the fewest (dividing N) that fit
+// the N x N outputs into 32 lanes of RT x 4 tiles (1 at N <= 8, 2 at 12-16, 4 at
+// 20, 6 at 24)
+constexpr int tile_rows_per_lane(int N) {
+  int rt = 1;
+  while (N % rt != 0 || (N / rt) * (N / 4) > 32) ++rt;
+  return rt;
+}
+
 template <typename T, int N>
 constexpr size_t tile_warp_bytes() {
   return sizeof(T) * (2 * N * N + N * (N + 1) + 2 * N + 32);
@@ -1851,10 +1860,10 @@ __global__ void __launch_bounds__(32 * W) tile_chain_kernel(ChainArgs a) {
   // dependent arithmetic of the steps in between.
   constexpr int PF = N * sizeof(T) <= 32 ? 4 : 2;  // the deeper ring only where it fits
   constexpr int E = (N * N + 31) / 32;  // block entries a lane stages in pass A
-  constexpr int RT = N >= 12 ? 2 : 1;    // pass A register tile: RT rows x 4 columns
+  constexpr int RT = tile_rows_per_lane(N);  // pass A register tile: RT rows x 4 columns
   constexpr int NCQ = N / 4;
-  constexpr int kLanesA = (N / RT) * NCQ;  // <= 32
-  static_assert(N % 4 == 0 && kLanesA <= 32, "tile chain widths are multiples of 4 up to 16");
+  constexpr int kLanesA = (N / RT) * NCQ;    // <= 32
+  static_assert(N % 4 == 0 && N % RT == 0 && kLanesA <= 32, "tile chain widths: multiples of 4 up to 24");
   // ---- pass A: (P, q) = composite of the tile's maps, starting from (I, 0) ----
   for (int e = lane; e < N * N; e += 32) P0[e] = (e / N == e % N) ? T(1) : T(0);
   if (lane < N) sq[lane] = T(0);
@@ -2067,11 +2076,31 @@ cudaError_t launch_seq_chain(const ChainArgs& ch, cudaStream_t s) {
 // neural ODE 5.70e6 -> 6.06e6 with the tiles; n = 20 mass-damper-spring
 // 1.79e7 -> 1.57e7 (1.84e7 with the blocks read ahead: even, at slightly more
 // Newton updates) and n = 32 neural ODE 3.02e6 -> 2.42e6 (2.46e6), so the wider
-// blocks keep the sequential solve.
+// blocks keep the sequential solve.  Those figures predate the register tiles of
+// pass A (one output a lane and iteration before, two shared loads per FMA); with
+// them the tiles also take FP32 widths 20 and 24 whenever every series gets its
+// own SM (the tiled kernel runs one block of W warps per series; the sequential
+// one packs one warp per series, so it keeps large batches): measured, n = 20
+// mass-damper-spring (100 series) 1.60e7 -> 2.16e7 and n = 24 coupled neurons
+// (50 series) 8.47e6 -> 1.11e7, while n = 32 lost 3-5 % (50 and 128 series).
 template <typename T>
 cudaError_t launch_chain(const ChainArgs& ch, cudaStream_t s) {
   const int tile_max = sizeof(T) == sizeof(double) ? 8 : 16;
-  if (ch.n > tile_max) return launch_seq_chain<T>(ch, s);
+  if (ch.n > tile_max) {
+    if constexpr (sizeof(T) == sizeof(float)) {
+      int dev = 0, sms = 0;
+      if (ch.n <= 24 && cudaGetDevice(&dev) == cudaSuccess &&
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+          ch.B <= sms) {
+        switch (ch.n) {
+          case 20: return launch_tile_n<T, 20>(ch, s);
+          case 24: return launch_tile_n<T, 24>(ch, s);
+          default: break;
+        }
+      }
+    }
+    return launch_seq_chain<T>(ch, s);
+  }
   switch (ch.n) {
     case 4: return launch_tile_n<T, 4>(ch, s);
     case 8: return launch_tile_n<T, 8>(ch, s);
