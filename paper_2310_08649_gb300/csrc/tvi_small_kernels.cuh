@@ -282,8 +282,10 @@ __global__ void __launch_bounds__(small_max_threads(RPT)) forward_small_kernel(F
           mdl.rhs(yh, act[r] ? model_time<Model>(tb, fwd_euler ? k - 1 : k) : 0.0, h);
 #pragma unroll
           for (int s = 0; s < NS; ++s) {
-            R[r][s] = act[r] ? fma(-dt[r], h[s], yv[r][s] - yp[s]) : 0.0;
-            mx = umax64(mx, abs_bits(R[r][s]));
+            // rows past the attempt's end compute a value that nothing reads (every
+            // later use of R is guarded by act): no select on the FP64 result
+            R[r][s] = fma(-dt[r], h[s], yv[r][s] - yp[s]);
+            if (act[r]) mx = umax64(mx, abs_bits(R[r][s]));
           }
         }
       }
