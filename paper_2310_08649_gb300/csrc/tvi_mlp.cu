@@ -1306,42 +1306,42 @@ __global__ void __launch_bounds__(kTileThreads) mlp_vjp_kernel(VjpArgs a) {
             step_dt(tb, len, step_of(1, a.i0, a.L, jj) + kshift) * widen(v);
       }
     }
-    return;
-  }
-  // delta2 = (W3^T delta3) * act'(z2)
-  for (int c = g; c < h2; c += G) {
-    T acc = T(0);
-    for (int r = 0; r < n; ++r) acc = fma(__ldg(w.W3 + r * h2 + c), sz3[r * TP + p], acc);
-    sd2[c * TP + p] *= acc;
-  }
-  __syncthreads();
-  // delta1 = (W2^T delta2) * act'(z1)
-  for (int c = g; c < h1; c += G) {
-    T acc = T(0);
-    for (int r = 0; r < h2; ++r) acc = fma(__ldg(w.W2 + r * h1 + c), sd2[r * TP + p], acc);
-    sd1[c * TP + p] *= acc;
-  }
-  __syncthreads();
-  if (!live) return;
-  const int k = step_of(1, a.i0, a.L, j);
-  const double dt = step_dt(tb, len, k + kshift);
-  if (a.res) {
-    // r_j = g_k + a_{j-1} - a_j + dt (W1^T delta1), assembled in FP64
-    for (int c = g; c < n; c += G) {
+  } else {  // FP64: one output element a thread
+    // delta2 = (W3^T delta3) * act'(z2)
+    for (int c = g; c < h2; c += G) {
       T acc = T(0);
-      for (int r = 0; r < h1; ++r) acc = fma(__ldg(w.W1 + r * n + c), sd1[r * TP + p], acc);
-      const double prev = (j > 0) ? avb[(j - 1) * n + c] : a.carry[b * n + c];
-      const double gk = a.g[(static_cast<size_t>(b) * (a.N + 1) + k) * n + c];
-      a.res[(static_cast<size_t>(b) * a.c + j) * n + c] =
-          fma(dt, widen(acc), gk + prev - avb[j * n + c]);
+      for (int r = 0; r < n; ++r) acc = fma(__ldg(w.W3 + r * h2 + c), sz3[r * TP + p], acc);
+      sd2[c * TP + p] *= acc;
     }
-  }
-  if (a.del) {
-    const int dw = h1 + h2 + n;
-    double* dr = a.del + (static_cast<size_t>(b) * a.c + j) * dw;
-    for (int c = g; c < h1; c += G) dr[c] = dt * widen(sd1[c * TP + p]);
-    for (int c = g; c < h2; c += G) dr[h1 + c] = dt * widen(sd2[c * TP + p]);
-    for (int c = g; c < n; c += G) dr[h1 + h2 + c] = dt * widen(sz3[c * TP + p]);
+    __syncthreads();
+    // delta1 = (W2^T delta2) * act'(z1)
+    for (int c = g; c < h1; c += G) {
+      T acc = T(0);
+      for (int r = 0; r < h2; ++r) acc = fma(__ldg(w.W2 + r * h1 + c), sd2[r * TP + p], acc);
+      sd1[c * TP + p] *= acc;
+    }
+    __syncthreads();
+    if (!live) return;
+    const int k = step_of(1, a.i0, a.L, j);
+    const double dt = step_dt(tb, len, k + kshift);
+    if (a.res) {
+      // r_j = g_k + a_{j-1} - a_j + dt (W1^T delta1), assembled in FP64
+      for (int c = g; c < n; c += G) {
+        T acc = T(0);
+        for (int r = 0; r < h1; ++r) acc = fma(__ldg(w.W1 + r * n + c), sd1[r * TP + p], acc);
+        const double prev = (j > 0) ? avb[(j - 1) * n + c] : a.carry[b * n + c];
+        const double gk = a.g[(static_cast<size_t>(b) * (a.N + 1) + k) * n + c];
+        a.res[(static_cast<size_t>(b) * a.c + j) * n + c] =
+            fma(dt, widen(acc), gk + prev - avb[j * n + c]);
+      }
+    }
+    if (a.del) {
+      const int dw = h1 + h2 + n;
+      double* dr = a.del + (static_cast<size_t>(b) * a.c + j) * dw;
+      for (int c = g; c < h1; c += G) dr[c] = dt * widen(sd1[c * TP + p]);
+      for (int c = g; c < h2; c += G) dr[h1 + c] = dt * widen(sd2[c * TP + p]);
+      for (int c = g; c < n; c += G) dr[h1 + h2 + c] = dt * widen(sz3[c * TP + p]);
+    }
   }
 }
 
